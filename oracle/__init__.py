@@ -1,0 +1,195 @@
+"""Python view of the CPU oracle (plain C, FP64 / integer) for the checkerboard
+single-spin-flip Metropolis method (Weigel & Yavors'kii 2011, Section 2).
+
+TEST INFRASTRUCTURE ONLY.  The oracle is the slow, obviously correct
+restatement of the method that the CUDA library is checked against.  Only
+``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import it; the library under test never does.
+
+All spin arrays are in natural order (index x + L*y (+ L*L*z)); see
+``oracle/oracle.h`` for the conventions and the random-number counter layout.
+"""
+import ctypes
+import numpy as np
+
+from .build import build as _build
+
+_lib = None
+
+_i8p = np.ctypeslib.ndpointer(np.int8, flags="C_CONTIGUOUS")
+_f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+_f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
+_i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+_i64p = np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")
+_u32p = np.ctypeslib.ndpointer(np.uint32, flags="C_CONTIGUOUS")
+_vp = ctypes.c_void_p
+_int, _u32, _u64, _i64, _dbl = (ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64,
+                                ctypes.c_int64, ctypes.c_double)
+
+
+def lib():
+    """Load (building first if needed) the oracle shared library."""
+    global _lib
+    if _lib is None:
+        L = ctypes.CDLL(_build())
+        L.orc_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
+        L.orc_ising_init.argtypes = [_int, _int, _u64, _u32, _i8p]
+        L.orc_ea_couplings.argtypes = [_int, _int, _u64, _u32, _i8p]
+        L.orc_ising_measure.argtypes = [_int, _int, _dbl, _vp, _i8p,
+                                        ctypes.POINTER(_dbl), ctypes.POINTER(_dbl)]
+        L.orc_ising_sweeps.argtypes = [_int, _int, _dbl, _vp, _dbl, _u64, _u32, _i64, _i64,
+                                       _i8p, _vp, _vp]
+        L.orc_xy_init.argtypes = [_int, _int, _u64, _u32, _f64p]
+        L.orc_heis_init.argtypes = [_int, _int, _u64, _u32, _f64p]
+        L.orc_xy_measure.argtypes = [_int, _int, _dbl, _vp, _f64p, ctypes.POINTER(_dbl), _f64p]
+        L.orc_heis_measure.argtypes = [_int, _int, _dbl, _vp, _f64p, ctypes.POINTER(_dbl), _f64p]
+        L.orc_xy_sweeps.argtypes = [_int, _int, _dbl, _vp, _dbl, _u64, _u32, _i64, _i64,
+                                    _f64p, _vp, _vp, _dbl, _vp, _i64]
+        L.orc_xy_sweeps.restype = _i64
+        L.orc_heis_sweeps.argtypes = [_int, _int, _dbl, _vp, _dbl, _u64, _u32, _i64, _i64,
+                                      _int, _f64p, _vp, _vp, _dbl, _vp, _i64]
+        L.orc_heis_sweeps.restype = _i64
+        L.orc_ea_pt_sweeps.argtypes = [_int, _int, _i8p, _int, _f64p, _u64, _u32, _i64, _i64,
+                                       _i8p, _i32p, _f64p]
+        _lib = L
+    return _lib
+
+
+def nsites(d, L):
+    return L ** d
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def philox4x32_10(ctr, key):
+    """Philox4x32-10 of a 4-word counter under a 2-word key."""
+    out = np.zeros(4, np.uint32)
+    lib().orc_philox4x32_10(np.ascontiguousarray(ctr, np.uint32),
+                            np.ascontiguousarray(key, np.uint32), out)
+    return out
+
+
+# ------------------------------------------------------------------ Ising --
+
+def ising_init(d, L, seed, replica=0):
+    s = np.empty(nsites(d, L), np.int8)
+    lib().orc_ising_init(d, L, seed, replica, s)
+    return s
+
+
+def ea_couplings(d, L, seed, sample):
+    """+-1 forward-bond couplings, shape (d, N)."""
+    jb = np.empty((d, nsites(d, L)), np.int8)
+    lib().orc_ea_couplings(d, L, seed, sample, jb.reshape(-1))
+    return jb
+
+
+def _bonds_i8(Jb, d, L):
+    if Jb is None:
+        return None
+    jb = np.ascontiguousarray(Jb, np.int8)
+    assert jb.size == d * nsites(d, L)
+    return jb
+
+
+def _bonds_f32(Jb, d, L):
+    if Jb is None:
+        return None
+    jb = np.ascontiguousarray(Jb, np.float32)
+    assert jb.size == d * nsites(d, L)
+    return jb
+
+
+def ising_measure(d, L, s, J=1.0, Jb=None):
+    """(E, M) of an Ising configuration (Eq. 1)."""
+    jb = _bonds_i8(Jb, d, L)
+    E, M = _dbl(), _dbl()
+    lib().orc_ising_measure(d, L, J, _ptr(jb), np.ascontiguousarray(s, np.int8),
+                            ctypes.byref(E), ctypes.byref(M))
+    return E.value, M.value
+
+
+def ising_sweeps(d, L, s, beta, seed, t0, nsweeps, J=1.0, Jb=None, replica=0, series=True):
+    """Run nsweeps sweeps in place on s; return (E[nsweeps], |m|[nsweeps])."""
+    assert s.dtype == np.int8 and s.flags.c_contiguous
+    jb = _bonds_i8(Jb, d, L)
+    E = np.empty(nsweeps) if series else None
+    m = np.empty(nsweeps) if series else None
+    lib().orc_ising_sweeps(d, L, J, _ptr(jb), beta, seed, replica, t0, nsweeps, s,
+                           _ptr(E), _ptr(m))
+    return E, m
+
+
+# --------------------------------------------------------------- O(n) -----
+
+def xy_init(d, L, seed, replica=0):
+    th = np.empty(nsites(d, L))
+    lib().orc_xy_init(d, L, seed, replica, th)
+    return th
+
+
+def heis_init(d, L, seed, replica=0):
+    s = np.empty((nsites(d, L), 3))
+    lib().orc_heis_init(d, L, seed, replica, s.reshape(-1))
+    return s
+
+
+def xy_measure(d, L, theta, J=1.0, Jb=None):
+    jb = _bonds_f32(Jb, d, L)
+    E, M = _dbl(), np.zeros(2)
+    lib().orc_xy_measure(d, L, J, _ptr(jb), np.ascontiguousarray(theta, np.float64),
+                         ctypes.byref(E), M)
+    return E.value, M
+
+
+def heis_measure(d, L, s, J=1.0, Jb=None):
+    jb = _bonds_f32(Jb, d, L)
+    E, M = _dbl(), np.zeros(3)
+    lib().orc_heis_measure(d, L, J, _ptr(jb), np.ascontiguousarray(s, np.float64).reshape(-1),
+                           ctypes.byref(E), M)
+    return E.value, M
+
+
+def xy_sweeps(d, L, theta, beta, seed, t0, nsweeps, J=1.0, Jb=None, replica=0,
+              tie_tol=0.0, ties_cap=0, series=True):
+    """Sweeps in place on theta; return (E, |m|, near-ties (k,2) array, count)."""
+    assert theta.dtype == np.float64 and theta.flags.c_contiguous
+    jb = _bonds_f32(Jb, d, L)
+    E = np.empty(nsweeps) if series else None
+    m = np.empty(nsweeps) if series else None
+    ties = np.zeros((max(ties_cap, 1), 2), np.int64)
+    n = lib().orc_xy_sweeps(d, L, J, _ptr(jb), beta, seed, replica, t0, nsweeps, theta,
+                            _ptr(E), _ptr(m), tie_tol, _ptr(ties), ties_cap)
+    return E, m, ties[:min(n, ties_cap)], n
+
+
+def heis_sweeps(d, L, s, beta, seed, t0, nsweeps, J=1.0, Jb=None, replica=0,
+                renorm_every=16, tie_tol=0.0, ties_cap=0, series=True):
+    """Sweeps in place on s (N,3); return (E, |m|, near-ties (k,2) array, count)."""
+    assert s.dtype == np.float64 and s.flags.c_contiguous
+    jb = _bonds_f32(Jb, d, L)
+    E = np.empty(nsweeps) if series else None
+    m = np.empty(nsweeps) if series else None
+    ties = np.zeros((max(ties_cap, 1), 2), np.int64)
+    n = lib().orc_heis_sweeps(d, L, J, _ptr(jb), beta, seed, replica, t0, nsweeps,
+                              renorm_every, s.reshape(-1), _ptr(E), _ptr(m), tie_tol,
+                              _ptr(ties), ties_cap)
+    return E, m, ties[:min(n, ties_cap)], n
+
+
+# ------------------------------------------------------------ EA + PT -----
+
+def ea_pt_sweeps(d, L, Jb, betas, seed, sample, t0, nsweeps, spins, slot_of_temp):
+    """Replica-exchange sweeps of one EA sample, in place on spins (ntemps, N)
+    and slot_of_temp (ntemps,); return E[nsweeps, ntemps] by temperature."""
+    betas = np.ascontiguousarray(betas, np.float64)
+    nt = betas.size
+    assert spins.dtype == np.int8 and spins.shape == (nt, nsites(d, L))
+    assert slot_of_temp.dtype == np.int32 and slot_of_temp.flags.c_contiguous
+    E = np.empty((nsweeps, nt))
+    lib().orc_ea_pt_sweeps(d, L, np.ascontiguousarray(Jb, np.int8).reshape(-1), nt, betas,
+                           seed, sample, t0, nsweeps, spins.reshape(-1), slot_of_temp,
+                           E.reshape(-1))
+    return E

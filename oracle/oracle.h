@@ -1,0 +1,111 @@
+/*
+ * CPU oracle for the checkerboard single-spin-flip Metropolis method of
+ * Weigel & Yavors'kii, "GPU accelerated Monte Carlo simulations of lattice
+ * spin models" (Physics Procedia 15, 2011), Section 2.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This library is the slow, plain, obviously
+ * correct restatement of the method that the CUDA library is checked against.
+ * Only the test suite, the smoke check and the CPU-baseline leg of the bench
+ * may load it.  It shares no code, header, table or constant generator with
+ * the CUDA library, and the CUDA library never calls it.
+ *
+ * Conventions (the paper is silent on all of them; they are the readings the
+ * CUDA library implements too, written here independently):
+ *   - d in {2,3}, L even (the checkerboard needs an even period), N = L^d.
+ *   - natural index i = x + L*y (+ L*L*z); colour c(i) = (x+y(+z)) & 1;
+ *     colour index j = i >> 1 (the rank of i among the sites of its colour).
+ *   - a sweep updates every colour-0 site, then every colour-1 site
+ *     (Section 2: one sub-lattice, a barrier, then the other).
+ *   - neighbours are taken in the order -x,+x,-y,+y(,-z,+z) with periodic
+ *     wrap; for L = 2 a neighbour appears twice (a multigraph), so every site
+ *     always has 2d bonds and E counts d*N bonds.
+ *   - forward-bond couplings Jb[mu][i] give the bond (i, i + e_mu); the bond
+ *     to i - e_mu is Jb[mu][i - e_mu].  J_ij = J * Jb (Eq. 1 with the scalar
+ *     J factored out).
+ *   - random numbers: Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11),
+ *     key = (seed & 0xffffffff, seed >> 32), counter
+ *       ctr = (group, t, replica, purpose << 1 | colour)
+ *     with purpose 0 = sweep, 1 = initial state, 2 = couplings, 3 = replica
+ *     exchange.  The group is j >> 2 for Ising (site j uses output j & 3),
+ *     j >> 1 for XY (site j uses outputs 2(j&1), 2(j&1)+1), and j for
+ *     Heisenberg (outputs 0, 1, 2).
+ */
+#ifndef SPINMC_ORACLE_H
+#define SPINMC_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- Philox4x32-10 (published definition, SC'11) ---------------------- */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
+/* ---- Ising model, n = 1 (Eq. 1 with s_i = +-1; Eq. 2) ------------------ */
+
+/* Start configuration: s = +1 if the top bit of the site's Philox output
+ * (purpose 1, t = 0) is set, else -1.  s is in natural order, N entries. */
+void orc_ising_init(int d, int L, uint64_t seed, uint32_t replica, int8_t* s);
+
+/* Edwards-Anderson couplings: Jb[mu][i] = +1 if the top bit of output 0 of
+ * Philox(ctr = (i, mu, sample, 2 << 1)) is set, else -1. */
+void orc_ea_couplings(int d, int L, uint64_t seed, uint32_t sample, int8_t* Jb);
+
+/* Energy (Eq. 1) and total magnetisation of an Ising configuration. */
+void orc_ising_measure(int d, int L, double J, const int8_t* Jb, const int8_t* s,
+                       double* E, double* M);
+
+/* nsweeps Metropolis sweeps with sweep indices t0 .. t0+nsweeps-1.  After
+ * sweep k the energy and |m| = |M|/N are written to E_out[k], absm_out[k]
+ * (either may be NULL).  Jb may be NULL (all bonds +1). */
+void orc_ising_sweeps(int d, int L, double J, const int8_t* Jb, double beta,
+                      uint64_t seed, uint32_t replica, int64_t t0, int64_t nsweeps,
+                      int8_t* s, double* E_out, double* absm_out);
+
+/* ---- O(n) models with continuous spins, n = 2 (XY), n = 3 (Heisenberg) ---
+ * XY spins are angles theta (s = (cos theta, sin theta)); Heisenberg spins
+ * are unit vectors stored as s[3*i + a].  All arithmetic is FP64. */
+
+void orc_xy_init(int d, int L, uint64_t seed, uint32_t replica, double* theta);
+void orc_heis_init(int d, int L, uint64_t seed, uint32_t replica, double* s);
+
+/* Energy and magnetisation vector M[0..n-1] (Eq. 1). Jb (float per forward
+ * bond, [d][N]) may be NULL. */
+void orc_xy_measure(int d, int L, double J, const float* Jb, const double* theta,
+                    double* E, double* M);
+void orc_heis_measure(int d, int L, double J, const float* Jb, const double* s,
+                      double* E, double* M);
+
+/* Decisions whose margin |u - exp(-beta dE)| is below tie_tol are recorded as
+ * (t, site) pairs in ties[2*k], ties[2*k+1] for k < ties_cap; the return value
+ * is the total number of such near-ties.  E_out / absm_out as for Ising.
+ * renorm_every > 0 renormalises each spin of the colour being updated right
+ * after its decision in every sweep t with (t+1) % renorm_every == 0. */
+int64_t orc_xy_sweeps(int d, int L, double J, const float* Jb, double beta,
+                      uint64_t seed, uint32_t replica, int64_t t0, int64_t nsweeps,
+                      double* theta, double* E_out, double* absm_out,
+                      double tie_tol, int64_t* ties, int64_t ties_cap);
+int64_t orc_heis_sweeps(int d, int L, double J, const float* Jb, double beta,
+                        uint64_t seed, uint32_t replica, int64_t t0, int64_t nsweeps,
+                        int renorm_every, double* s, double* E_out, double* absm_out,
+                        double tie_tol, int64_t* ties, int64_t ties_cap);
+
+/* ---- Edwards-Anderson +-J spin glass with replica exchange --------------
+ * One disorder sample of side L with ntemps replicas (slots).  spins holds
+ * ntemps configurations [slot][N]; slot_of_temp[k] is the slot currently at
+ * inverse temperature betas[k].  Each sweep t: every slot r performs one
+ * Metropolis sweep at betas[temp of r] with replica id sample*ntemps + r;
+ * the energy of every slot is measured and E_out[(step)*ntemps + k] receives
+ * the energy at temperature k; then pairs (k, k+1) with k = t mod 2, t mod 2
+ * + 2, ... attempt a swap accepted iff Delta >= 0 or U < exp(Delta) * 2^32,
+ * Delta = (b_k - b_{k+1}) (E_{r(k)} - E_{r(k+1)}), U = output 0 of
+ * Philox(ctr = (k, t, sample, 3 << 1)). */
+void orc_ea_pt_sweeps(int d, int L, const int8_t* Jb, int ntemps, const double* betas,
+                      uint64_t seed, uint32_t sample, int64_t t0, int64_t nsweeps,
+                      int8_t* spins, int32_t* slot_of_temp, double* E_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,199 @@
+"""Exact results used to pin the oracle (no Monte Carlo, no oracle code).
+
+- Brute-force enumeration of small Ising lattices (Eq. 1 summed over all
+  2^N states) and of their exact checkerboard transition matrices (Eq. 2
+  applied to one colour at a time, Section 2).
+- Kaufman's closed-form partition function of the L x L periodic Ising model
+  (the finite-lattice solution behind the exact density of states the paper
+  compares its Wang-Landau runs with, Section 4).
+- Two-spin O(n) bond distributions p(x) ~ exp(beta J x) (1 - x^2)^((n-3)/2).
+- Binning error bars.
+
+Energies here are computed with numpy rolls of the whole configuration: a
+different formulation of Eq. (1) from the oracle's site loop.
+"""
+import itertools
+import math
+
+import numpy as np
+from scipy import integrate, special
+
+
+def roll_energy(s, d, L, J=1.0, Jb=None):
+    """E = -J sum_i sum_mu Jb[mu][i] s_i s_{i+e_mu} for natural-order arrays.
+
+    s has shape (..., N) (Ising) or (..., N, n) (vector spins)."""
+    vec = s.ndim >= 2 and s.shape[-1] in (2, 3) and s.shape[-2] == L ** d
+    shape = (L,) * d
+    lead = s.shape[:-2] if vec else s.shape[:-1]
+    if vec:
+        a = s.reshape(lead + shape[::-1] + (s.shape[-1],))
+    else:
+        a = s.reshape(lead + shape[::-1])
+    nlead = len(lead)
+    e = 0.0
+    for mu in range(d):
+        axis = nlead + (d - 1 - mu)          # natural order: x fastest
+        nb = np.roll(a, -1, axis=axis)
+        prod = (a * nb).sum(axis=-1) if vec else a.astype(np.int64) * nb
+        if Jb is not None:
+            jb = np.asarray(Jb[mu]).reshape(shape[::-1])
+            prod = prod * jb
+        e = e + prod.reshape(lead + (-1,)).sum(axis=-1)
+    return -J * e
+
+
+def all_states(N):
+    """All 2^N Ising configurations, shape (2^N, N), int8."""
+    idx = np.arange(2 ** N, dtype=np.int64)[:, None]
+    bits = (idx >> np.arange(N)) & 1
+    return (1 - 2 * bits).astype(np.int8)
+
+
+def enumerate_ising(d, L, beta, J=1.0, Jb=None):
+    """Exact <E>, <E^2>, <|m|> and ln Z by summing over all states."""
+    N = L ** d
+    S = all_states(N)
+    E = roll_energy(S, d, L, J, Jb).astype(np.float64)
+    absm = np.abs(S.astype(np.int64).sum(axis=1)) / N
+    w = -beta * E
+    wmax = w.max()
+    p = np.exp(w - wmax)
+    Z = p.sum()
+    p /= Z
+    return dict(E=(p * E).sum(), E2=(p * E * E).sum(), absm=(p * absm).sum(),
+                lnZ=math.log(Z) + wmax, energies=E, probs=p, states=S)
+
+
+def colour_of_site(d, L):
+    N = L ** d
+    i = np.arange(N)
+    c = i % L + (i // L) % L
+    if d == 3:
+        c = c + i // (L * L)
+    return c & 1
+
+
+def exact_sweep_matrix(d, L, beta, J=1.0, Jb=None):
+    """Exact transition matrix of one checkerboard sweep (colour 0 then 1).
+
+    Within a half-sweep the sites of one colour flip independently, each with
+    probability min(1, exp(-beta dE)), dE taken from the full Hamiltonian."""
+    N = L ** d
+    S = all_states(N)
+    E = roll_energy(S, d, L, J, Jb).astype(np.float64)
+    colour = colour_of_site(d, L)
+    index = {tuple(s): k for k, s in enumerate(S)}
+    mats = []
+    for c in (0, 1):
+        sites = np.nonzero(colour == c)[0]
+        T = np.zeros((len(S), len(S)))
+        for a in range(len(S)):
+            # per-site flip probabilities given the (fixed) other colour
+            pflip = []
+            for i in sites:
+                s2 = S[a].copy()
+                s2[i] = -s2[i]
+                dE = E[index[tuple(s2)]] - E[a]
+                pflip.append(1.0 if dE <= 0 else math.exp(-beta * dE))
+            for flips in itertools.product((0, 1), repeat=len(sites)):
+                s2 = S[a].copy()
+                prob = 1.0
+                for f, i, pf in zip(flips, sites, pflip):
+                    if f:
+                        s2[i] = -s2[i]
+                        prob *= pf
+                    else:
+                        prob *= 1.0 - pf
+                T[a, index[tuple(s2)]] += prob
+        mats.append(T)
+    return mats[0], mats[1], S, E
+
+
+# ------------------------------------------------------- Kaufman 1949 ----
+
+def _ln2cosh(x):
+    ax = abs(x)
+    return ax + math.log1p(math.exp(-2.0 * ax))
+
+
+def _ln2sinh_signed(x):
+    ax = abs(x)
+    return ax + math.log1p(-math.exp(-2.0 * ax)), (1.0 if x >= 0 else -1.0)
+
+
+def kaufman_lnZ(K, L):
+    """ln Z of the L x L periodic Ising model at coupling K = beta J.
+
+    Z = 1/2 (2 sinh 2K)^(L^2/2) (Z1 + Z2 + Z3 + Z4) with
+    Z1,2 = prod_{r<L} 2 cosh|sinh (L gamma_{2r+1} / 2),
+    Z3,4 = prod_{r<L} 2 cosh|sinh (L gamma_{2r} / 2),
+    cosh gamma_l = cosh 2K coth 2K - cos(pi l / L), gamma_0 = 2K + ln tanh K."""
+    c = math.cosh(2 * K) / math.tanh(2 * K)
+
+    def gamma(l):
+        if l == 0:
+            return 2 * K + math.log(math.tanh(K))
+        return math.acosh(c - math.cos(math.pi * l / L))
+
+    terms = []          # (log|Z_i|, sign)
+    for parity in (1, 0):
+        g = [gamma(2 * r + parity) for r in range(L)]
+        terms.append((sum(_ln2cosh(L * x / 2) for x in g), 1.0))
+        lsum, sgn = 0.0, 1.0
+        for x in g:
+            v, s = _ln2sinh_signed(L * x / 2)
+            lsum += v
+            sgn *= s
+        terms.append((lsum, sgn))
+    m = max(t[0] for t in terms)
+    acc = sum(s * math.exp(v - m) for v, s in terms)
+    return math.log(0.5) + (L * L / 2) * math.log(2 * math.sinh(2 * K)) + m + math.log(acc)
+
+
+def kaufman_energy_per_site(beta, L, J=1.0, h=1e-5):
+    """<E>/N = -(1/N) d ln Z / d beta by a central difference."""
+    f = lambda b: kaufman_lnZ(b * J, L)
+    return -(f(beta + h) - f(beta - h)) / (2 * h) / (L * L)
+
+
+# ------------------------------------------------- two-spin O(n) laws ----
+
+def two_spin_mean(n, beta):
+    """<s_a . s_b> for one bond of strength 1 between two O(n) spins."""
+    if n == 1:
+        return math.tanh(beta)
+    if n == 2:
+        return special.i1(beta) / special.i0(beta)
+    if n == 3:
+        return 1.0 / math.tanh(beta) - 1.0 / beta
+    raise ValueError(n)
+
+
+def two_spin_cdf(n, beta):
+    """CDF of x = s_a . s_b (n = 2, 3) under p(x) ~ e^{beta x} (1-x^2)^((n-3)/2)."""
+    if n == 3:
+        return lambda x: (np.exp(beta * x) - math.exp(-beta)) / (math.exp(beta) - math.exp(-beta))
+    if n == 2:
+        dens = lambda x: math.exp(beta * x) / math.sqrt(1 - x * x)
+        Z = integrate.quad(dens, -1, 1, limit=200)[0]
+
+        def cdf(xs):
+            xs = np.atleast_1d(xs)
+            # substitute x = cos(theta): F(x) = int_{arccos x}^{pi} e^{beta cos t} dt / Z
+            return np.array([integrate.quad(lambda t: math.exp(beta * math.cos(t)),
+                                            math.acos(min(1.0, max(-1.0, x))), math.pi)[0]
+                             for x in xs]) / Z
+        return cdf
+    raise ValueError(n)
+
+
+# ------------------------------------------------------------ errors ----
+
+def binned_mean(x, nbins=20):
+    """Mean and its standard error from nbins equal bins (autocorrelation-safe
+    when each bin is much longer than the autocorrelation time)."""
+    x = np.asarray(x, dtype=np.float64)
+    n = (len(x) // nbins) * nbins
+    b = x[:n].reshape(nbins, -1).mean(axis=1)
+    return b.mean(), b.std(ddof=1) / math.sqrt(nbins)

@@ -1,0 +1,345 @@
+"""Pins of the CPU oracle to things other than itself (no GPU).
+
+Each test ties one part of the oracle to a library routine, a closed form, an
+exact enumeration or an invariant of the method (Weigel & Yavors'kii 2011,
+Section 2: Eq. 1, Eq. 2, checkerboard order), chosen so that a dropped term,
+a wrong sign or index, or a swapped colour order fails at least one of them.
+Statistical checks run from fixed seeds, so they are deterministic.
+"""
+import ctypes
+import ctypes.util
+import math
+
+import numpy as np
+import pytest
+from scipy import stats
+
+import oracle
+from paper_1107_5463_gb300 import inputs
+from tests import exact
+
+BETA_C = inputs.BETA_C_2D_ISING
+
+
+# ------------------------------------------------------------- Philox ----
+
+def _curand():
+    for name in ("libcurand.so.10", "libcurand.so", ctypes.util.find_library("curand")):
+        if not name:
+            continue
+        try:
+            return ctypes.CDLL(name)
+        except OSError:
+            continue
+    pytest.skip("cuRAND not available")
+
+
+def _curand_host_philox(lib, seed, first_block, nblocks):
+    """nblocks x 4 outputs of cuRAND's host Philox4_32_10 generator."""
+    gen = ctypes.c_void_p()
+    assert lib.curandCreateGeneratorHost(ctypes.byref(gen), 161) == 0  # PHILOX4_32_10
+    try:
+        assert lib.curandSetPseudoRandomGeneratorSeed(gen, ctypes.c_ulonglong(seed)) == 0
+        assert lib.curandSetGeneratorOffset(gen, ctypes.c_ulonglong(4 * first_block)) == 0
+        buf = (ctypes.c_uint32 * (4 * nblocks))()
+        assert lib.curandGenerate(gen, buf, 4 * nblocks) == 0
+    finally:
+        lib.curandDestroyGenerator(gen)
+    return np.frombuffer(buf, np.uint32).reshape(nblocks, 4).copy()
+
+
+@pytest.mark.parametrize("seed", [0, 1, 0xFFFFFFFF, 1 << 32, inputs.DEFAULT_SEED, 2**64 - 1])
+def test_philox_matches_curand_host_generator(seed):
+    """cuRAND's host Philox4_32_10 generator (a library routine) emits block B
+    as Philox4x32-10 of counter (B >> 16, B >> 48, B & 0xffff, 0) under key
+    (seed_lo, seed_hi); the oracle must reproduce it.  Blocks with non-zero
+    words 0, 1 and 2 are covered, so each counter word and both key words
+    reach the check."""
+    lib = _curand()
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    for first in (0, 65536 * 5 + 7, (3 << 48) + (11 << 16) + 65530):
+        got = _curand_host_philox(lib, seed, first, 12)
+        for b in range(12):
+            B = first + b
+            ctr = [(B >> 16) & 0xFFFFFFFF, B >> 48, B & 0xFFFF, 0]
+            np.testing.assert_array_equal(oracle.philox4x32_10(ctr, key), got[b])
+
+
+def test_philox_is_a_bijection_on_sampled_counters():
+    """Distinct counters give distinct outputs (Philox is a bijection for a
+    fixed key) and one flipped input bit changes about half the output bits."""
+    key = [0x1234, 0x5678]
+    rng = np.random.default_rng(7)
+    ctrs = rng.integers(0, 2**32, size=(2000, 4), dtype=np.uint64).astype(np.uint32)
+    outs = {tuple(oracle.philox4x32_10(c, key)) for c in ctrs}
+    assert len(outs) == len({tuple(c) for c in ctrs})
+    flips = []
+    for c in ctrs[:200]:
+        a = oracle.philox4x32_10(c, key)
+        c2 = c.copy()
+        c2[rng.integers(4)] ^= np.uint32(1 << int(rng.integers(32)))
+        b = oracle.philox4x32_10(c2, key)
+        flips.append(sum(bin(int(x) ^ int(y)).count("1") for x, y in zip(a, b)))
+    assert abs(np.mean(flips) - 64) < 3
+
+
+# ------------------------------------------------------------ energy ----
+
+@pytest.mark.parametrize("d,L", [(2, 2), (2, 6), (3, 2), (3, 4)])
+def test_ising_measure_matches_roll_energy(d, L):
+    s = inputs.ising_spins(d, L, 11)
+    jb = inputs.ising_bonds(d, L, 12, p_zero=0.2)
+    for J, bonds in ((1.0, None), (-0.7, jb)):
+        E, M = oracle.ising_measure(d, L, s, J=J, Jb=bonds)
+        assert E == pytest.approx(exact.roll_energy(s, d, L, J, bonds), abs=1e-12)
+        assert M == s.sum()
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_ising_measure_special_states(d):
+    L = 4
+    N = L ** d
+    up = np.ones(N, np.int8)
+    assert oracle.ising_measure(d, L, up)[0] == -d * N
+    neel = (1 - 2 * exact.colour_of_site(d, L)).astype(np.int8)
+    assert oracle.ising_measure(d, L, neel)[0] == d * N
+    one = up.copy()
+    one[5] = -1
+    assert oracle.ising_measure(d, L, one)[0] == -d * N + 4 * d
+
+
+@pytest.mark.parametrize("d,L", [(2, 4), (3, 2)])
+def test_continuous_measure_matches_roll_energy(d, L):
+    th = inputs.angles(d, L, 3)
+    jbf = inputs.float_bonds(d, L, 4)
+    E, M = oracle.xy_measure(d, L, th, J=0.9, Jb=jbf)
+    v = np.stack([np.cos(th), np.sin(th)], axis=1)
+    assert E == pytest.approx(exact.roll_energy(v, d, L, 0.9, jbf.astype(np.float64)), abs=1e-12)
+    np.testing.assert_allclose(M, v.sum(axis=0), atol=1e-12)
+    s = inputs.unit_vectors(d, L, 5)
+    E, M = oracle.heis_measure(d, L, s, J=1.3, Jb=jbf)
+    assert E == pytest.approx(exact.roll_energy(s, d, L, 1.3, jbf.astype(np.float64)), abs=1e-12)
+    np.testing.assert_allclose(M, s.sum(axis=0), atol=1e-12)
+
+
+# ---------------------------------------------- exact small lattices ----
+
+def test_ising_4x4_equilibrium_matches_enumeration():
+    """<E>, <E^2>, <|m|> of the 4x4 torus at beta_c from all 2^16 states; the
+    oracle's Metropolis chain must agree within 3 sigma (binning errors)."""
+    ex = exact.enumerate_ising(2, 4, BETA_C)
+    s = oracle.ising_init(2, 4, 99)
+    E, m = oracle.ising_sweeps(2, 4, s, BETA_C, 99, 0, 200_000)
+    E, m = E[1000:], m[1000:]
+    for obs, ref in ((E, ex["E"]), (E * E, ex["E2"]), (m, ex["absm"])):
+        mean, err = exact.binned_mean(obs, 40)
+        assert abs(mean - ref) < 3 * err, (mean, ref, err)
+
+
+def _chi2_rows(counts, T, rows):
+    """Pooled chi-square p-value over the given rows; cells with an expected
+    count below 5 are lumped into one cell per row."""
+    chi2, dof = 0.0, 0
+    for a in rows:
+        n = counts[a].sum()
+        expct = n * T[a]
+        assert counts[a][expct == 0].sum() == 0, "transition with zero exact probability"
+        big = expct >= 5
+        obs = list(counts[a][big])
+        exp_ = list(expct[big])
+        if (~big).any() and expct[~big].sum() > 0:
+            obs.append(counts[a][~big].sum())
+            exp_.append(expct[~big].sum())
+        obs, exp_ = np.array(obs), np.array(exp_)
+        chi2 += ((obs - exp_) ** 2 / exp_).sum()
+        dof += len(obs) - 1
+    return stats.chi2.sf(chi2, dof)
+
+
+@pytest.mark.parametrize("d,beta", [(2, 0.15), (3, 0.1)])
+def test_one_sweep_transition_matrix_on_L2(d, beta):
+    """Exact matrix of one sweep (colour 0 then colour 1, each site of a colour
+    flipped independently with min[1, e^{-beta dE}], dE from the full Eq. 1)
+    against the oracle's empirical transitions.  T0 and T1 each satisfy
+    detailed balance and the Boltzmann weights are stationary under T0 T1."""
+    L = 2
+    T0, T1, S, E = exact.exact_sweep_matrix(d, L, beta)
+    pi = np.exp(-beta * E)
+    pi /= pi.sum()
+    for T in (T0, T1):
+        np.testing.assert_allclose(pi[:, None] * T, (pi[:, None] * T).T, atol=1e-14)
+    T = T0 @ T1
+    np.testing.assert_allclose(pi @ T, pi, atol=1e-14)
+    if d == 2:
+        assert np.abs(T0 @ T1 - T1 @ T0).max() > 1e-3  # the colour order is visible
+    index = {tuple(s): k for k, s in enumerate(S)}
+    nst = len(S)
+    rows = range(nst) if d == 2 else range(0, nst, 37)
+    reps = 3000
+    counts = np.zeros((nst, nst))
+    for a in rows:
+        for r in range(reps):
+            s = S[a].copy()
+            oracle.ising_sweeps(d, L, s, beta, 1234, r, 1, series=False)
+            counts[a, index[tuple(s)]] += 1
+    assert _chi2_rows(counts, T, rows) > 1e-4
+
+
+@pytest.mark.slow
+def test_ising_L64_energy_matches_kaufman():
+    """The 2D Ising workload of side 64 at beta_c = ln(1+sqrt2)/2, 4 x 10^4
+    sweeps from a random start: mean energy per site against Kaufman's exact
+    finite-torus value (about -1.4239; Onsager's -sqrt(2) is the L -> infinity
+    limit)."""
+    L = 64
+    ref = exact.kaufman_energy_per_site(BETA_C, L)
+    assert -1.43 < ref < -1.42
+    s = oracle.ising_init(2, L, inputs.DEFAULT_SEED)
+    E, _ = oracle.ising_sweeps(2, L, s, BETA_C, inputs.DEFAULT_SEED, 0, 40_000)
+    mean, err = exact.binned_mean(E[2000:] / L**2, 16)
+    assert abs(mean - ref) < 3 * err, (mean, ref, err)
+    assert err < 5e-3
+
+
+# ---------------------------------------------------- two-spin laws ----
+
+@pytest.mark.parametrize("n,beta", [(1, 0.8), (2, 1.3), (3, 1.7)])
+def test_two_spin_bond_distribution(n, beta):
+    """A 4x4 lattice whose only non-zero coupling joins sites 0 and 1: the bond
+    variable x = s_0 . s_1 = -E must follow p(x) ~ e^{beta x}(1-x^2)^{(n-3)/2}
+    (mean tanh, I1/I0, Langevin) and, for n = 2, 3, its full CDF (KS test)."""
+    d, L = 2, 4
+    jb = inputs.two_spin_bonds(d, L, 0, 0)
+    nsw = 60_000
+    if n == 1:
+        s = oracle.ising_init(d, L, 5)
+        E, _ = oracle.ising_sweeps(d, L, s, beta, 6, 0, nsw, Jb=jb)
+    elif n == 2:
+        th = oracle.xy_init(d, L, 5)
+        E, _, _, _ = oracle.xy_sweeps(d, L, th, beta, 6, 0, nsw, Jb=jb.astype(np.float32))
+    else:
+        s = oracle.heis_init(d, L, 5)
+        E, _, _, _ = oracle.heis_sweeps(d, L, s, beta, 6, 0, nsw, Jb=jb.astype(np.float32))
+    x = -E[100:]
+    mean, err = exact.binned_mean(x, 50)
+    assert abs(mean - exact.two_spin_mean(n, beta)) < 3 * err, (mean, err)
+    if n > 1:
+        sample = x[::10][:2000]
+        assert stats.kstest(sample, exact.two_spin_cdf(n, beta)).pvalue > 1e-3
+
+
+# ------------------------------------------------------ limiting beta ----
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_beta_zero_accepts_every_move(d):
+    """At beta = 0 every proposal is accepted: every Ising spin flips and every
+    continuous spin becomes its proposal, which is the Philox stream itself."""
+    L, seed, t = 4, 77, 5
+    N = L ** d
+    s0 = inputs.ising_spins(d, L, 1)
+    s = s0.copy()
+    oracle.ising_sweeps(d, L, s, 0.0, seed, t, 1, series=False)
+    np.testing.assert_array_equal(s, -s0)
+
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    colour = exact.colour_of_site(d, L)
+    u24 = lambda x: (int(x) >> 8) * 2.0**-24
+    th = inputs.angles(d, L, 2)
+    oracle.xy_sweeps(d, L, th, 0.0, seed, t, 1, series=False)
+    v = inputs.unit_vectors(d, L, 3)
+    oracle.heis_sweeps(d, L, v, 0.0, seed, t, 1, renorm_every=0, series=False)
+    for i in range(N):
+        j, c = i >> 1, int(colour[i])
+        out = oracle.philox4x32_10([j >> 1, t, 0, c], key)
+        assert th[i] == 2 * math.pi * u24(out[2 * (j & 1) + 1])
+        out = oracle.philox4x32_10([j, t, 0, c], key)
+        z = 2 * u24(out[1]) - 1
+        phi = 2 * math.pi * u24(out[2])
+        r = math.sqrt(1 - z * z)
+        np.testing.assert_allclose(v[i], [r * math.cos(phi), r * math.sin(phi), z], atol=1e-15)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_large_beta_never_raises_energy(d):
+    """With beta large, no move with dE > 0 is accepted: the ordered Ising
+    ground state survives and continuous-spin energies never increase."""
+    L = 6
+    up = np.ones(L ** d, np.int8)
+    oracle.ising_sweeps(d, L, up, 40.0, 3, 0, 50, series=False)
+    assert (up == 1).all()
+    th = inputs.angles(d, L, 8)
+    E, _, _, _ = oracle.xy_sweeps(d, L, th, 1e12, 3, 0, 30)
+    assert (np.diff(E) <= 1e-8).all()
+    assert E[-1] < E[0]
+    v = inputs.unit_vectors(d, L, 9)
+    E, _, _, _ = oracle.heis_sweeps(d, L, v, 1e12, 3, 0, 30)
+    assert (np.diff(E) <= 1e-8).all()
+    assert E[-1] < E[0]
+
+
+# ------------------------------------------------------- bookkeeping ----
+
+@pytest.mark.parametrize("d,L", [(2, 6), (2, 8), (3, 4)])
+def test_series_matches_recomputed_state(d, L):
+    """The series after the last sweep equals Eq. 1 recomputed by rolls; the
+    2D energy is 2N mod 4 (unsatisfied bonds come in even numbers on a torus);
+    sweeps a then b equal a + b sweeps (the stream is keyed by sweep index)."""
+    s = oracle.ising_init(d, L, 4)
+    s2 = s.copy()
+    E, m = oracle.ising_sweeps(d, L, s, 0.3, 9, 0, 20)
+    assert E[-1] == exact.roll_energy(s, d, L)
+    assert m[-1] == abs(int(s.astype(np.int64).sum())) / L**d
+    if d == 2:
+        assert all(int(e) % 4 == (2 * L * L) % 4 for e in E)
+    oracle.ising_sweeps(d, L, s2, 0.3, 9, 0, 7, series=False)
+    oracle.ising_sweeps(d, L, s2, 0.3, 9, 7, 13, series=False)
+    np.testing.assert_array_equal(s, s2)
+
+
+def test_heisenberg_renormalisation_keeps_unit_length():
+    d, L = 3, 4
+    v = inputs.unit_vectors(d, L, 1) * 1.5
+    oracle.heis_sweeps(d, L, v, 0.7, 2, 15, 1, renorm_every=16, series=False)
+    np.testing.assert_allclose(np.linalg.norm(v, axis=1), 1.0, atol=1e-14)
+
+
+# ---------------------------------------------------------- EA + PT ----
+
+def test_ea_couplings_are_balanced_pm1():
+    jb = oracle.ea_couplings(3, 16, 5, 0)
+    assert set(np.unique(jb)) == {-1, 1}
+    p = (jb == 1).mean()
+    assert abs(p - 0.5) < 3 * math.sqrt(0.25 / jb.size)
+    assert not np.array_equal(jb, oracle.ea_couplings(3, 16, 5, 1))
+
+
+def test_exchange_with_equal_betas_always_swaps():
+    """Delta = 0 when all temperatures are equal, so every attempted pair
+    swaps: the labels follow the fixed even/odd transposition pattern."""
+    d, L, nt = 3, 2, 5
+    jb = oracle.ea_couplings(d, L, 1, 0)
+    spins = np.stack([oracle.ising_init(d, L, 1, r) for r in range(nt)])
+    perm = np.arange(nt, dtype=np.int32)
+    expect = list(range(nt))
+    for t in range(6):
+        oracle.ea_pt_sweeps(d, L, jb, [0.4] * nt, 2, 0, t, 1, spins, perm)
+        for k in range(t % 2, nt - 1, 2):
+            expect[k], expect[k + 1] = expect[k + 1], expect[k]
+        assert list(perm) == expect
+
+
+def test_exchange_keeps_canonical_energies_on_L2_sample():
+    """Replica exchange must leave each temperature canonical: the mean energy
+    at every beta of a 3D L = 2 EA sample (256 states, enumerated exactly)
+    agrees with the exact value within 3 sigma."""
+    d, L = 3, 2
+    jb = oracle.ea_couplings(d, L, 21, 3)
+    betas = np.array([0.2, 0.45, 0.8, 1.4])
+    spins = np.stack([oracle.ising_init(d, L, 21, 3 * 4 + r) for r in range(4)])
+    perm = np.arange(4, dtype=np.int32)
+    E = oracle.ea_pt_sweeps(d, L, jb, betas, 22, 3, 0, 200_000, spins, perm)
+    assert sorted(perm) == [0, 1, 2, 3]
+    for k, b in enumerate(betas):
+        ex = exact.enumerate_ising(d, L, b, Jb=jb.astype(np.int64))
+        mean, err = exact.binned_mean(E[1000:, k], 40)
+        assert abs(mean - ex["E"]) < 3 * err, (k, mean, ex["E"], err)
