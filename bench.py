@@ -1,0 +1,347 @@
+#!/usr/bin/env python
+"""Throughput of the checkerboard Metropolis sweep (Weigel & Yavors'kii 2011,
+Section 2, Table 1) on one GB300, in spin flips per nanosecond.
+
+One step = one full sweep (colour 0, colour 1, fused energy and |m|) of the
+workload lattice, inputs resident in HBM.  The headline workload is the 2D
+Ising ferromagnet of side 16384 (2.7e8 int8 spins, larger than L2) at
+beta_c = 0.440687 from a random start.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank runs its own independent replica (weak scaling);
+rank 0 prints one JSON line.  ``--impl reference`` times the CPU oracle (the
+plain C restatement of the method) on the host cores instead.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "spin flips/ns"
+UNIT = "flips/ns"
+
+WORKLOADS = {
+    "ising2d_L16384_i8": dict(d=2, L=16384, n=1, beta=0.440687, storage="i8",
+                              desc="2D Ising ferromagnet J=1, L=16384 periodic, int8 spins, "
+                                   "beta_c=0.440687, random start"),
+    "ising3d_L512_i8": dict(d=3, L=512, n=1, beta=0.2216546, storage="i8",
+                            desc="3D Ising ferromagnet J=1, L=512 simple cubic, int8 spins, "
+                                 "beta=0.2216546, random start"),
+}
+HEADLINE = "ising2d_L16384_i8"
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            j = json.load(f)
+        return j.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1107_5463_gb300", "csrc"))):
+        with open(os.path.join(ROOT, "paper_1107_5463_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload):
+    """DRAM bytes per launch of the dominant kernel from a committed ncu
+    summary, only if the kernel sources are unchanged since it was taken."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        j = json.load(f)
+    e = j.get(workload)
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.2)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 8:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = sorted(float(r[0]) for r in rows if r[0].replace(".", "").isdigit())
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, name in enumerate(names):
+                if r[4 + k].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None,
+                "sm_max_mhz": float(rows[0][1]) if rows[0][1].replace(".", "").isdigit() else None,
+                "samples": len(rows), "reasons": sorted(reasons)}
+
+
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(local)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64,
+                     device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def time_sweeps(spinmc, wl, steps, warmup, replica, want_clocks, local):
+    """Device-timed K sweeps of one lattice; returns (ms, clocks)."""
+    import torch
+    from paper_1107_5463_gb300 import inputs
+    lat = spinmc.Lattice(wl["d"], wl["L"], n=wl["n"], seed=inputs.DEFAULT_SEED, replica=replica)
+    E = torch.empty(max(steps, warmup, 1), dtype=torch.float64, device="cuda")
+    m = torch.empty_like(E)
+    spinmc.sl_sweep_series(lat.h, wl["beta"], warmup, inputs.DEFAULT_SEED, E, m)
+    torch.cuda.synchronize()
+    clocks = Clocks(local) if want_clocks else None
+    if clocks:
+        clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(lat.stream)
+    spinmc.sl_sweep_series(lat.h, wl["beta"], steps, inputs.DEFAULT_SEED, E, m)
+    ev1.record(lat.stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    cl = clocks.stop() if clocks else None
+    e_last = float(E[steps - 1].item())
+    lat.close()
+    return ms, cl, e_last
+
+
+def e2e_run(spinmc, wl, jobs, sweeps_per_job, replica):
+    """End to end through the public API with host buffers: per job, upload
+    the start configuration from pinned host memory, run the sweeps, read the
+    E and |m| series back to pinned host memory."""
+    import numpy as np
+    import torch
+    from paper_1107_5463_gb300 import inputs
+    d, L = wl["d"], wl["L"]
+    N = L ** d
+    host = torch.empty(N, dtype=torch.int8, pin_memory=True)
+    host.numpy()[:] = inputs.ising_spins(d, L, inputs.DEFAULT_SEED + replica)
+    out = torch.empty(2 * sweeps_per_job, dtype=torch.float64, pin_memory=True)
+    lat = spinmc.Lattice(d, L, n=1, seed=inputs.DEFAULT_SEED, replica=replica)
+    E = torch.empty(sweeps_per_job, dtype=torch.float64, device="cuda")
+    m = torch.empty_like(E)
+    # warm: one job
+    spinmc.sl_set_spins(lat.h, host.data_ptr())
+    spinmc.sl_sweep_series(lat.h, wl["beta"], sweeps_per_job, 99, E, m)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(jobs):
+        spinmc.sl_set_spins(lat.h, host.data_ptr())
+        spinmc.sl_sweep_series(lat.h, wl["beta"], sweeps_per_job, 99, E, m)
+        with torch.cuda.stream(lat.stream):
+            out[:sweeps_per_job].copy_(E, non_blocking=True)
+            out[sweeps_per_job:].copy_(m, non_blocking=True)
+        lat.stream.synchronize()
+    dt = time.perf_counter() - t0
+    lat.close()
+    flips = N * sweeps_per_job * jobs
+    return dict(value=flips / (dt * 1e9), unit=UNIT, h2d_bytes_per_step=N,
+                d2h_bytes_per_step=2 * 8 * sweeps_per_job, sweeps_per_step=sweeps_per_job,
+                steps=jobs)
+
+
+def cpu_baseline(wl, target_s=15.0):
+    """The oracle (plain C, single thread) on a bounded sample: whole sweeps
+    of the full workload lattice, with the per-sweep measurement."""
+    import oracle
+    from paper_1107_5463_gb300 import inputs
+    d, L = wl["d"], wl["L"]
+    N = L ** d
+    s = oracle.ising_init(d, L, inputs.DEFAULT_SEED)
+    t0 = time.perf_counter()
+    nsw = 0
+    while True:
+        oracle.ising_sweeps(d, L, s, wl["beta"], inputs.DEFAULT_SEED, nsw, 1)
+        nsw += 1
+        if time.perf_counter() - t0 > target_s or nsw >= 50:
+            break
+    dt = time.perf_counter() - t0
+    return dict(value=N * nsw / (dt * 1e9), unit=UNIT, cores=1, kind="oracle",
+                sample="%d full sweep(s) of the %d^%d lattice incl. per-sweep E/|m|, "
+                       "single-threaded C oracle, %.1f s" % (nsw, L, d, dt))
+
+
+def reference_arm(args, world, rank):
+    """--impl reference: the CPU oracle as it stands, each step one sweep of a
+    2D L=1024 sample of the headline workload, on the host cores."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_1107_5463_gb300 import inputs
+    wl = WORKLOADS[HEADLINE]
+    L = 1024
+    s = oracle.ising_init(2, L, inputs.DEFAULT_SEED)
+    for k in range(args.warmup):
+        oracle.ising_sweeps(2, L, s, wl["beta"], 7, k, 1)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        oracle.ising_sweeps(2, L, s, wl["beta"], 7, args.warmup + k, 1)
+    dt = time.perf_counter() - t0
+    v = L * L * args.steps / (dt * 1e9)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int8", "data": "synthetic",
+            "config": {"workload": HEADLINE, "sample": "one sweep of a 2D L=1024 lattice per step",
+                       "parallelism": "host, 1 thread"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "2D Ising L=1024 at beta_c, one sweep incl. E/|m| per step"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=HEADLINE, choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--e2e-jobs", type=int, default=3)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        reference_arm(args, world, rank)
+        return
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import torch
+    from paper_1107_5463_gb300 import spinmc
+
+    wl = WORKLOADS[args.workload]
+    d, L = wl["d"], wl["L"]
+    N = L ** d
+    barrier(world)
+    ms, clocks, e_last = time_sweeps(spinmc, wl, args.steps, args.warmup, rank, rank == 0, local)
+    ms = max_over_ranks(ms, world)
+    value = N * args.steps * world / (ms * 1e6)
+
+    hbm, peak_kind = peaks()
+    launches_per_step = 2
+    launch_ms = ms / (args.steps * launches_per_step)
+    bytes_per_launch = 3 * (N // 2)          # read own + other colour, write own (int8)
+    achieved_gbs = bytes_per_launch / (launch_ms * 1e-3) / 1e9
+    traffic = recorded_traffic(args.workload)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int8", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": wl["desc"], "d": d, "L": L,
+                   "sites": N, "beta": wl["beta"], "step": "one full sweep + fused E,|m|",
+                   "l2": "inputs larger than L2 (%d MB of spins)" % (N // 2**20),
+                   "parallelism": "replica per GPU" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved_gbs / hbm, "peak_kind": peak_kind,
+                     "traffic": traffic, "kernel": "i8_stream<%d,0>" % d,
+                     "bytes_per_launch": bytes_per_launch, "launch_ms": launch_ms},
+        "gpu_launches": args.steps * launches_per_step + 1,
+        "clocks": clocks,
+        "check": {"E_per_site_last": e_last / N},
+    }
+    if rank == 0:
+        line["e2e"] = e2e_run(spinmc, wl, args.e2e_jobs, 1000, rank)
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(wl)
+        if not args.no_variants:
+            var = {}
+            for name, w in WORKLOADS.items():
+                if name == args.workload:
+                    continue
+                k = 300
+                vms, _, _ = time_sweeps(spinmc, w, k, 5, rank, False, local)
+                n = w["L"] ** w["d"]
+                var[name] = {"value": n * k / (vms * 1e6), "unit": UNIT, "ms_per_step": vms / k,
+                             "hbm_frac": 3 * (n // 2) / (vms / (2 * k) * 1e-3) / 1e9 / hbm}
+            line["variants"] = var
+        print(json.dumps(line), flush=True)
+    barrier(world)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,169 @@
+/*
+ * spinmc — checkerboard single-spin-flip Metropolis for classical O(n) lattice
+ * spin models on one GB300 (sm_103a).  C ABI.
+ *
+ * Method: Weigel & Yavors'kii, "GPU accelerated Monte Carlo simulations of
+ * lattice spin models", Physics Procedia 15 (2011), Section 2:
+ *   Eq. (1)  H = - sum_<ij> J_ij s_i . s_j, nearest neighbours on a periodic
+ *            square (d = 2) or simple-cubic (d = 3) lattice, n = 1 (Ising),
+ *            2 (XY) or 3 (Heisenberg);
+ *   Eq. (2)  a single-spin move s_i -> s_i' is accepted with probability
+ *            min[1, exp(-beta dE)];
+ *   the lattice is split into two checkerboard colours; all sites of one
+ *   colour are updated in parallel, then all sites of the other (one sweep).
+ * The Edwards-Anderson +-J spin glass (Section 2, last paragraph) runs as a
+ * batch of disorder samples with replica exchange between temperatures.
+ *
+ * Conventions shared by every call:
+ *   - L must be even (the checkerboard must close under the periodic wrap);
+ *     N = L^d sites; natural index i = x + L*y (+ L*L*z); colour
+ *     c = (x+y(+z)) & 1; colour index j = i >> 1.
+ *   - Random numbers are Philox4x32-10 (Salmon et al., SC'11) keyed by the
+ *     64-bit seed (key = (seed_lo, seed_hi)) with counter
+ *     (group, sweep index t, replica, purpose << 1 | colour), purpose 0 for a
+ *     sweep, 1 for the initial state, 2 for couplings, 3 for replica
+ *     exchange; group = j >> 2 (Ising, site uses output j & 3), j >> 1 (XY,
+ *     outputs 2(j&1) accept and 2(j&1)+1 proposal), j (Heisenberg, outputs 0
+ *     accept, 1 and 2 proposal).  A run is therefore a pure function of
+ *     (seed, sweep indices, start state).
+ *   - Ising moves with dE > 0 are accepted iff u < exp(-beta dE) * 2^32 for
+ *     the site's raw 32-bit output u (exact integer thresholds built on the
+ *     host in FP64); dE <= 0 is always accepted.  Continuous spins propose a
+ *     fresh uniform angle (XY) or direction (Heisenberg), compute dE and the
+ *     acceptance in FP32 against u24 = (u >> 8) 2^-24, and accumulate the
+ *     observables in FP64.
+ *   - Every call returns SL_OK or a negative status and never throws.  Calls
+ *     that take a stream pointer enqueue work on it and return before the
+ *     GPU finishes, except where a call says it synchronises.
+ *   - Ownership: device memory is owned by the caller.  sl_create takes a
+ *     caller-allocated device buffer of sl_required_bytes bytes, 256-byte
+ *     aligned, which must outlive the handle; passing NULL makes the library
+ *     allocate (and free in sl_destroy) its own.  Host pointers passed in are
+ *     only read during the call.
+ */
+#ifndef SPINMC_H
+#define SPINMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define SL_OK 0
+#define SL_EINVAL (-1)    /* invalid argument (message in sl_last_error) */
+#define SL_ENOMEM (-2)    /* buffer too small or allocation failed */
+#define SL_ECUDA (-3)     /* a CUDA runtime call failed */
+#define SL_ETIMEOUT (-4)  /* a bounded device-side wait gave up */
+#define SL_EDEVICE (-5)   /* a kernel raised the sticky device error word */
+
+/* coupling layouts */
+#define SL_J_UNIFORM 0    /* every bond has J_ij = J */
+#define SL_J_BONDS 1      /* J_ij = J * Jb[mu][i] per forward bond (i, i+e_mu) */
+
+/* spin storage */
+#define SL_STORE_I8 0         /* Ising, one int8 (+1 / -1) per site */
+#define SL_STORE_BITS 1       /* Ising, one bit per site (1 = spin down) */
+#define SL_STORE_F32_ANGLE 2  /* XY, FP32 angle in [0, 2 pi) */
+#define SL_STORE_F32_VEC 3    /* Heisenberg, FP32 unit vector (3 components) */
+
+/* options for sl_set_option */
+#define SL_OPT_RENORM_EVERY 1  /* Heisenberg: renormalise every k sweeps (default 16, 0 = never) */
+#define SL_OPT_FAST_MATH 2     /* continuous spins: 1 = hardware sin/cos/exp intrinsics */
+#define SL_OPT_KERNEL 3        /* 0 = automatic, 1 = generic per-site kernel, 2 = row-streaming kernel */
+#define SL_OPT_ROWS 4          /* rows each thread marches through in the streaming kernel */
+#define SL_OPT_GRAPH 5         /* 1 = replay sweeps through CUDA graphs (default), 0 = plain launches */
+
+typedef struct sl_lattice sl_lattice;
+
+/*
+ * sl_required_bytes — device bytes sl_create needs for this lattice.
+ * d in {2,3}; L even, >= 2; n = 1 with storage SL_STORE_I8 or SL_STORE_BITS
+ * (bits need L % 64 == 0), n = 2 with SL_STORE_F32_ANGLE, n = 3 with
+ * SL_STORE_F32_VEC.  Returns SL_EINVAL for other combinations.
+ */
+int sl_required_bytes(int d, int L, int n, int j_layout, int storage, size_t* bytes);
+
+/*
+ * sl_create — build a lattice (Eq. 1) on the caller's stream and draw its
+ * start configuration from Philox purpose 1 keyed by `seed`: Ising s = +1 iff
+ * the top bit of the site's output is set; XY theta = 2 pi u24 (output
+ * 2(j&1)+1); Heisenberg z = 2 u24(out 1) - 1, phi = 2 pi u24(out 2).
+ *   J         the scalar coupling.
+ *   J_bonds   SL_J_BONDS only: natural-order forward-bond couplings [d][N],
+ *             int8 in {-1, 0, +1} for n = 1, float for n > 1; host or device
+ *             pointer; J_ij = J * J_bonds.  Ignored for SL_J_UNIFORM.
+ *   replica   the counter word 2 used for this lattice's random streams.
+ *   dev_buf   device buffer of dev_buf_bytes >= sl_required_bytes bytes,
+ *             256-byte aligned, owned by the caller; NULL = library-owned.
+ *   stream    cudaStream_t (NULL = legacy default stream).
+ * On success *out receives the handle.
+ */
+int sl_create(int d, int L, int n, int j_layout, int storage, double J, const void* J_bonds,
+              uint64_t seed, uint32_t replica, void* dev_buf, size_t dev_buf_bytes,
+              void* stream, sl_lattice** out);
+
+/*
+ * sl_sweep — nsweeps checkerboard Metropolis sweeps (Section 2, Eq. 2) at
+ * inverse temperature beta >= 0, random stream keyed by `seed`, sweep indices
+ * continuing from the handle's sweeps_done (so sweep(a) then sweep(b) equals
+ * sweep(a+b)).  Asynchronous on the handle's stream.  SL_EINVAL if beta is
+ * negative or so large that exp(-beta dE) underflows to zero.
+ */
+int sl_sweep(sl_lattice* lat, double beta, int64_t nsweeps, uint64_t seed);
+
+/*
+ * sl_sweep_series — as sl_sweep, and after sweep k writes the energy (Eq. 1)
+ * to dev_E[k] and |m| = |M|/N to dev_absm[k] (device pointers to nsweeps
+ * doubles; either may be NULL).  Ising values are exact (integer sums);
+ * continuous-spin values are FP64 sums of FP32 per-thread partials.
+ */
+int sl_sweep_series(sl_lattice* lat, double beta, int64_t nsweeps, uint64_t seed,
+                    double* dev_E, double* dev_absm);
+
+/*
+ * sl_measure — energy (Eq. 1) and magnetisation of the current state.
+ * magnetisation receives n components of M = sum_i s_i followed by |M|/N
+ * (n + 1 doubles).  Synchronises the handle's stream; returns SL_EDEVICE if
+ * a kernel has raised the device error word since the last check.
+ */
+int sl_measure(sl_lattice* lat, double* energy, double* magnetisation);
+
+/*
+ * sl_get_spins / sl_set_spins — copy the configuration out of / into the
+ * lattice in natural order: int8 +-1 per site (n = 1), float angle (n = 2),
+ * float[3] per site (n = 3).  dst / src may be host or device memory.  Both
+ * synchronise the handle's stream.
+ */
+int sl_get_spins(sl_lattice* lat, void* dst);
+int sl_set_spins(sl_lattice* lat, const void* src);
+
+/*
+ * sl_get_state / sl_set_state — checkpoint support: the start seed and the
+ * number of sweeps done (the next sweep index).  With the spins saved by
+ * sl_get_spins, restoring both resumes the run exactly.
+ */
+int sl_get_state(sl_lattice* lat, uint64_t* init_seed, int64_t* sweeps_done);
+int sl_set_state(sl_lattice* lat, int64_t sweeps_done);
+
+/* sl_set_option — set one SL_OPT_* value; SL_EINVAL for unknown options or
+ * values out of range. */
+int sl_set_option(sl_lattice* lat, int option, int64_t value);
+
+/* sl_destroy — release host metadata (and the buffer if library-owned).
+ * Synchronises the handle's stream first. */
+void sl_destroy(sl_lattice* lat);
+
+/* sl_strerror — static text for a status code. */
+const char* sl_strerror(int status);
+
+/* sl_last_error — copy the calling thread's last error message (or "") into
+ * msg (cap bytes, NUL-terminated); returns its full length. */
+int sl_last_error(char* msg, size_t cap);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPINMC_H */

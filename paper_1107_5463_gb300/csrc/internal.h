@@ -1,0 +1,82 @@
+// Host-side internals of libspinmc shared between translation units: the
+// lattice handle, the layout of the caller's device buffer, and the kernel
+// launchers each model's .cu file provides.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/spinmc.h"
+#include "common.cuh"
+
+namespace spinmc {
+
+constexpr int kMaxBlocks = 4096;     // upper bound on any measuring grid
+constexpr size_t kAlign = 256;
+
+inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// Acceptance thresholds for the Ising classes (see ising_thresholds()).
+struct IsingTable {
+    uint32_t thr[6];
+    int ncmp;      // number of classes with dE > 0 (d, or 2d when bonds may be zero)
+    int scheme;    // 0: class = unsatisfied bonds (couplings +-1); 1: class = 2d - e
+    int sigma_neg; // the scalar J is negative
+};
+
+// Per-sweep parameters common to every model.
+struct SweepParams {
+    double beta;
+    uint64_t seed;
+    RoundKeys rk;
+    IsingTable tab;   // Ising only
+    float beta_f;     // continuous spins
+};
+
+}  // namespace spinmc
+
+struct sl_lattice {
+    int d, L, n, j_layout, storage;
+    int64_t N, H;            // sites, sites per colour
+    int W;                   // sites of one colour in one row (L / 2)
+    double J;
+    uint64_t init_seed;
+    uint32_t replica;
+    int64_t sweeps_done;
+    cudaStream_t stream;     // the caller's stream
+    cudaStream_t cap_stream; // private stream used only to capture graphs
+    // views into the device buffer
+    void* spins[2];          // per colour
+    void* bonds[2][3];       // per colour, per direction (null for uniform J)
+    void* staging;           // natural-order staging area
+    size_t staging_bytes;
+    spinmc::Ctrl* ctrl;
+    spinmc::Partial* partials;
+    bool bonds_have_zero;
+    // options
+    int renorm_every, fast_math, kernel, rows, use_graph;
+    // cached graph of kGraphSweeps sweeps
+    cudaGraphExec_t graph;
+    int graph_sweeps;
+    uint64_t graph_key[4];
+    void* owned_buf;
+};
+
+namespace spinmc {
+
+// error reporting (thread-local message, see sl_last_error)
+int fail(int status, const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what);
+
+// ---- Ising int8 (ising_i8.cu) ----
+cudaError_t ising_i8_init(const sl_lattice* h, cudaStream_t s);
+cudaError_t ising_i8_scatter(const sl_lattice* h, const int8_t* nat, cudaStream_t s);
+cudaError_t ising_i8_gather(const sl_lattice* h, int8_t* nat, cudaStream_t s);
+cudaError_t ising_bonds_scatter(const sl_lattice* h, const int8_t* nat, unsigned* flags,
+                                cudaStream_t s);
+cudaError_t ising_i8_sweeps(const sl_lattice* h, const SweepParams& p, int64_t count,
+                            cudaStream_t s);
+cudaError_t ising_i8_measure(const sl_lattice* h, cudaStream_t s);
+
+}  // namespace spinmc

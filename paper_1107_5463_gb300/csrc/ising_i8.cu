@@ -1,0 +1,515 @@
+// Ising model (n = 1) with one int8 (+1 / -1) per site, checkerboard
+// Metropolis (Weigel & Yavors'kii 2011, Section 2, Eq. 1 and Eq. 2).
+//
+// Storage: two colour arrays S[c][j], j = i >> 1, each N/2 bytes.  A row of
+// the lattice (fixed y, z) holds W = L/2 sites of each colour, contiguous in
+// S[c]; the colour-c site at colour column k of row (y, z) sits at
+// x = 2k + p with p = (y + z + c) & 1, so its -x / +x neighbours are the
+// other colour's columns k-1 / k (p = 0) or k / k+1 (p = 1).
+//
+// Acceptance: class g of a site (number of unsatisfied bonds for +-1
+// couplings, 2d - s_i h_i sign(J) when couplings may be zero) and the count
+// q(u) of classes whose threshold lies below the site's 32-bit uniform u;
+// the move is accepted iff g >= q(u), which equals u <= T[g] for g < ncmp and
+// "always" for the classes with dE <= 0 (thresholds are non-decreasing in g).
+//
+// Two kernels compute the same decisions bit for bit:
+//   i8_generic  one thread per Philox group of 4 sites, scalar, any even L and
+//               any couplings; also the standalone measurement;
+//   i8_stream   one thread per 16-byte column chunk marching through R rows
+//               with a rolling window of the other colour's rows in registers,
+//               128-bit loads and stores, SIMD-within-a-word neighbour
+//               counts; needs W % 16 == 0 and +-1 couplings.
+#include "internal.h"
+
+namespace spinmc {
+namespace {
+
+struct I8Args {
+    int8_t* own;
+    const int8_t* oth;
+    const int8_t* Jown[3];
+    const int8_t* Joth[3];
+    int d, L, W, c, R;
+    long long H, N;
+    uint32_t replica;
+    IsingTable tab;
+    RoundKeys rk;
+    Ctrl* ctrl;
+    Partial* partials;
+    double J;
+    int measure;  // accumulate E and M and finish the pass
+    int update;   // 0: standalone measurement (no moves, no sweep advance)
+};
+
+__device__ __forceinline__ void i8_finish(const I8Args& a, const Partial& tot)
+{
+    Ctrl* C = a.ctrl;
+    const double E = -a.J * (double)tot.i0;
+    const double M = (double)(a.N - 2 * tot.i1);
+    C->obs[0] = E;
+    C->obs[1] = M;
+    C->obs[2] = 0.0;
+    C->obs[3] = 0.0;
+    if (a.update) {
+        const long long k = (long long)C->t - C->series_base;
+        if (C->series_E) C->series_E[k] = E;
+        if (C->series_absm) C->series_absm[k] = fabs(M) / (double)a.N;
+        C->t = C->t + 1;
+    }
+}
+
+__device__ __forceinline__ int q_of(uint32_t u, const IsingTable& tab)
+{
+    int q = 0;
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+        if (k < tab.ncmp) q += (u > tab.thr[k]) ? 1 : 0;
+    return q;
+}
+
+// ----------------------------------------------------------- generic ----
+
+template <int D>
+__global__ void __launch_bounds__(256) i8_generic(const I8Args a)
+{
+    __shared__ long long red[32];
+    const uint32_t t = (uint32_t)a.ctrl->t;
+    const long long ngroups = (a.H + 3) >> 2;
+    const int L = a.L;
+    long long bond = 0, down = 0;
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < ngroups;
+         g += (long long)gridDim.x * blockDim.x) {
+        uint32_t rr[4] = {0u, 0u, 0u, 0u};
+        if (a.update) {
+            const uint4 r = philox4x32_10(
+                make_uint4((uint32_t)g, t, a.replica, (kSweep << 1) | (uint32_t)a.c), a.rk);
+            rr[0] = r.x; rr[1] = r.y; rr[2] = r.z; rr[3] = r.w;
+        }
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const long long j = 4 * g + b;
+            if (j >= a.H) break;
+            const long long i0 = 2 * j;
+            int x = (int)(i0 % L);
+            const long long rrow = i0 / L;
+            const int y = (int)(rrow % L);
+            const int z = (int)(rrow / L);
+            x += (a.c + y + z) & 1;
+            int hs = 0;
+#pragma unroll
+            for (int mu = 0; mu < D; ++mu) {
+                int cm[3] = {x, y, z}, cp[3] = {x, y, z};
+                cm[mu] = cm[mu] == 0 ? L - 1 : cm[mu] - 1;
+                cp[mu] = cp[mu] == L - 1 ? 0 : cp[mu] + 1;
+                const long long nm =
+                    (cm[0] + (long long)L * (cm[1] + (long long)L * cm[2])) >> 1;
+                const long long np =
+                    (cp[0] + (long long)L * (cp[1] + (long long)L * cp[2])) >> 1;
+                const int jm = a.Jown[0] ? (int)a.Joth[mu][nm] : 1;
+                const int jp = a.Jown[0] ? (int)a.Jown[mu][j] : 1;
+                hs += jm * (int)a.oth[nm] + jp * (int)a.oth[np];
+            }
+            int s = a.own[j];
+            int sh = s * hs;
+            if (a.update) {
+                const int e = a.tab.sigma_neg ? -sh : sh;
+                const int gcls = a.tab.scheme ? (2 * D - e) : ((2 * D - e) >> 1);
+                if (gcls >= q_of(rr[b], a.tab)) {
+                    s = -s;
+                    sh = -sh;
+                    a.own[j] = (int8_t)s;
+                }
+            }
+            if (a.measure) {
+                bond += sh;
+                down += (s < 0) + (a.oth[j] < 0);
+            }
+        }
+    }
+    if (!a.measure) return;
+    Partial mine;
+    mine.i0 = block_sum(bond, red);
+    mine.i1 = block_sum(down, red);
+    mine.f[0] = mine.f[1] = mine.f[2] = mine.f[3] = 0.0;
+    finish_pass(a.ctrl, a.partials, mine, [&](const Partial& tot) { i8_finish(a, tot); });
+}
+
+// ---------------------------------------------------------- streaming ----
+
+__device__ __forceinline__ uint4 ld_rows(const int8_t* p)
+{
+    return __ldg(reinterpret_cast<const uint4*>(p));
+}
+
+// The other colour's row shifted by one column so that byte b holds the
+// -x (p = 0) or +x (p = 1) neighbour of own byte b; `edge` is the byte that
+// enters from the adjacent chunk.
+__device__ __forceinline__ uint4 shift_row(uint4 v, uint32_t edge, int p)
+{
+    uint4 s;
+    if (p == 0) {
+        s.x = __funnelshift_l(edge << 24, v.x, 8);
+        s.y = __funnelshift_l(v.x, v.y, 8);
+        s.z = __funnelshift_l(v.y, v.z, 8);
+        s.w = __funnelshift_l(v.z, v.w, 8);
+    } else {
+        s.x = __funnelshift_r(v.x, v.y, 8);
+        s.y = __funnelshift_r(v.y, v.z, 8);
+        s.z = __funnelshift_r(v.z, v.w, 8);
+        s.w = __funnelshift_r(v.w, edge, 8);
+    }
+    return s;
+}
+
+__device__ __forceinline__ uint32_t w_of(const uint4& v, int k)
+{
+    return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w;
+}
+
+// 0x02 in each byte whose three +-1 factors multiply to -1
+__device__ __forceinline__ uint32_t unsat2(uint32_t a, uint32_t n, uint32_t j)
+{
+    return (a ^ n ^ j) & 0x02020202u;
+}
+
+template <int D, int BONDS>
+__global__ void __launch_bounds__(128) i8_stream(const I8Args a)
+{
+    __shared__ long long red[32];
+    const uint32_t t = (uint32_t)a.ctrl->t;
+    const int W = a.W, L = a.L, R = a.R;
+    const int W16 = W >> 4;
+    const long long nseg = L / R;
+    const long long nitems = (long long)W16 * (D == 3 ? L : 1) * nseg;
+    const uint32_t ctr_w = (kSweep << 1) | (uint32_t)a.c;
+    const uint32_t two_d = 0x01010101u * (uint32_t)(2 * D);
+    unsigned long long sum_na = 0, down = 0, nsite = 0;
+
+    for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < nitems;
+         it += (long long)gridDim.x * blockDim.x) {
+        const int cx = (int)(it % W16);
+        const long long rest = it / W16;
+        const int y3 = D == 3 ? (int)(rest % L) : 0;
+        const int seg = D == 3 ? (int)(rest / L) : (int)rest;
+        const int k0 = cx << 4;
+        const int m0 = seg * R;
+        // offset of row (yy, zz)
+        auto off = [&](int yy, int zz) -> long long {
+            return ((long long)zz * L + yy) * W;
+        };
+        // rows along the marching axis m: 2D m = y, 3D m = z (y fixed = y3)
+        auto moff = [&](int m) -> long long {
+            return D == 3 ? off(y3, m) : off(m, 0);
+        };
+        const int mprev = m0 == 0 ? L - 1 : m0 - 1;
+        uint4 prev = ld_rows(a.oth + moff(mprev) + k0);
+        uint4 cur = ld_rows(a.oth + moff(m0) + k0);
+        uint4 jprev = make_uint4(0, 0, 0, 0);
+        if (BONDS) {
+            const int mu = D == 3 ? 2 : 1;  // bonds along the marching axis
+            jprev = ld_rows(a.Joth[mu] + moff(mprev) + k0);
+        }
+        for (int r = 0; r < R; ++r) {
+            const int m = m0 + r;
+            const int mnext = m == L - 1 ? 0 : m + 1;
+            const uint4 next = ld_rows(a.oth + moff(mnext) + k0);
+            const int yy = D == 3 ? y3 : m;
+            const int zz = D == 3 ? m : 0;
+            const int p = (yy + zz + a.c) & 1;
+            const long long ro = off(yy, zz);
+            const int eidx = p ? (k0 + 16 == W ? 0 : k0 + 16) : (k0 == 0 ? W - 1 : k0 - 1);
+            const uint32_t edge = (uint8_t)a.oth[ro + eidx];
+            const uint4 A = *reinterpret_cast<const uint4*>(a.own + ro + k0);
+            const uint4 S = shift_row(cur, edge, p);
+            uint4 ym = make_uint4(0, 0, 0, 0), yp = ym;
+            if (D == 3) {
+                const int ym_ = yy == 0 ? L - 1 : yy - 1;
+                const int yp_ = yy == L - 1 ? 0 : yy + 1;
+                ym = ld_rows(a.oth + off(ym_, zz) + k0);
+                yp = ld_rows(a.oth + off(yp_, zz) + k0);
+            }
+            // couplings: +x/+y/+z from own forward bonds; -x from the other
+            // colour's x bonds (shifted when the -x neighbour is column k-1);
+            // -y / -z from the other colour's rows behind.
+            uint4 jx_own, jx_oth, jy_own, jy_oth, jz_own, jz_oth;
+            uint4 jnext = make_uint4(0, 0, 0, 0);
+            if (BONDS) {
+                jx_own = ld_rows(a.Jown[0] + ro + k0);
+                const uint4 jo = ld_rows(a.Joth[0] + ro + k0);
+                if (p == 0) {
+                    const uint32_t jedge = (uint8_t)a.Joth[0][ro + eidx];
+                    jx_oth = shift_row(jo, jedge, 0);
+                } else {
+                    jx_oth = jo;
+                }
+                if (D == 2) {
+                    jy_own = ld_rows(a.Jown[1] + ro + k0);
+                    jy_oth = jprev;  // Joth[1] at row m - 1
+                    jnext = ld_rows(a.Joth[1] + ro + k0);
+                } else {
+                    const int ym_ = yy == 0 ? L - 1 : yy - 1;
+                    jy_own = ld_rows(a.Jown[1] + ro + k0);
+                    jy_oth = ld_rows(a.Joth[1] + off(ym_, zz) + k0);
+                    jz_own = ld_rows(a.Jown[2] + ro + k0);
+                    jz_oth = jprev;  // Joth[2] at plane m - 1
+                    jnext = ld_rows(a.Joth[2] + ro + k0);
+                }
+            }
+            const uint32_t g0 = (uint32_t)((ro + k0) >> 2);
+            uint4 Anew;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t av = w_of(A, k);
+                uint32_t na2;
+                // -x / +x neighbours: p = 0 -> (S, cur), p = 1 -> (cur, S)
+                const uint32_t nxm = p ? w_of(cur, k) : w_of(S, k);
+                const uint32_t nxp = p ? w_of(S, k) : w_of(cur, k);
+                if (!BONDS) {
+                    na2 = unsat2(av, nxm, 0) + unsat2(av, nxp, 0) + unsat2(av, w_of(prev, k), 0) +
+                          unsat2(av, w_of(next, k), 0);
+                    if (D == 3) na2 += unsat2(av, w_of(ym, k), 0) + unsat2(av, w_of(yp, k), 0);
+                } else {
+                    na2 = unsat2(av, nxm, w_of(jx_oth, k)) + unsat2(av, nxp, w_of(jx_own, k));
+                    if (D == 2) {
+                        na2 += unsat2(av, w_of(prev, k), w_of(jy_oth, k)) +
+                               unsat2(av, w_of(next, k), w_of(jy_own, k));
+                    } else {
+                        na2 += unsat2(av, w_of(ym, k), w_of(jy_oth, k)) +
+                               unsat2(av, w_of(yp, k), w_of(jy_own, k)) +
+                               unsat2(av, w_of(prev, k), w_of(jz_oth, k)) +
+                               unsat2(av, w_of(next, k), w_of(jz_own, k));
+                    }
+                }
+                uint32_t na = na2 >> 1;
+                if (a.tab.sigma_neg) na = two_d - na;
+                const uint4 rnd = philox4x32_10(make_uint4(g0 + k, t, a.replica, ctr_w), a.rk);
+                const uint32_t qw = (uint32_t)q_of(rnd.x, a.tab) |
+                                    ((uint32_t)q_of(rnd.y, a.tab) << 8) |
+                                    ((uint32_t)q_of(rnd.z, a.tab) << 16) |
+                                    ((uint32_t)q_of(rnd.w, a.tab) << 24);
+                const uint32_t acc7 = ((na | 0x80808080u) - qw) & 0x80808080u;
+                const uint32_t flip = acc7 >> 7;
+                const uint32_t an = av ^ (flip * 0xFEu);
+                if (k == 0) Anew.x = an;
+                else if (k == 1) Anew.y = an;
+                else if (k == 2) Anew.z = an;
+                else Anew.w = an;
+                if (a.measure) {
+                    const uint32_t fm = flip * 0xFFu;
+                    const uint32_t nap = na ^ ((na ^ (two_d - na)) & fm);
+                    sum_na += (unsigned)__dp4a(nap, 0x01010101u, 0u);
+                    down += __popc(an & 0x80808080u) + __popc(w_of(cur, k) & 0x80808080u);
+                }
+            }
+            *reinterpret_cast<uint4*>(a.own + ro + k0) = Anew;
+            if (a.measure) nsite += 16;
+            prev = cur;
+            cur = next;
+            if (BONDS) jprev = jnext;
+        }
+    }
+    if (!a.measure) return;
+    long long bond = (long long)(2 * D) * (long long)nsite - 2 * (long long)sum_na;
+    if (a.tab.sigma_neg) bond = -bond;
+    Partial mine;
+    mine.i0 = block_sum(bond, red);
+    mine.i1 = block_sum((long long)down, red);
+    mine.f[0] = mine.f[1] = mine.f[2] = mine.f[3] = 0.0;
+    finish_pass(a.ctrl, a.partials, mine, [&](const Partial& tot) { i8_finish(a, tot); });
+}
+
+// ------------------------------------------------------ init / layout ----
+
+__global__ void i8_init_kernel(int8_t* s0, int8_t* s1, long long H, uint32_t replica, RoundKeys rk)
+{
+    const long long ng = (H + 3) >> 2;
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < 2 * ng;
+         g += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(g / ng);
+        const long long gg = g % ng;
+        const uint4 r = philox4x32_10(
+            make_uint4((uint32_t)gg, 0u, replica, (kInit << 1) | (uint32_t)c), rk);
+        const uint32_t rr[4] = {r.x, r.y, r.z, r.w};
+        int8_t* s = c ? s1 : s0;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const long long j = 4 * gg + b;
+            if (j < H) s[j] = (rr[b] >> 31) ? (int8_t)1 : (int8_t)-1;
+        }
+    }
+}
+
+__device__ __forceinline__ int colour_of(long long i, int L)
+{
+    const int x = (int)(i % L);
+    const long long r = i / L;
+    return (x + (int)(r % L) + (int)(r / L)) & 1;
+}
+
+__global__ void i8_scatter_kernel(int8_t* s0, int8_t* s1, const int8_t* nat, long long N, int L)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (long long)gridDim.x * blockDim.x)
+        (colour_of(i, L) ? s1 : s0)[i >> 1] = nat[i];
+}
+
+__global__ void i8_gather_kernel(const int8_t* s0, const int8_t* s1, int8_t* nat, long long N, int L)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (long long)gridDim.x * blockDim.x)
+        nat[i] = (colour_of(i, L) ? s1 : s0)[i >> 1];
+}
+
+struct BondPtrs {
+    int8_t* p[2][3];
+};
+
+__global__ void bonds_scatter_kernel(BondPtrs bp, const int8_t* nat, long long N, int L, int d,
+                                     unsigned* flags)
+{
+    unsigned f = 0;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < d * N;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int mu = (int)(k / N);
+        const long long i = k % N;
+        const int8_t v = nat[k];
+        if (v == 0) f |= 1u;
+        if (v < -1 || v > 1) f |= 2u;
+        bp.p[colour_of(i, L)][mu][i >> 1] = v;
+    }
+    if (f) atomicOr(flags, f);
+}
+
+int grid_for(long long work, int block)
+{
+    long long g = (work + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > kMaxBlocks) g = kMaxBlocks;
+    return (int)g;
+}
+
+I8Args make_args(const sl_lattice* h, int c)
+{
+    I8Args a;
+    a.own = (int8_t*)h->spins[c];
+    a.oth = (const int8_t*)h->spins[1 - c];
+    for (int mu = 0; mu < 3; ++mu) {
+        a.Jown[mu] = (const int8_t*)h->bonds[c][mu];
+        a.Joth[mu] = (const int8_t*)h->bonds[1 - c][mu];
+    }
+    a.d = h->d;
+    a.L = h->L;
+    a.W = h->W;
+    a.c = c;
+    a.R = 1;
+    a.H = h->H;
+    a.N = h->N;
+    a.replica = h->replica;
+    a.ctrl = h->ctrl;
+    a.partials = h->partials;
+    a.J = h->J;
+    a.measure = c == 1;
+    a.update = 1;
+    return a;
+}
+
+bool stream_ok(const sl_lattice* h)
+{
+    return h->W % 16 == 0 && !h->bonds_have_zero;
+}
+
+int pick_rows(const sl_lattice* h)
+{
+    if (h->rows > 0) return h->rows;
+    const long long W16 = h->W / 16;
+    const long long cross = h->d == 3 ? h->L : 1;
+    int R = 32;
+    while (R > 1 && (h->L % R != 0 || W16 * cross * (h->L / R) < 152LL * 512)) R >>= 1;
+    return R;
+}
+
+cudaError_t launch_pass(const sl_lattice* h, I8Args a, cudaStream_t s, bool stream)
+{
+    if (stream) {
+        a.R = pick_rows(h);
+        const long long items = (long long)(h->W / 16) * (h->d == 3 ? h->L : 1) * (h->L / a.R);
+        const int grid = grid_for(items, 128);
+        const bool bonds = a.Jown[0] != nullptr;
+        if (h->d == 2) {
+            if (bonds) i8_stream<2, 1><<<grid, 128, 0, s>>>(a);
+            else i8_stream<2, 0><<<grid, 128, 0, s>>>(a);
+        } else {
+            if (bonds) i8_stream<3, 1><<<grid, 128, 0, s>>>(a);
+            else i8_stream<3, 0><<<grid, 128, 0, s>>>(a);
+        }
+    } else {
+        const int grid = grid_for((h->H + 3) >> 2, 256);
+        if (h->d == 2) i8_generic<2><<<grid, 256, 0, s>>>(a);
+        else i8_generic<3><<<grid, 256, 0, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t ising_i8_init(const sl_lattice* h, cudaStream_t s)
+{
+    i8_init_kernel<<<grid_for(2 * ((h->H + 3) >> 2), 256), 256, 0, s>>>(
+        (int8_t*)h->spins[0], (int8_t*)h->spins[1], h->H, h->replica,
+        make_round_keys(h->init_seed));
+    return cudaGetLastError();
+}
+
+cudaError_t ising_i8_scatter(const sl_lattice* h, const int8_t* nat, cudaStream_t s)
+{
+    i8_scatter_kernel<<<grid_for(h->N, 256), 256, 0, s>>>((int8_t*)h->spins[0],
+                                                          (int8_t*)h->spins[1], nat, h->N, h->L);
+    return cudaGetLastError();
+}
+
+cudaError_t ising_i8_gather(const sl_lattice* h, int8_t* nat, cudaStream_t s)
+{
+    i8_gather_kernel<<<grid_for(h->N, 256), 256, 0, s>>>(
+        (const int8_t*)h->spins[0], (const int8_t*)h->spins[1], nat, h->N, h->L);
+    return cudaGetLastError();
+}
+
+cudaError_t ising_bonds_scatter(const sl_lattice* h, const int8_t* nat, unsigned* flags,
+                                cudaStream_t s)
+{
+    BondPtrs bp;
+    for (int c = 0; c < 2; ++c)
+        for (int mu = 0; mu < 3; ++mu) bp.p[c][mu] = (int8_t*)h->bonds[c][mu];
+    bonds_scatter_kernel<<<grid_for(h->d * h->N, 256), 256, 0, s>>>(bp, nat, h->N, h->L, h->d,
+                                                                    flags);
+    return cudaGetLastError();
+}
+
+cudaError_t ising_i8_sweeps(const sl_lattice* h, const SweepParams& p, int64_t count,
+                            cudaStream_t s)
+{
+    const bool stream = h->kernel == 2 || (h->kernel == 0 && stream_ok(h));
+    for (int64_t k = 0; k < count; ++k) {
+        for (int c = 0; c < 2; ++c) {
+            I8Args a = make_args(h, c);
+            a.tab = p.tab;
+            a.rk = p.rk;
+            const cudaError_t e = launch_pass(h, a, s, stream);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    return cudaSuccess;
+}
+
+cudaError_t ising_i8_measure(const sl_lattice* h, cudaStream_t s)
+{
+    I8Args a = make_args(h, 1);
+    a.update = 0;
+    a.measure = 1;
+    memset(&a.tab, 0, sizeof(a.tab));
+    memset(&a.rk, 0, sizeof(a.rk));
+    return launch_pass(h, a, s, false);
+}
+
+}  // namespace spinmc

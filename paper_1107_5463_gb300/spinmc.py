@@ -1,0 +1,217 @@
+"""Thin Python binding of libspinmc (include/spinmc.h).
+
+Argument marshalling only: every function below forwards to the C function of
+the same name, and every step of a sweep runs in the library's CUDA kernels.
+PyTorch supplies device memory and streams (the ``Lattice`` helper allocates
+its buffer as a torch uint8 tensor and passes the current CUDA stream).
+
+Importing this module loads ``libspinmc.so`` from the package directory and
+raises ImportError if it has not been built (``python -c "import
+__graft_entry__ as g; g.build()"``); there is no CPU fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libspinmc.so")
+
+SL_OK, SL_EINVAL, SL_ENOMEM, SL_ECUDA, SL_ETIMEOUT, SL_EDEVICE = 0, -1, -2, -3, -4, -5
+SL_J_UNIFORM, SL_J_BONDS = 0, 1
+SL_STORE_I8, SL_STORE_BITS, SL_STORE_F32_ANGLE, SL_STORE_F32_VEC = 0, 1, 2, 3
+SL_OPT_RENORM_EVERY, SL_OPT_FAST_MATH, SL_OPT_KERNEL, SL_OPT_ROWS, SL_OPT_GRAPH = 1, 2, 3, 4, 5
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libspinmc.so is not built at %s; run paper_1107_5463_gb300.build.build()"
+                      % LIB_PATH)
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+_vp, _int, _u32, _u64, _i64, _dbl, _sz = (ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32,
+                                          ctypes.c_uint64, ctypes.c_int64, ctypes.c_double,
+                                          ctypes.c_size_t)
+
+
+def _sig(name, restype, *argtypes):
+    f = getattr(_lib, name)
+    f.restype = restype
+    f.argtypes = list(argtypes)
+    return f
+
+
+_sig("sl_required_bytes", _int, _int, _int, _int, _int, _int, ctypes.POINTER(_sz))
+_sig("sl_create", _int, _int, _int, _int, _int, _int, _dbl, _vp, _u64, _u32, _vp, _sz, _vp,
+     ctypes.POINTER(_vp))
+_sig("sl_sweep", _int, _vp, _dbl, _i64, _u64)
+_sig("sl_sweep_series", _int, _vp, _dbl, _i64, _u64, _vp, _vp)
+_sig("sl_measure", _int, _vp, ctypes.POINTER(_dbl), ctypes.POINTER(_dbl))
+_sig("sl_get_spins", _int, _vp, _vp)
+_sig("sl_set_spins", _int, _vp, _vp)
+_sig("sl_get_state", _int, _vp, ctypes.POINTER(_u64), ctypes.POINTER(_i64))
+_sig("sl_set_state", _int, _vp, _i64)
+_sig("sl_set_option", _int, _vp, _int, _i64)
+_sig("sl_destroy", None, _vp)
+_sig("sl_strerror", ctypes.c_char_p, _int)
+_sig("sl_last_error", _int, ctypes.c_char_p, _sz)
+
+
+class SpinMCError(RuntimeError):
+    def __init__(self, status, where):
+        buf = ctypes.create_string_buffer(512)
+        _lib.sl_last_error(buf, 512)
+        super().__init__("%s: %s (%d): %s" % (where, _lib.sl_strerror(status).decode(), status,
+                                              buf.value.decode(errors="replace")))
+        self.status = status
+
+
+def _check(status, where):
+    if status != SL_OK:
+        raise SpinMCError(status, where)
+    return status
+
+
+def _addr(x):
+    """Raw address of a torch tensor, numpy array, int or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError("cannot take the address of %r" % type(x))
+
+
+# ---------------------------------------------------------- raw C ABI ----
+
+def sl_required_bytes(d, L, n, j_layout, storage):
+    out = _sz()
+    _check(_lib.sl_required_bytes(d, L, n, j_layout, storage, ctypes.byref(out)),
+           "sl_required_bytes")
+    return out.value
+
+
+def sl_create(d, L, n, j_layout, storage, J, J_bonds, seed, replica, dev_buf, dev_buf_bytes,
+              stream):
+    h = _vp()
+    _check(_lib.sl_create(d, L, n, j_layout, storage, J, _addr(J_bonds), seed, replica,
+                          _addr(dev_buf), dev_buf_bytes, stream, ctypes.byref(h)), "sl_create")
+    return h.value
+
+
+def sl_sweep(h, beta, nsweeps, seed):
+    _check(_lib.sl_sweep(h, beta, nsweeps, seed), "sl_sweep")
+
+
+def sl_sweep_series(h, beta, nsweeps, seed, dev_E, dev_absm):
+    _check(_lib.sl_sweep_series(h, beta, nsweeps, seed, _addr(dev_E), _addr(dev_absm)),
+           "sl_sweep_series")
+
+
+def sl_measure(h, n):
+    E = _dbl()
+    M = (_dbl * (n + 1))()
+    _check(_lib.sl_measure(h, ctypes.byref(E), M), "sl_measure")
+    return E.value, np.array(M[:])
+
+
+def sl_get_spins(h, dst):
+    _check(_lib.sl_get_spins(h, _addr(dst)), "sl_get_spins")
+
+
+def sl_set_spins(h, src):
+    _check(_lib.sl_set_spins(h, _addr(src)), "sl_set_spins")
+
+
+def sl_get_state(h):
+    s, t = _u64(), _i64()
+    _check(_lib.sl_get_state(h, ctypes.byref(s), ctypes.byref(t)), "sl_get_state")
+    return s.value, t.value
+
+
+def sl_set_state(h, sweeps_done):
+    _check(_lib.sl_set_state(h, sweeps_done), "sl_set_state")
+
+
+def sl_set_option(h, option, value):
+    _check(_lib.sl_set_option(h, option, value), "sl_set_option")
+
+
+def sl_destroy(h):
+    _lib.sl_destroy(h)
+
+
+# ------------------------------------------------- torch-backed helper ----
+
+_STORAGE_OF_N = {1: SL_STORE_I8, 2: SL_STORE_F32_ANGLE, 3: SL_STORE_F32_VEC}
+_NAT_DTYPE = {1: np.int8, 2: np.float32, 3: np.float32}
+
+
+class Lattice:
+    """A lattice whose device buffer is a torch CUDA tensor.
+
+    Spins exchanged with the host are natural-order numpy arrays: int8 +-1
+    (n = 1), float32 angles (n = 2), float32 (N, 3) vectors (n = 3)."""
+
+    def __init__(self, d, L, n=1, J=1.0, J_bonds=None, seed=0, replica=0, storage=None,
+                 stream=None, device="cuda"):
+        import torch
+        self.d, self.L, self.n = d, L, n
+        self.N = L ** d
+        self.storage = _STORAGE_OF_N[n] if storage is None else storage
+        j_layout = SL_J_UNIFORM if J_bonds is None else SL_J_BONDS
+        nbytes = sl_required_bytes(d, L, n, j_layout, self.storage)
+        self.buf = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        self.stream = torch.cuda.current_stream(self.buf.device) if stream is None else stream
+        if J_bonds is not None and isinstance(J_bonds, np.ndarray):
+            J_bonds = np.ascontiguousarray(J_bonds, np.int8 if n == 1 else np.float32)
+        self._bonds_keepalive = J_bonds
+        self.h = sl_create(d, L, n, j_layout, self.storage, J, J_bonds, seed, replica, self.buf,
+                           nbytes, self.stream.cuda_stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            sl_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sweep(self, beta, nsweeps, seed):
+        sl_sweep(self.h, beta, nsweeps, seed)
+
+    def sweep_series(self, beta, nsweeps, seed):
+        """Run sweeps and return (E, |m|) as torch float64 CUDA tensors."""
+        import torch
+        E = torch.empty(nsweeps, dtype=torch.float64, device=self.buf.device)
+        m = torch.empty(nsweeps, dtype=torch.float64, device=self.buf.device)
+        sl_sweep_series(self.h, beta, nsweeps, seed, E, m)
+        return E, m
+
+    def measure(self):
+        return sl_measure(self.h, self.n)
+
+    def get_spins(self):
+        shape = (self.N,) if self.n != 3 else (self.N, 3)
+        out = np.empty(shape, _NAT_DTYPE[self.n])
+        sl_get_spins(self.h, out)
+        return out
+
+    def set_spins(self, s):
+        s = np.ascontiguousarray(s, _NAT_DTYPE[self.n])
+        assert s.size == self.N * (3 if self.n == 3 else 1)
+        sl_set_spins(self.h, s)
+
+    def state(self):
+        return sl_get_state(self.h)
+
+    def set_state(self, sweeps_done):
+        sl_set_state(self.h, sweeps_done)
+
+    def set_option(self, option, value):
+        sl_set_option(self.h, option, value)
