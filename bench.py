@@ -325,7 +325,8 @@ def main():
         "check": {"E_per_site_last": e_last / N},
     }
     if rank == 0:
-        line["e2e"] = e2e_run(spinmc, wl, args.e2e_jobs, 1000, rank)
+        if args.e2e_jobs > 0:
+            line["e2e"] = e2e_run(spinmc, wl, args.e2e_jobs, 1000, rank)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(wl)
         if not args.no_variants:

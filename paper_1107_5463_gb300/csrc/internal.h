@@ -79,4 +79,11 @@ cudaError_t ising_i8_sweeps(const sl_lattice* h, const SweepParams& p, int64_t c
                             cudaStream_t s);
 cudaError_t ising_i8_measure(const sl_lattice* h, cudaStream_t s);
 
+// ---- XY / Heisenberg FP32 (on_f32.cu) ----
+cudaError_t on_init(const sl_lattice* h, cudaStream_t s);
+cudaError_t on_layout(const sl_lattice* h, float* nat, int dir, cudaStream_t s);
+cudaError_t float_bonds_scatter(const sl_lattice* h, const float* nat, cudaStream_t s);
+cudaError_t on_sweeps(const sl_lattice* h, const SweepParams& p, int64_t count, cudaStream_t s);
+cudaError_t on_measure(const sl_lattice* h, cudaStream_t s);
+
 }  // namespace spinmc

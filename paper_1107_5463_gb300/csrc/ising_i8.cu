@@ -1,7 +1,10 @@
-// Ising model (n = 1) with one int8 (+1 / -1) per site, checkerboard
+// Ising model (n = 1) with one byte per site, checkerboard
 // Metropolis (Weigel & Yavors'kii 2011, Section 2, Eq. 1 and Eq. 2).
 //
-// Storage: two colour arrays S[c][j], j = i >> 1, each N/2 bytes.  A row of
+// Storage: two colour arrays S[c][j], j = i >> 1, each N/2 bytes holding 0
+// for spin +1 and 1 for spin -1 (so neighbour counts are plain byte sums and
+// flips a byte XOR); sl_get_spins / sl_set_spins convert to +-1.  Couplings
+// are stored per colour and direction as 0 (+1), 1 (-1) or 2 (0).  A row of
 // the lattice (fixed y, z) holds W = L/2 sites of each colour, contiguous in
 // S[c]; the colour-c site at colour column k of row (y, z) sits at
 // x = 2k + p with p = (y + z + c) & 1, so its -x / +x neighbours are the
@@ -59,6 +62,9 @@ __device__ __forceinline__ void i8_finish(const I8Args& a, const Partial& tot)
     }
 }
 
+__device__ __forceinline__ int spin_value(int8_t b) { return 1 - 2 * (int)b; }
+__device__ __forceinline__ int bond_value(int8_t b) { return b == 2 ? 0 : 1 - 2 * (int)b; }
+
 __device__ __forceinline__ int q_of(uint32_t u, const IsingTable& tab)
 {
     int q = 0;
@@ -106,11 +112,11 @@ __global__ void __launch_bounds__(256) i8_generic(const I8Args a)
                     (cm[0] + (long long)L * (cm[1] + (long long)L * cm[2])) >> 1;
                 const long long np =
                     (cp[0] + (long long)L * (cp[1] + (long long)L * cp[2])) >> 1;
-                const int jm = a.Jown[0] ? (int)a.Joth[mu][nm] : 1;
-                const int jp = a.Jown[0] ? (int)a.Jown[mu][j] : 1;
-                hs += jm * (int)a.oth[nm] + jp * (int)a.oth[np];
+                const int jm = a.Jown[0] ? bond_value(a.Joth[mu][nm]) : 1;
+                const int jp = a.Jown[0] ? bond_value(a.Jown[mu][j]) : 1;
+                hs += jm * spin_value(a.oth[nm]) + jp * spin_value(a.oth[np]);
             }
-            int s = a.own[j];
+            int s = spin_value(a.own[j]);
             int sh = s * hs;
             if (a.update) {
                 const int e = a.tab.sigma_neg ? -sh : sh;
@@ -118,12 +124,12 @@ __global__ void __launch_bounds__(256) i8_generic(const I8Args a)
                 if (gcls >= q_of(rr[b], a.tab)) {
                     s = -s;
                     sh = -sh;
-                    a.own[j] = (int8_t)s;
+                    a.own[j] = (int8_t)(s < 0);
                 }
             }
             if (a.measure) {
                 bond += sh;
-                down += (s < 0) + (a.oth[j] < 0);
+                down += (s < 0) + (a.oth[j] != 0);
             }
         }
     }
@@ -167,13 +173,21 @@ __device__ __forceinline__ uint32_t w_of(const uint4& v, int k)
     return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w;
 }
 
-// 0x02 in each byte whose three +-1 factors multiply to -1
-__device__ __forceinline__ uint32_t unsat2(uint32_t a, uint32_t n, uint32_t j)
+// Per byte: 0x80 minus the number of thresholds below u, i.e. 0x80 - q(u)
+// for the four sites of one Philox block (byte b <- output b).
+template <int NCMP>
+__device__ __forceinline__ uint32_t q_bias(const uint4& r, const IsingTable& tab)
 {
-    return (a ^ n ^ j) & 0x02020202u;
+    uint32_t acc = 0x80808080u;
+    const uint32_t u[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+        for (int k = 0; k < NCMP; ++k) acc -= (u[b] > tab.thr[k]) ? (1u << (8 * b)) : 0u;
+    return acc;
 }
 
-template <int D, int BONDS>
+template <int D, int BONDS, int JNEG>
 __global__ void __launch_bounds__(128) i8_stream(const I8Args a)
 {
     __shared__ long long red[32];
@@ -184,7 +198,8 @@ __global__ void __launch_bounds__(128) i8_stream(const I8Args a)
     const long long nitems = (long long)W16 * (D == 3 ? L : 1) * nseg;
     const uint32_t ctr_w = (kSweep << 1) | (uint32_t)a.c;
     const uint32_t two_d = 0x01010101u * (uint32_t)(2 * D);
-    unsigned long long sum_na = 0, down = 0, nsite = 0;
+    const uint32_t ones = 0x01010101u;
+    unsigned long long s_na = 0, s_flip = 0, s_flipna = 0, down = 0, nsite = 0;
 
     for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < nitems;
          it += (long long)gridDim.x * blockDim.x) {
@@ -194,22 +209,14 @@ __global__ void __launch_bounds__(128) i8_stream(const I8Args a)
         const int seg = D == 3 ? (int)(rest / L) : (int)rest;
         const int k0 = cx << 4;
         const int m0 = seg * R;
-        // offset of row (yy, zz)
-        auto off = [&](int yy, int zz) -> long long {
-            return ((long long)zz * L + yy) * W;
-        };
-        // rows along the marching axis m: 2D m = y, 3D m = z (y fixed = y3)
-        auto moff = [&](int m) -> long long {
-            return D == 3 ? off(y3, m) : off(m, 0);
-        };
+        auto off = [&](int yy, int zz) -> long long { return ((long long)zz * L + yy) * W; };
+        auto moff = [&](int m) -> long long { return D == 3 ? off(y3, m) : off(m, 0); };
         const int mprev = m0 == 0 ? L - 1 : m0 - 1;
         uint4 prev = ld_rows(a.oth + moff(mprev) + k0);
         uint4 cur = ld_rows(a.oth + moff(m0) + k0);
         uint4 jprev = make_uint4(0, 0, 0, 0);
-        if (BONDS) {
-            const int mu = D == 3 ? 2 : 1;  // bonds along the marching axis
-            jprev = ld_rows(a.Joth[mu] + moff(mprev) + k0);
-        }
+        if (BONDS) jprev = ld_rows(a.Joth[D == 3 ? 2 : 1] + moff(mprev) + k0);
+        uint32_t i_na = 0, i_flip = 0, i_flipna = 0, i_down = 0;
         for (int r = 0; r < R; ++r) {
             const int m = m0 + r;
             const int mnext = m == L - 1 ? 0 : m + 1;
@@ -229,30 +236,23 @@ __global__ void __launch_bounds__(128) i8_stream(const I8Args a)
                 ym = ld_rows(a.oth + off(ym_, zz) + k0);
                 yp = ld_rows(a.oth + off(yp_, zz) + k0);
             }
-            // couplings: +x/+y/+z from own forward bonds; -x from the other
-            // colour's x bonds (shifted when the -x neighbour is column k-1);
-            // -y / -z from the other colour's rows behind.
-            uint4 jx_own, jx_oth, jy_own, jy_oth, jz_own, jz_oth;
-            uint4 jnext = make_uint4(0, 0, 0, 0);
+            // couplings (0 = +1, 1 = -1): +x/+y/+z from own forward bonds; -x
+            // from the other colour's x bonds (shifted when the -x neighbour is
+            // column k-1); -y / -z from the other colour's rows behind.
+            uint4 jx_own, jx_oth, jy_own, jy_oth, jz_own, jz_oth, jnext;
             if (BONDS) {
                 jx_own = ld_rows(a.Jown[0] + ro + k0);
                 const uint4 jo = ld_rows(a.Joth[0] + ro + k0);
-                if (p == 0) {
-                    const uint32_t jedge = (uint8_t)a.Joth[0][ro + eidx];
-                    jx_oth = shift_row(jo, jedge, 0);
-                } else {
-                    jx_oth = jo;
-                }
+                jx_oth = p == 0 ? shift_row(jo, (uint8_t)a.Joth[0][ro + eidx], 0) : jo;
+                jy_own = ld_rows(a.Jown[1] + ro + k0);
                 if (D == 2) {
-                    jy_own = ld_rows(a.Jown[1] + ro + k0);
-                    jy_oth = jprev;  // Joth[1] at row m - 1
+                    jy_oth = jprev;
                     jnext = ld_rows(a.Joth[1] + ro + k0);
                 } else {
                     const int ym_ = yy == 0 ? L - 1 : yy - 1;
-                    jy_own = ld_rows(a.Jown[1] + ro + k0);
                     jy_oth = ld_rows(a.Joth[1] + off(ym_, zz) + k0);
                     jz_own = ld_rows(a.Jown[2] + ro + k0);
-                    jz_oth = jprev;  // Joth[2] at plane m - 1
+                    jz_oth = jprev;
                     jnext = ld_rows(a.Joth[2] + ro + k0);
                 }
             }
@@ -261,57 +261,61 @@ __global__ void __launch_bounds__(128) i8_stream(const I8Args a)
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const uint32_t av = w_of(A, k);
-                uint32_t na2;
-                // -x / +x neighbours: p = 0 -> (S, cur), p = 1 -> (cur, S)
                 const uint32_t nxm = p ? w_of(cur, k) : w_of(S, k);
                 const uint32_t nxp = p ? w_of(S, k) : w_of(cur, k);
+                uint32_t na;  // unsatisfied bonds per byte (ferromagnetic sense)
                 if (!BONDS) {
-                    na2 = unsat2(av, nxm, 0) + unsat2(av, nxp, 0) + unsat2(av, w_of(prev, k), 0) +
-                          unsat2(av, w_of(next, k), 0);
-                    if (D == 3) na2 += unsat2(av, w_of(ym, k), 0) + unsat2(av, w_of(yp, k), 0);
+                    uint32_t nd = nxm + nxp + w_of(prev, k) + w_of(next, k);
+                    if (D == 3) nd += w_of(ym, k) + w_of(yp, k);
+                    // own spin down: na = 2d - nd = (nd ^ 7) - (7 - 2d)
+                    na = (nd ^ (av * 7u)) - av * (uint32_t)(7 - 2 * D);
                 } else {
-                    na2 = unsat2(av, nxm, w_of(jx_oth, k)) + unsat2(av, nxp, w_of(jx_own, k));
+                    na = (av ^ nxm ^ w_of(jx_oth, k)) + (av ^ nxp ^ w_of(jx_own, k));
                     if (D == 2) {
-                        na2 += unsat2(av, w_of(prev, k), w_of(jy_oth, k)) +
-                               unsat2(av, w_of(next, k), w_of(jy_own, k));
+                        na += (av ^ w_of(prev, k) ^ w_of(jy_oth, k)) +
+                              (av ^ w_of(next, k) ^ w_of(jy_own, k));
                     } else {
-                        na2 += unsat2(av, w_of(ym, k), w_of(jy_oth, k)) +
-                               unsat2(av, w_of(yp, k), w_of(jy_own, k)) +
-                               unsat2(av, w_of(prev, k), w_of(jz_oth, k)) +
-                               unsat2(av, w_of(next, k), w_of(jz_own, k));
+                        na += (av ^ w_of(ym, k) ^ w_of(jy_oth, k)) +
+                              (av ^ w_of(yp, k) ^ w_of(jy_own, k)) +
+                              (av ^ w_of(prev, k) ^ w_of(jz_oth, k)) +
+                              (av ^ w_of(next, k) ^ w_of(jz_own, k));
                     }
                 }
-                uint32_t na = na2 >> 1;
-                if (a.tab.sigma_neg) na = two_d - na;
+                if (JNEG) na = two_d - na;
                 const uint4 rnd = philox4x32_10(make_uint4(g0 + k, t, a.replica, ctr_w), a.rk);
-                const uint32_t qw = (uint32_t)q_of(rnd.x, a.tab) |
-                                    ((uint32_t)q_of(rnd.y, a.tab) << 8) |
-                                    ((uint32_t)q_of(rnd.z, a.tab) << 16) |
-                                    ((uint32_t)q_of(rnd.w, a.tab) << 24);
-                const uint32_t acc7 = ((na | 0x80808080u) - qw) & 0x80808080u;
-                const uint32_t flip = acc7 >> 7;
-                const uint32_t an = av ^ (flip * 0xFEu);
+                // byte bit 7 set iff na >= q(u): accept
+                const uint32_t flip = ((na + q_bias<D>(rnd, a.tab)) & 0x80808080u) >> 7;
+                const uint32_t an = av ^ flip;
                 if (k == 0) Anew.x = an;
                 else if (k == 1) Anew.y = an;
                 else if (k == 2) Anew.z = an;
                 else Anew.w = an;
                 if (a.measure) {
-                    const uint32_t fm = flip * 0xFFu;
-                    const uint32_t nap = na ^ ((na ^ (two_d - na)) & fm);
-                    sum_na += (unsigned)__dp4a(nap, 0x01010101u, 0u);
-                    down += __popc(an & 0x80808080u) + __popc(w_of(cur, k) & 0x80808080u);
+                    i_na = __dp4a(na, ones, i_na);
+                    i_flip = __dp4a(flip, ones, i_flip);
+                    i_flipna = __dp4a(flip, na, i_flipna);
+                    i_down = __dp4a(an, ones, __dp4a(w_of(cur, k), ones, i_down));
                 }
             }
             *reinterpret_cast<uint4*>(a.own + ro + k0) = Anew;
-            if (a.measure) nsite += 16;
             prev = cur;
             cur = next;
             if (BONDS) jprev = jnext;
         }
+        if (a.measure) {
+            s_na += i_na;
+            s_flip += i_flip;
+            s_flipna += i_flipna;
+            down += i_down;
+            nsite += 16 * R;
+        }
     }
     if (!a.measure) return;
-    long long bond = (long long)(2 * D) * (long long)nsite - 2 * (long long)sum_na;
-    if (a.tab.sigma_neg) bond = -bond;
+    // sum over colour-1 sites of the unsatisfied bonds after the move:
+    // na' = na + flip (2d - 2 na)
+    const long long na_after = (long long)s_na + 2 * D * (long long)s_flip - 2 * (long long)s_flipna;
+    long long bond = (long long)(2 * D) * (long long)nsite - 2 * na_after;
+    if (JNEG) bond = -bond;
     Partial mine;
     mine.i0 = block_sum(bond, red);
     mine.i1 = block_sum((long long)down, red);
@@ -335,7 +339,7 @@ __global__ void i8_init_kernel(int8_t* s0, int8_t* s1, long long H, uint32_t rep
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
             const long long j = 4 * gg + b;
-            if (j < H) s[j] = (rr[b] >> 31) ? (int8_t)1 : (int8_t)-1;
+            if (j < H) s[j] = (rr[b] >> 31) ? (int8_t)0 : (int8_t)1;
         }
     }
 }
@@ -351,14 +355,14 @@ __global__ void i8_scatter_kernel(int8_t* s0, int8_t* s1, const int8_t* nat, lon
 {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
          i += (long long)gridDim.x * blockDim.x)
-        (colour_of(i, L) ? s1 : s0)[i >> 1] = nat[i];
+        (colour_of(i, L) ? s1 : s0)[i >> 1] = (int8_t)(nat[i] < 0);
 }
 
 __global__ void i8_gather_kernel(const int8_t* s0, const int8_t* s1, int8_t* nat, long long N, int L)
 {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
          i += (long long)gridDim.x * blockDim.x)
-        nat[i] = (colour_of(i, L) ? s1 : s0)[i >> 1];
+        nat[i] = (colour_of(i, L) ? s1 : s0)[i >> 1] ? (int8_t)-1 : (int8_t)1;
 }
 
 struct BondPtrs {
@@ -376,7 +380,7 @@ __global__ void bonds_scatter_kernel(BondPtrs bp, const int8_t* nat, long long N
         const int8_t v = nat[k];
         if (v == 0) f |= 1u;
         if (v < -1 || v > 1) f |= 2u;
-        bp.p[colour_of(i, L)][mu][i >> 1] = v;
+        bp.p[colour_of(i, L)][mu][i >> 1] = (int8_t)(v == 0 ? 2 : (v < 0 ? 1 : 0));
     }
     if (f) atomicOr(flags, f);
 }
@@ -436,13 +440,16 @@ cudaError_t launch_pass(const sl_lattice* h, I8Args a, cudaStream_t s, bool stre
         const long long items = (long long)(h->W / 16) * (h->d == 3 ? h->L : 1) * (h->L / a.R);
         const int grid = grid_for(items, 128);
         const bool bonds = a.Jown[0] != nullptr;
+        const bool jneg = a.tab.sigma_neg != 0;
+#define SPINMC_LAUNCH(D, B, N) i8_stream<D, B, N><<<grid, 128, 0, s>>>(a)
         if (h->d == 2) {
-            if (bonds) i8_stream<2, 1><<<grid, 128, 0, s>>>(a);
-            else i8_stream<2, 0><<<grid, 128, 0, s>>>(a);
+            if (bonds) { if (jneg) SPINMC_LAUNCH(2, 1, 1); else SPINMC_LAUNCH(2, 1, 0); }
+            else { if (jneg) SPINMC_LAUNCH(2, 0, 1); else SPINMC_LAUNCH(2, 0, 0); }
         } else {
-            if (bonds) i8_stream<3, 1><<<grid, 128, 0, s>>>(a);
-            else i8_stream<3, 0><<<grid, 128, 0, s>>>(a);
+            if (bonds) { if (jneg) SPINMC_LAUNCH(3, 1, 1); else SPINMC_LAUNCH(3, 1, 0); }
+            else { if (jneg) SPINMC_LAUNCH(3, 0, 1); else SPINMC_LAUNCH(3, 0, 0); }
         }
+#undef SPINMC_LAUNCH
     } else {
         const int grid = grid_for((h->H + 3) >> 2, 256);
         if (h->d == 2) i8_generic<2><<<grid, 256, 0, s>>>(a);

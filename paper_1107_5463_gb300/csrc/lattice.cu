@@ -60,10 +60,10 @@ int check_config(int d, int L, int n, int j_layout, int storage)
         return fail(SL_EINVAL, "SL_STORE_BITS is not available in this build");
     case SL_STORE_F32_ANGLE:
         if (n != 2) return fail(SL_EINVAL, "SL_STORE_F32_ANGLE needs n = 2");
-        return fail(SL_EINVAL, "SL_STORE_F32_ANGLE is not available in this build");
+        break;
     case SL_STORE_F32_VEC:
         if (n != 3) return fail(SL_EINVAL, "SL_STORE_F32_VEC needs n = 3");
-        return fail(SL_EINVAL, "SL_STORE_F32_VEC is not available in this build");
+        break;
     default:
         return fail(SL_EINVAL, "unknown storage %d", storage);
     }
@@ -145,6 +145,7 @@ int model_sweeps(const sl_lattice* h, const SweepParams& p, int64_t count, cudaS
 {
     cudaError_t e = cudaErrorInvalidValue;
     if (h->storage == SL_STORE_I8) e = ising_i8_sweeps(h, p, count, s);
+    else if (h->n > 1) e = on_sweeps(h, p, count, s);
     return e == cudaSuccess ? SL_OK : cuda_fail(e, "sweep launch");
 }
 
@@ -287,6 +288,7 @@ int sl_create(int d, int L, int n, int j_layout, int storage, double J, const vo
     }
     e = cudaMemsetAsync(h->ctrl, 0, sizeof(Ctrl), h->stream);
     if (e == cudaSuccess && storage == SL_STORE_I8) e = ising_i8_init(h, h->stream);
+    if (e == cudaSuccess && n > 1) e = on_init(h, h->stream);
     if (e == cudaSuccess && j_layout == SL_J_BONDS) {
         unsigned* flags = (unsigned*)h->partials;
         e = cudaMemsetAsync(flags, 0, sizeof(unsigned), h->stream);
@@ -295,6 +297,8 @@ int sl_create(int d, int L, int n, int j_layout, int storage, double J, const vo
                                 cudaMemcpyDefault, h->stream);
         if (e == cudaSuccess && n == 1)
             e = ising_bonds_scatter(h, (const int8_t*)h->staging, flags, h->stream);
+        if (e == cudaSuccess && n > 1)
+            e = float_bonds_scatter(h, (const float*)h->staging, h->stream);
         unsigned f = 0;
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
         if (e == cudaSuccess) e = cudaMemcpy(&f, flags, sizeof f, cudaMemcpyDeviceToHost);
@@ -365,6 +369,7 @@ int sl_measure(sl_lattice* h, double* energy, double* magnetisation)
     if (!h) return fail(SL_EINVAL, "lattice is NULL");
     cudaError_t e = cudaErrorInvalidValue;
     if (h->storage == SL_STORE_I8) e = ising_i8_measure(h, h->stream);
+    else if (h->n > 1) e = on_measure(h, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "measure launch");
     int st = sync_and_check(h);
     if (st != SL_OK) return st;
@@ -388,6 +393,7 @@ int sl_get_spins(sl_lattice* h, void* dst)
     if (!h || !dst) return fail(SL_EINVAL, "NULL argument");
     cudaError_t e = cudaErrorInvalidValue;
     if (h->storage == SL_STORE_I8) e = ising_i8_gather(h, (int8_t*)h->staging, h->stream);
+    else if (h->n > 1) e = on_layout(h, (float*)h->staging, 1, h->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(dst, h->staging, nat_bytes(h), cudaMemcpyDefault, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "sl_get_spins");
@@ -400,6 +406,7 @@ int sl_set_spins(sl_lattice* h, const void* src)
     cudaError_t e = cudaMemcpyAsync(h->staging, src, nat_bytes(h), cudaMemcpyDefault, h->stream);
     if (e == cudaSuccess) {
         if (h->storage == SL_STORE_I8) e = ising_i8_scatter(h, (const int8_t*)h->staging, h->stream);
+        else if (h->n > 1) e = on_layout(h, (float*)h->staging, 0, h->stream);
         else e = cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return cuda_fail(e, "sl_set_spins");

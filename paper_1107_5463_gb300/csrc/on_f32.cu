@@ -1,0 +1,408 @@
+// Continuous-spin O(n) models in FP32 with FP64 observable totals
+// (Weigel & Yavors'kii 2011, Section 2: Eq. 1, Eq. 2, and the mixed-precision
+// scheme of Table 1, "Metro. single": spins in single precision, aggregate
+// quantities such as the total energy in double precision).
+//
+//   XY (n = 2):          one FP32 angle per site, colour arrays theta[c][j];
+//   Heisenberg (n = 3):  FP32 unit vectors, colour arrays of components
+//                        s[c][a*H + j] (structure of arrays).
+//
+// A move proposes a fresh uniform angle (XY) or direction (Heisenberg) from
+// the site's Philox outputs, computes dE = -(s' - s) . h in FP32 and accepts
+// iff dE <= 0 or u24 < exp(-beta dE).  Per-thread partial sums of the
+// observables are FP32; blocks and the final fixed-order total are FP64.
+// FAST selects the hardware sin/cos/exp intrinsics (the "fast math" row of
+// Table 1), with angles shifted into [-pi, pi) where the intrinsics are
+// accurate.
+#include "internal.h"
+
+namespace spinmc {
+namespace {
+
+constexpr float kTwoPiF = 6.28318530717958647692f;
+constexpr float kPiF = 3.14159265358979323846f;
+
+struct OnArgs {
+    float* own;
+    const float* oth;
+    const float* Jown[3];
+    const float* Joth[3];
+    int d, L, W, c;
+    long long H, N;
+    uint32_t replica;
+    RoundKeys rk;
+    float beta;
+    float J;
+    Ctrl* ctrl;
+    Partial* partials;
+    int measure, update;
+    int renorm_every;  // Heisenberg: normalise each updated spin when (t+1) % renorm_every == 0
+};
+
+__device__ __forceinline__ float u24(uint32_t x) { return (float)(x >> 8) * (1.0f / 16777216.0f); }
+
+template <bool FAST>
+__device__ __forceinline__ void sincos_angle(float th, float* s, float* c)
+{
+    if (FAST) {
+        // sin(th) = -sin(th - pi), cos(th) = -cos(th - pi); th - pi in [-pi, pi)
+        __sincosf(th - kPiF, s, c);
+        *s = -*s;
+        *c = -*c;
+    } else {
+        sincosf(th, s, c);
+    }
+}
+
+template <bool FAST>
+__device__ __forceinline__ float boltzmann(float x)
+{
+    return FAST ? __expf(x) : expf(x);
+}
+
+// fresh uniform direction on the sphere from two 32-bit outputs
+template <bool FAST>
+__device__ __forceinline__ float3 sphere_point(uint32_t oz, uint32_t ophi)
+{
+    const float z = 2.0f * u24(oz) - 1.0f;
+    const float r = sqrtf((1.0f - z) * (1.0f + z));
+    float sp, cp;
+    if (FAST) {
+        __sincosf(kTwoPiF * u24(ophi) - kPiF, &sp, &cp);
+        sp = -sp;
+        cp = -cp;
+    } else {
+        sincospif(2.0f * u24(ophi), &sp, &cp);
+    }
+    return make_float3(r * cp, r * sp, z);
+}
+
+__device__ __forceinline__ void on_finish(const OnArgs& a, const Partial& tot)
+{
+    Ctrl* C = a.ctrl;
+    C->obs[0] = tot.f[0];
+    C->obs[1] = tot.f[1];
+    C->obs[2] = tot.f[2];
+    C->obs[3] = tot.f[3];
+    if (a.update) {
+        const long long k = (long long)C->t - C->series_base;
+        const double m = sqrt(tot.f[1] * tot.f[1] + tot.f[2] * tot.f[2] + tot.f[3] * tot.f[3]);
+        if (C->series_E) C->series_E[k] = tot.f[0];
+        if (C->series_absm) C->series_absm[k] = m / (double)a.N;
+        C->t = C->t + 1;
+    }
+}
+
+// One thread per site; a block walks whole rows (fixed y, z) so that the
+// loads of a warp are contiguous.  Any even L.
+template <int NC, int D, bool FAST>
+__global__ void __launch_bounds__(128) on_generic(const OnArgs a)
+{
+    __shared__ double red[32];
+    const unsigned long long t64 = a.ctrl->t;
+    const uint32_t t = (uint32_t)t64;
+    const bool renorm = NC == 3 && a.update && a.renorm_every > 0 &&
+                        (t64 + 1) % (unsigned long long)a.renorm_every == 0;
+    const int L = a.L, W = a.W;
+    const long long H = a.H;
+    const long long nrows = (long long)L * (D == 3 ? L : 1);
+    const bool bonds = a.Jown[0] != nullptr;
+    float pe = 0.f, pmx = 0.f, pmy = 0.f, pmz = 0.f;
+    for (long long row = blockIdx.x; row < nrows; row += gridDim.x) {
+        const int y = (int)(row % L);
+        const int z = (int)(row / L);
+        const int p = (y + z + a.c) & 1;
+        const long long base = row * W;
+        const long long rym = (long long)(z)*L + (y == 0 ? L - 1 : y - 1);
+        const long long ryp = (long long)(z)*L + (y == L - 1 ? 0 : y + 1);
+        const long long rzm = (long long)(z == 0 ? L - 1 : z - 1) * L + y;
+        const long long rzp = (long long)(z == L - 1 ? 0 : z + 1) * L + y;
+        for (int k = threadIdx.x; k < W; k += blockDim.x) {
+            const long long j = base + k;
+            int kxm = k - 1 + p, kxp = k + p;
+            if (kxm < 0) kxm = W - 1;
+            if (kxp == W) kxp = 0;
+            long long nb[6] = {base + kxm, base + kxp, rym * W + k, ryp * W + k, 0, 0};
+            if (D == 3) {
+                nb[4] = rzm * W + k;
+                nb[5] = rzp * W + k;
+            }
+            float jk[6];
+#pragma unroll
+            for (int q = 0; q < 2 * D; ++q) {
+                const int mu = q >> 1;
+                jk[q] = bonds ? a.J * ((q & 1) ? a.Jown[mu][j] : a.Joth[mu][nb[q]]) : a.J;
+            }
+            // local field h and the colour-0 site sharing index j
+            float hx = 0.f, hy = 0.f, hz = 0.f, ox = 0.f, oy = 0.f, oz = 0.f;
+            const int q_same = p ? 0 : 1;  // neighbour with colour index k in this row
+#pragma unroll
+            for (int q = 0; q < 2 * D; ++q) {
+                float vx, vy, vz = 0.f;
+                if (NC == 2) {
+                    sincos_angle<FAST>(a.oth[nb[q]], &vy, &vx);
+                } else {
+                    vx = a.oth[nb[q]];
+                    vy = a.oth[H + nb[q]];
+                    vz = a.oth[2 * H + nb[q]];
+                }
+                hx += jk[q] * vx;
+                hy += jk[q] * vy;
+                hz += jk[q] * vz;
+                if (q == q_same) {
+                    ox = vx;
+                    oy = vy;
+                    oz = vz;
+                }
+            }
+            float sx, sy, sz = 0.f, th = 0.f;
+            if (NC == 2) {
+                th = a.own[j];
+                sincos_angle<FAST>(th, &sy, &sx);
+            } else {
+                sx = a.own[j];
+                sy = a.own[H + j];
+                sz = a.own[2 * H + j];
+            }
+            bool changed = false;
+            if (a.update) {
+                float nx, ny, nz = 0.f, nth = 0.f, u;
+                if (NC == 2) {
+                    const uint4 r = philox4x32_10(
+                        make_uint4((uint32_t)(j >> 1), t, a.replica, (kSweep << 1) | (uint32_t)a.c),
+                        a.rk);
+                    const uint32_t oa = (j & 1) ? r.z : r.x;
+                    const uint32_t op = (j & 1) ? r.w : r.y;
+                    u = u24(oa);
+                    nth = kTwoPiF * u24(op);
+                    sincos_angle<FAST>(nth, &ny, &nx);
+                } else {
+                    const uint4 r = philox4x32_10(
+                        make_uint4((uint32_t)j, t, a.replica, (kSweep << 1) | (uint32_t)a.c), a.rk);
+                    u = u24(r.x);
+                    const float3 v = sphere_point<FAST>(r.y, r.z);
+                    nx = v.x;
+                    ny = v.y;
+                    nz = v.z;
+                }
+                const float dE = -((nx - sx) * hx + (ny - sy) * hy + (nz - sz) * hz);
+                const bool acc = dE <= 0.f || u < boltzmann<FAST>(-a.beta * dE);
+                if (acc) {
+                    sx = nx;
+                    sy = ny;
+                    sz = nz;
+                    th = nth;
+                    changed = true;
+                }
+                if (renorm) {
+                    const float inv = rsqrtf(sx * sx + sy * sy + sz * sz);
+                    sx *= inv;
+                    sy *= inv;
+                    sz *= inv;
+                    changed = true;
+                }
+                if (changed) {
+                    if (NC == 2) {
+                        a.own[j] = th;
+                    } else {
+                        a.own[j] = sx;
+                        a.own[H + j] = sy;
+                        a.own[2 * H + j] = sz;
+                    }
+                }
+            }
+            if (a.measure) {
+                pe -= sx * hx + sy * hy + sz * hz;
+                pmx += sx + ox;
+                pmy += sy + oy;
+                pmz += sz + oz;
+            }
+        }
+    }
+    if (!a.measure) return;
+    Partial mine;
+    mine.i0 = mine.i1 = 0;
+    mine.f[0] = block_sum((double)pe, red);
+    mine.f[1] = block_sum((double)pmx, red);
+    mine.f[2] = block_sum((double)pmy, red);
+    mine.f[3] = block_sum((double)pmz, red);
+    finish_pass(a.ctrl, a.partials, mine, [&](const Partial& tot) { on_finish(a, tot); });
+}
+
+template <int NC>
+__global__ void on_init_kernel(float* s0, float* s1, long long H, uint32_t replica, RoundKeys rk)
+{
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < 2 * H;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(q / H);
+        const long long j = q % H;
+        float* s = c ? s1 : s0;
+        if (NC == 2) {
+            const uint4 r = philox4x32_10(
+                make_uint4((uint32_t)(j >> 1), 0u, replica, (kInit << 1) | (uint32_t)c), rk);
+            s[j] = kTwoPiF * u24((j & 1) ? r.w : r.y);
+        } else {
+            const uint4 r =
+                philox4x32_10(make_uint4((uint32_t)j, 0u, replica, (kInit << 1) | (uint32_t)c), rk);
+            const float3 v = sphere_point<false>(r.y, r.z);
+            s[j] = v.x;
+            s[H + j] = v.y;
+            s[2 * H + j] = v.z;
+        }
+    }
+}
+
+__device__ __forceinline__ int colour_of(long long i, int L)
+{
+    const int x = (int)(i % L);
+    const long long r = i / L;
+    return (x + (int)(r % L) + (int)(r / L)) & 1;
+}
+
+// natural order <-> colour arrays; `dir` 0 = scatter (nat -> colours), 1 = gather
+template <int NC>
+__global__ void on_layout_kernel(float* s0, float* s1, float* nat, long long N, long long H, int L,
+                                 int dir)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (long long)gridDim.x * blockDim.x) {
+        float* s = colour_of(i, L) ? s1 : s0;
+        const long long j = i >> 1;
+        if (NC == 2) {
+            if (dir == 0) s[j] = nat[i];
+            else nat[i] = s[j];
+        } else {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                if (dir == 0) s[q * H + j] = nat[3 * i + q];
+                else nat[3 * i + q] = s[q * H + j];
+            }
+        }
+    }
+}
+
+struct FBondPtrs {
+    float* p[2][3];
+};
+
+__global__ void fbonds_scatter_kernel(FBondPtrs bp, const float* nat, long long N, int L, int d)
+{
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < d * N;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int mu = (int)(k / N);
+        const long long i = k % N;
+        bp.p[colour_of(i, L)][mu][i >> 1] = nat[k];
+    }
+}
+
+int grid_for(long long work, int block)
+{
+    long long g = (work + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > kMaxBlocks) g = kMaxBlocks;
+    return (int)g;
+}
+
+OnArgs make_args(const sl_lattice* h, int c)
+{
+    OnArgs a;
+    a.own = (float*)h->spins[c];
+    a.oth = (const float*)h->spins[1 - c];
+    for (int mu = 0; mu < 3; ++mu) {
+        a.Jown[mu] = (const float*)h->bonds[c][mu];
+        a.Joth[mu] = (const float*)h->bonds[1 - c][mu];
+    }
+    a.d = h->d;
+    a.L = h->L;
+    a.W = h->W;
+    a.c = c;
+    a.H = h->H;
+    a.N = h->N;
+    a.replica = h->replica;
+    a.J = (float)h->J;
+    a.ctrl = h->ctrl;
+    a.partials = h->partials;
+    a.measure = c == 1;
+    a.update = 1;
+    a.renorm_every = h->renorm_every;
+    return a;
+}
+
+template <int NC>
+cudaError_t launch_on(const sl_lattice* h, const OnArgs& a, cudaStream_t s)
+{
+    const long long rows = (long long)h->L * (h->d == 3 ? h->L : 1);
+    int grid = (int)(rows < 152LL * 8 ? rows : 152LL * 8);
+    if (grid > kMaxBlocks) grid = kMaxBlocks;
+    const bool fast = h->fast_math != 0;
+    if (h->d == 2) {
+        if (fast) on_generic<NC, 2, true><<<grid, 128, 0, s>>>(a);
+        else on_generic<NC, 2, false><<<grid, 128, 0, s>>>(a);
+    } else {
+        if (fast) on_generic<NC, 3, true><<<grid, 128, 0, s>>>(a);
+        else on_generic<NC, 3, false><<<grid, 128, 0, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t on_init(const sl_lattice* h, cudaStream_t s)
+{
+    const RoundKeys rk = make_round_keys(h->init_seed);
+    const int grid = grid_for(2 * h->H, 256);
+    if (h->n == 2)
+        on_init_kernel<2><<<grid, 256, 0, s>>>((float*)h->spins[0], (float*)h->spins[1], h->H,
+                                               h->replica, rk);
+    else
+        on_init_kernel<3><<<grid, 256, 0, s>>>((float*)h->spins[0], (float*)h->spins[1], h->H,
+                                               h->replica, rk);
+    return cudaGetLastError();
+}
+
+cudaError_t on_layout(const sl_lattice* h, float* nat, int dir, cudaStream_t s)
+{
+    const int grid = grid_for(h->N, 256);
+    if (h->n == 2)
+        on_layout_kernel<2><<<grid, 256, 0, s>>>((float*)h->spins[0], (float*)h->spins[1], nat, h->N,
+                                                 h->H, h->L, dir);
+    else
+        on_layout_kernel<3><<<grid, 256, 0, s>>>((float*)h->spins[0], (float*)h->spins[1], nat, h->N,
+                                                 h->H, h->L, dir);
+    return cudaGetLastError();
+}
+
+cudaError_t float_bonds_scatter(const sl_lattice* h, const float* nat, cudaStream_t s)
+{
+    FBondPtrs bp;
+    for (int c = 0; c < 2; ++c)
+        for (int mu = 0; mu < 3; ++mu) bp.p[c][mu] = (float*)h->bonds[c][mu];
+    fbonds_scatter_kernel<<<grid_for(h->d * h->N, 256), 256, 0, s>>>(bp, nat, h->N, h->L, h->d);
+    return cudaGetLastError();
+}
+
+cudaError_t on_sweeps(const sl_lattice* h, const SweepParams& p, int64_t count, cudaStream_t s)
+{
+    for (int64_t k = 0; k < count; ++k) {
+        for (int c = 0; c < 2; ++c) {
+            OnArgs a = make_args(h, c);
+            a.rk = p.rk;
+            a.beta = p.beta_f;
+            const cudaError_t e = h->n == 2 ? launch_on<2>(h, a, s) : launch_on<3>(h, a, s);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    return cudaSuccess;
+}
+
+cudaError_t on_measure(const sl_lattice* h, cudaStream_t s)
+{
+    OnArgs a = make_args(h, 1);
+    a.update = 0;
+    a.measure = 1;
+    memset(&a.rk, 0, sizeof a.rk);
+    a.beta = 0.f;
+    return h->n == 2 ? launch_on<2>(h, a, s) : launch_on<3>(h, a, s);
+}
+
+}  // namespace spinmc
