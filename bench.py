@@ -29,13 +29,24 @@ sys.path.insert(0, ROOT)
 METRIC = "spin flips/ns"
 UNIT = "flips/ns"
 
+# bytes: algorithmic HBM bytes per site update of one colour pass (read the
+# updated colour and the other colour, write the updated colour)
 WORKLOADS = {
-    "ising2d_L16384_i8": dict(d=2, L=16384, n=1, beta=0.440687, storage="i8",
+    "ising2d_L16384_i8": dict(d=2, L=16384, n=1, beta=0.440687, storage="i8", bytes=3.0,
                               desc="2D Ising ferromagnet J=1, L=16384 periodic, int8 spins, "
                                    "beta_c=0.440687, random start"),
-    "ising3d_L512_i8": dict(d=3, L=512, n=1, beta=0.2216546, storage="i8",
+    "ising3d_L512_i8": dict(d=3, L=512, n=1, beta=0.2216546, storage="i8", bytes=3.0,
                             desc="3D Ising ferromagnet J=1, L=512 simple cubic, int8 spins, "
                                  "beta=0.2216546, random start"),
+    "ising2d_L16384_bits": dict(d=2, L=16384, n=1, beta=0.440687, storage="bits", bytes=0.375,
+                                desc="2D Ising, L=16384, one bit per spin"),
+    "ising3d_L512_bits": dict(d=3, L=512, n=1, beta=0.2216546, storage="bits", bytes=0.375,
+                              desc="3D Ising, L=512, one bit per spin"),
+    "heis3d_L256_f32": dict(d=3, L=256, n=3, beta=0.693, storage="vec", bytes=36.0,
+                            desc="3D Heisenberg J=1, L=256, FP32 unit vectors, beta=0.693, "
+                                 "renormalised every 16 sweeps"),
+    "xy2d_L4096_f32": dict(d=2, L=4096, n=2, beta=1.12, storage="angle", bytes=12.0,
+                           desc="2D XY J=1, L=4096, FP32 angles, beta=1.12"),
 }
 HEADLINE = "ising2d_L16384_i8"
 
@@ -162,7 +173,9 @@ def time_sweeps(spinmc, wl, steps, warmup, replica, want_clocks, local):
     """Device-timed K sweeps of one lattice; returns (ms, clocks)."""
     import torch
     from paper_1107_5463_gb300 import inputs
-    lat = spinmc.Lattice(wl["d"], wl["L"], n=wl["n"], seed=inputs.DEFAULT_SEED, replica=replica)
+    storage = spinmc.SL_STORE_BITS if wl["storage"] == "bits" else None
+    lat = spinmc.Lattice(wl["d"], wl["L"], n=wl["n"], seed=inputs.DEFAULT_SEED, replica=replica,
+                         storage=storage)
     E = torch.empty(max(steps, warmup, 1), dtype=torch.float64, device="cuda")
     m = torch.empty_like(E)
     spinmc.sl_sweep_series(lat.h, wl["beta"], warmup, inputs.DEFAULT_SEED, E, m)
@@ -304,14 +317,15 @@ def main():
     hbm, peak_kind = peaks()
     launches_per_step = 2
     launch_ms = ms / (args.steps * launches_per_step)
-    bytes_per_launch = 3 * (N // 2)          # read own + other colour, write own (int8)
+    bytes_per_launch = wl["bytes"] * (N // 2)   # one colour pass
     achieved_gbs = bytes_per_launch / (launch_ms * 1e-3) / 1e9
     traffic = recorded_traffic(args.workload)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "int8", "data": "synthetic",
+        "dtype": {"i8": "int8", "bits": "u32 bit-planes", "vec": "f32", "angle": "f32"}[
+            wl["storage"]], "data": "synthetic",
         "config": {"workload": args.workload, "desc": wl["desc"], "d": d, "L": L,
                    "sites": N, "beta": wl["beta"], "step": "one full sweep + fused E,|m|",
                    "l2": "inputs larger than L2 (%d MB of spins)" % (N // 2**20),
@@ -337,8 +351,9 @@ def main():
                 k = 300
                 vms, _, _ = time_sweeps(spinmc, w, k, 5, rank, False, local)
                 n = w["L"] ** w["d"]
+                gbs = w["bytes"] * (n // 2) / (vms / (2 * k) * 1e-3) / 1e9
                 var[name] = {"value": n * k / (vms * 1e6), "unit": UNIT, "ms_per_step": vms / k,
-                             "hbm_frac": 3 * (n // 2) / (vms / (2 * k) * 1e-3) / 1e9 / hbm}
+                             "achieved_gbs": gbs, "hbm_frac": gbs / hbm}
             line["variants"] = var
         print(json.dumps(line), flush=True)
     barrier(world)

@@ -79,6 +79,14 @@ cudaError_t ising_i8_sweeps(const sl_lattice* h, const SweepParams& p, int64_t c
                             cudaStream_t s);
 cudaError_t ising_i8_measure(const sl_lattice* h, cudaStream_t s);
 
+// ---- Ising bit-packed (ising_bits.cu) ----
+cudaError_t ising_bits_init(const sl_lattice* h, cudaStream_t s);
+cudaError_t ising_bits_scatter(const sl_lattice* h, const int8_t* nat, cudaStream_t s);
+cudaError_t ising_bits_gather(const sl_lattice* h, int8_t* nat, cudaStream_t s);
+cudaError_t ising_bits_sweeps(const sl_lattice* h, const SweepParams& p, int64_t count,
+                              cudaStream_t s);
+cudaError_t ising_bits_measure(const sl_lattice* h, cudaStream_t s);
+
 // ---- XY / Heisenberg FP32 (on_f32.cu) ----
 cudaError_t on_init(const sl_lattice* h, cudaStream_t s);
 cudaError_t on_layout(const sl_lattice* h, float* nat, int dir, cudaStream_t s);

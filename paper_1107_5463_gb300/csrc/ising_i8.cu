@@ -217,17 +217,40 @@ __global__ void __launch_bounds__(128) i8_stream(const I8Args a)
         uint4 jprev = make_uint4(0, 0, 0, 0);
         if (BONDS) jprev = ld_rows(a.Joth[D == 3 ? 2 : 1] + moff(mprev) + k0);
         uint32_t i_na = 0, i_flip = 0, i_flipna = 0, i_down = 0;
+        // software pipeline: row m's own chunk, its edge byte and row m+1 of
+        // the other colour are loaded one iteration ahead
+        auto row_of = [&](int m, int& yy, int& zz) {
+            yy = D == 3 ? y3 : m;
+            zz = D == 3 ? m : 0;
+        };
+        auto edge_idx = [&](int p) {
+            return p ? (k0 + 16 == W ? 0 : k0 + 16) : (k0 == 0 ? W - 1 : k0 - 1);
+        };
+        int yy0, zz0;
+        row_of(m0, yy0, zz0);
+        uint4 next = ld_rows(a.oth + moff(m0 == L - 1 ? 0 : m0 + 1) + k0);
+        uint4 A_nx = *reinterpret_cast<const uint4*>(a.own + off(yy0, zz0) + k0);
+        uint32_t edge_nx =
+            (uint8_t)a.oth[off(yy0, zz0) + edge_idx((yy0 + zz0 + a.c) & 1)];
         for (int r = 0; r < R; ++r) {
             const int m = m0 + r;
-            const int mnext = m == L - 1 ? 0 : m + 1;
-            const uint4 next = ld_rows(a.oth + moff(mnext) + k0);
-            const int yy = D == 3 ? y3 : m;
-            const int zz = D == 3 ? m : 0;
+            int yy, zz;
+            row_of(m, yy, zz);
             const int p = (yy + zz + a.c) & 1;
             const long long ro = off(yy, zz);
-            const int eidx = p ? (k0 + 16 == W ? 0 : k0 + 16) : (k0 == 0 ? W - 1 : k0 - 1);
-            const uint32_t edge = (uint8_t)a.oth[ro + eidx];
-            const uint4 A = *reinterpret_cast<const uint4*>(a.own + ro + k0);
+            const int eidx = edge_idx(p);
+            const uint4 A = A_nx;
+            const uint32_t edge = edge_nx;
+            const uint4 nxt = next;
+            if (r + 1 < R) {
+                const int m1 = m + 1;
+                const int m2 = m1 == L - 1 ? 0 : m1 + 1;
+                int y1, z1;
+                row_of(m1, y1, z1);
+                next = ld_rows(a.oth + moff(m2) + k0);
+                A_nx = *reinterpret_cast<const uint4*>(a.own + off(y1, z1) + k0);
+                edge_nx = (uint8_t)a.oth[off(y1, z1) + edge_idx((y1 + z1 + a.c) & 1)];
+            }
             const uint4 S = shift_row(cur, edge, p);
             uint4 ym = make_uint4(0, 0, 0, 0), yp = ym;
             if (D == 3) {
@@ -265,7 +288,7 @@ __global__ void __launch_bounds__(128) i8_stream(const I8Args a)
                 const uint32_t nxp = p ? w_of(S, k) : w_of(cur, k);
                 uint32_t na;  // unsatisfied bonds per byte (ferromagnetic sense)
                 if (!BONDS) {
-                    uint32_t nd = nxm + nxp + w_of(prev, k) + w_of(next, k);
+                    uint32_t nd = nxm + nxp + w_of(prev, k) + w_of(nxt, k);
                     if (D == 3) nd += w_of(ym, k) + w_of(yp, k);
                     // own spin down: na = 2d - nd = (nd ^ 7) - (7 - 2d)
                     na = (nd ^ (av * 7u)) - av * (uint32_t)(7 - 2 * D);
@@ -273,12 +296,12 @@ __global__ void __launch_bounds__(128) i8_stream(const I8Args a)
                     na = (av ^ nxm ^ w_of(jx_oth, k)) + (av ^ nxp ^ w_of(jx_own, k));
                     if (D == 2) {
                         na += (av ^ w_of(prev, k) ^ w_of(jy_oth, k)) +
-                              (av ^ w_of(next, k) ^ w_of(jy_own, k));
+                              (av ^ w_of(nxt, k) ^ w_of(jy_own, k));
                     } else {
                         na += (av ^ w_of(ym, k) ^ w_of(jy_oth, k)) +
                               (av ^ w_of(yp, k) ^ w_of(jy_own, k)) +
                               (av ^ w_of(prev, k) ^ w_of(jz_oth, k)) +
-                              (av ^ w_of(next, k) ^ w_of(jz_own, k));
+                              (av ^ w_of(nxt, k) ^ w_of(jz_own, k));
                     }
                 }
                 if (JNEG) na = two_d - na;
@@ -299,7 +322,7 @@ __global__ void __launch_bounds__(128) i8_stream(const I8Args a)
             }
             *reinterpret_cast<uint4*>(a.own + ro + k0) = Anew;
             prev = cur;
-            cur = next;
+            cur = nxt;
             if (BONDS) jprev = jnext;
         }
         if (a.measure) {

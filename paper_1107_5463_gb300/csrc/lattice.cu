@@ -57,7 +57,8 @@ int check_config(int d, int L, int n, int j_layout, int storage)
     case SL_STORE_BITS:
         if (n != 1) return fail(SL_EINVAL, "SL_STORE_BITS needs n = 1");
         if (L % 64) return fail(SL_EINVAL, "SL_STORE_BITS needs L %% 64 == 0 (got %d)", L);
-        return fail(SL_EINVAL, "SL_STORE_BITS is not available in this build");
+        if (j_layout != SL_J_UNIFORM) return fail(SL_EINVAL, "SL_STORE_BITS needs SL_J_UNIFORM");
+        break;
     case SL_STORE_F32_ANGLE:
         if (n != 2) return fail(SL_EINVAL, "SL_STORE_F32_ANGLE needs n = 2");
         break;
@@ -145,6 +146,7 @@ int model_sweeps(const sl_lattice* h, const SweepParams& p, int64_t count, cudaS
 {
     cudaError_t e = cudaErrorInvalidValue;
     if (h->storage == SL_STORE_I8) e = ising_i8_sweeps(h, p, count, s);
+    else if (h->storage == SL_STORE_BITS) e = ising_bits_sweeps(h, p, count, s);
     else if (h->n > 1) e = on_sweeps(h, p, count, s);
     return e == cudaSuccess ? SL_OK : cuda_fail(e, "sweep launch");
 }
@@ -288,6 +290,7 @@ int sl_create(int d, int L, int n, int j_layout, int storage, double J, const vo
     }
     e = cudaMemsetAsync(h->ctrl, 0, sizeof(Ctrl), h->stream);
     if (e == cudaSuccess && storage == SL_STORE_I8) e = ising_i8_init(h, h->stream);
+    if (e == cudaSuccess && storage == SL_STORE_BITS) e = ising_bits_init(h, h->stream);
     if (e == cudaSuccess && n > 1) e = on_init(h, h->stream);
     if (e == cudaSuccess && j_layout == SL_J_BONDS) {
         unsigned* flags = (unsigned*)h->partials;
@@ -369,6 +372,7 @@ int sl_measure(sl_lattice* h, double* energy, double* magnetisation)
     if (!h) return fail(SL_EINVAL, "lattice is NULL");
     cudaError_t e = cudaErrorInvalidValue;
     if (h->storage == SL_STORE_I8) e = ising_i8_measure(h, h->stream);
+    else if (h->storage == SL_STORE_BITS) e = ising_bits_measure(h, h->stream);
     else if (h->n > 1) e = on_measure(h, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "measure launch");
     int st = sync_and_check(h);
@@ -393,6 +397,7 @@ int sl_get_spins(sl_lattice* h, void* dst)
     if (!h || !dst) return fail(SL_EINVAL, "NULL argument");
     cudaError_t e = cudaErrorInvalidValue;
     if (h->storage == SL_STORE_I8) e = ising_i8_gather(h, (int8_t*)h->staging, h->stream);
+    else if (h->storage == SL_STORE_BITS) e = ising_bits_gather(h, (int8_t*)h->staging, h->stream);
     else if (h->n > 1) e = on_layout(h, (float*)h->staging, 1, h->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(dst, h->staging, nat_bytes(h), cudaMemcpyDefault, h->stream);
@@ -406,6 +411,8 @@ int sl_set_spins(sl_lattice* h, const void* src)
     cudaError_t e = cudaMemcpyAsync(h->staging, src, nat_bytes(h), cudaMemcpyDefault, h->stream);
     if (e == cudaSuccess) {
         if (h->storage == SL_STORE_I8) e = ising_i8_scatter(h, (const int8_t*)h->staging, h->stream);
+        else if (h->storage == SL_STORE_BITS)
+            e = ising_bits_scatter(h, (const int8_t*)h->staging, h->stream);
         else if (h->n > 1) e = on_layout(h, (float*)h->staging, 0, h->stream);
         else e = cudaErrorInvalidValue;
     }
@@ -447,6 +454,8 @@ int sl_set_option(sl_lattice* h, int option, int64_t value)
         return SL_OK;
     case SL_OPT_KERNEL:
         if (value < 0 || value > 2) return fail(SL_EINVAL, "kernel must be 0, 1 or 2");
+        if (value == 1 && h->storage == SL_STORE_BITS)
+            return fail(SL_EINVAL, "bit storage has only the streaming kernel");
         if (value == 2 && (h->W % 16 != 0 || h->bonds_have_zero))
             return fail(SL_EINVAL, "the streaming kernel needs L %% 32 == 0 and +-1 couplings");
         h->kernel = (int)value;

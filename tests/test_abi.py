@@ -69,3 +69,12 @@ def test_status_strings(lib):
     buf = ctypes.create_string_buffer(4)
     n = spinmc._lib.sl_last_error(buf, 4)
     assert n >= len(buf.value)
+
+
+def test_bit_storage_needs_L_multiple_of_64_and_uniform_J():
+    from paper_1107_5463_gb300 import spinmc
+    assert spinmc.sl_required_bytes(2, 128, 1, 0, spinmc.SL_STORE_BITS) > 0
+    for bad in ((2, 96, 1, 0, spinmc.SL_STORE_BITS), (2, 128, 1, 1, spinmc.SL_STORE_BITS),
+                (2, 128, 2, 0, spinmc.SL_STORE_BITS)):
+        with pytest.raises(spinmc.SpinMCError):
+            spinmc.sl_required_bytes(*bad)

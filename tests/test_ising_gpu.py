@@ -27,8 +27,9 @@ def sm():
 
 
 def gpu_run(sm, d, L, beta, seed, sweep_seed, nsw, J=1.0, Jb=None, kernel=0, rows=0, graph=1,
-            start=None, replica=0):
-    lat = sm.Lattice(d, L, n=1, J=J, J_bonds=Jb, seed=seed, replica=replica)
+            start=None, replica=0, bits=False):
+    lat = sm.Lattice(d, L, n=1, J=J, J_bonds=Jb, seed=seed, replica=replica,
+                     storage=sm.SL_STORE_BITS if bits else None)
     if kernel:
         lat.set_option(sm.SL_OPT_KERNEL, kernel)
     if rows:
@@ -105,10 +106,33 @@ def test_2d_L64_full_run_bit_exact(sm):
 @pytest.mark.parametrize("d,L,beta", [(2, 16384, 0.440687), (3, 512, inputs.BETA_3D_ISING)])
 def test_full_size_first_sweeps_bit_exact(sm, d, L, beta):
     """Full-size single-lattice workloads of the paper's Table 1 in the launch
-    configuration the bench times (automatic kernel choice, graphs on)."""
+    configuration the bench times (automatic kernel choice, graphs on), with
+    byte and bit storage."""
     seed = inputs.DEFAULT_SEED
-    got = gpu_run(sm, d, L, beta, seed, seed + 1, 5)
-    assert_same(got, oracle_run(d, L, beta, seed, seed + 1, 5))
+    ref = oracle_run(d, L, beta, seed, seed + 1, 5)
+    assert_same(gpu_run(sm, d, L, beta, seed, seed + 1, 5), ref)
+    assert_same(gpu_run(sm, d, L, beta, seed, seed + 1, 5, bits=True), ref)
+
+
+@pytest.mark.parametrize("d,L", [(2, 64), (2, 192), (2, 1024), (3, 64), (3, 128)])
+@pytest.mark.parametrize("beta,J", [(BETA_C, 1.0), (0.3, -0.7)])
+def test_bit_storage_parity(sm, d, L, beta, J):
+    """Multispin (one bit per site) storage: same start state and the same
+    trajectory as the oracle, bit for bit."""
+    got = gpu_run(sm, d, L, beta, 5, 77, 12, J=J, bits=True)
+    assert_same(got, oracle_run(d, L, beta, 5, 77, 12, J=J))
+
+
+def test_bit_storage_io_and_measure(sm):
+    for d, L in ((2, 128), (3, 64)):
+        s = inputs.ising_spins(d, L, 3)
+        lat = sm.Lattice(d, L, storage=sm.SL_STORE_BITS)
+        lat.set_spins(s)
+        np.testing.assert_array_equal(lat.get_spins(), s)
+        E, M = lat.measure()
+        E_ref, M_ref = oracle.ising_measure(d, L, s)
+        assert E == E_ref and M[0] == M_ref
+        lat.close()
 
 
 def test_kernels_rows_and_graphs_agree(sm):

@@ -21,7 +21,7 @@ pytestmark = pytest.mark.gpu
 
 TOL = 1e-5
 TIE_TOL = 2e-5
-TIE_TOL_FAST = 2e-4
+TIE_TOL_FAST = 5e-5
 
 
 @pytest.fixture(scope="module")
@@ -145,7 +145,7 @@ def test_parity_with_float_bonds_and_negative_J(sm, n):
     Pair(sm, n, d, L, 0.8, 8, J=-0.6, Jb=jb).check()
 
 
-@pytest.mark.parametrize("n,d,L,beta", [(2, 2, 32, 1.12), (3, 3, 16, 0.693)])
+@pytest.mark.parametrize("n,d,L,beta", [(2, 2, 32, 1.12), (3, 3, 24, 0.693)])
 def test_fast_math_parity(sm, n, d, L, beta):
     Pair(sm, n, d, L, beta, 10, fast=1, tie_tol=TIE_TOL_FAST).check()
 
