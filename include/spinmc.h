@@ -156,6 +156,60 @@ int sl_set_option(sl_lattice* lat, int option, int64_t value);
  * Synchronises the handle's stream first. */
 void sl_destroy(sl_lattice* lat);
 
+/* ---- Edwards-Anderson +-J spin glass, batched, with replica exchange ----
+ *
+ * Section 2 of the paper: for quenched disorder, independent disorder samples
+ * are a trivially parallel layer on top of the lattice decomposition.  A batch
+ * holds nsamples Edwards-Anderson samples (couplings J_ij = +-1 with p = 1/2,
+ * J_ij = +1 iff the top bit of output 0 of Philox(i, mu, sample, 2 << 1) under
+ * the create seed is set), each with ntemps <= 32 replicas ("slots") at the
+ * inverse temperatures betas[0..ntemps-1].  Slot r of sample s starts from
+ * the Ising start state of replica id s * ntemps + r and always draws its
+ * moves with that replica id.  After every sweep the energies of all slots
+ * are measured and temperature pairs (k, k+1), k = t mod 2, t mod 2 + 2, ...
+ * attempt an exchange accepted iff Delta >= 0 or U < exp(Delta) 2^32,
+ * Delta = (b_k - b_{k+1}) (E_{r(k)} - E_{r(k+1)}), U = output 0 of
+ * Philox(k, t, s, 3 << 1) under the sweep seed; accepted pairs swap which
+ * slot holds which temperature.  The replica exchange is not in the paper:
+ * it is the standard Metropolis swap between neighbouring temperatures. */
+
+typedef struct sl_batch sl_batch;
+
+/* Device bytes for a batch: d in {2,3}; L_per_sample[s] a multiple of 4 in
+ * [4, 32]; 2 <= ntemps <= 32; betas (host, ntemps finite values >= 0) size
+ * the exchange tables. */
+int sl_batch_required_bytes(int d, const int* L_per_sample, int nsamples, int ntemps,
+                            const double* betas, size_t* bytes);
+
+/* Create the batch on `stream` and draw its couplings and start states from
+ * `seed`.  betas: ntemps finite values >= 0 (host).  dev_buf as for
+ * sl_create (caller-owned, 256-byte aligned, NULL = library-owned). */
+int sl_batch_create(int d, const int* L_per_sample, int nsamples, int ntemps,
+                    const double* betas, uint64_t seed, void* dev_buf, size_t dev_buf_bytes,
+                    void* stream, sl_batch** out);
+
+/* nsweeps sweeps of every slot of every sample, each followed by the energy
+ * measurement and the exchange step, in one graph-captured launch per sample
+ * size.  Sweep indices continue from the batch's sweeps done.  dev_E (device,
+ * or NULL) receives nsamples * nsweeps * ntemps doubles: the energy at
+ * temperature k of sample s after sweep i (before its exchange step) at
+ * [(s * nsweeps + i) * ntemps + k].  Asynchronous. */
+int sl_batch_run(sl_batch* b, int64_t nsweeps, uint64_t seed, double* dev_E);
+
+/* Copy slot `slot` of sample `sample` out in natural order (int8 +-1, host or
+ * device dst) and report the temperature index it holds.  Synchronises. */
+int sl_batch_get(sl_batch* b, int sample, int slot, int8_t* dst, int* temp_index);
+
+/* Copy the couplings of a sample out as natural-order int8 [d][N] (+-1,
+ * forward bond of site i along mu).  Synchronises. */
+int sl_batch_get_bonds(sl_batch* b, int sample, int8_t* dst);
+
+/* Sweeps done by the batch (the next sweep index). */
+int sl_batch_sweeps_done(sl_batch* b, int64_t* sweeps_done);
+
+/* Release host metadata (and the buffer if library-owned); synchronises. */
+void sl_batch_destroy(sl_batch* b);
+
 /* sl_strerror — static text for a status code. */
 const char* sl_strerror(int status);
 

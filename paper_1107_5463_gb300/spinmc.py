@@ -52,6 +52,13 @@ _sig("sl_get_state", _int, _vp, ctypes.POINTER(_u64), ctypes.POINTER(_i64))
 _sig("sl_set_state", _int, _vp, _i64)
 _sig("sl_set_option", _int, _vp, _int, _i64)
 _sig("sl_destroy", None, _vp)
+_sig("sl_batch_required_bytes", _int, _int, _vp, _int, _int, _vp, ctypes.POINTER(_sz))
+_sig("sl_batch_create", _int, _int, _vp, _int, _int, _vp, _u64, _vp, _sz, _vp, ctypes.POINTER(_vp))
+_sig("sl_batch_run", _int, _vp, _i64, _u64, _vp)
+_sig("sl_batch_get", _int, _vp, _int, _int, _vp, ctypes.POINTER(_int))
+_sig("sl_batch_get_bonds", _int, _vp, _int, _vp)
+_sig("sl_batch_sweeps_done", _int, _vp, ctypes.POINTER(_i64))
+_sig("sl_batch_destroy", None, _vp)
 _sig("sl_strerror", ctypes.c_char_p, _int)
 _sig("sl_last_error", _int, ctypes.c_char_p, _sz)
 
@@ -143,6 +150,58 @@ def sl_destroy(h):
     _lib.sl_destroy(h)
 
 
+def _i32_array(xs):
+    a = np.ascontiguousarray(xs, np.int32)
+    return a, a.ctypes.data
+
+
+def _f64_array(xs):
+    a = np.ascontiguousarray(xs, np.float64)
+    return a, a.ctypes.data
+
+
+def sl_batch_required_bytes(d, L_per_sample, ntemps, betas):
+    Ls, pL = _i32_array(L_per_sample)
+    bs, pb = _f64_array(betas)
+    out = _sz()
+    _check(_lib.sl_batch_required_bytes(d, pL, Ls.size, ntemps, pb, ctypes.byref(out)),
+           "sl_batch_required_bytes")
+    return out.value
+
+
+def sl_batch_create(d, L_per_sample, ntemps, betas, seed, dev_buf, dev_buf_bytes, stream):
+    Ls, pL = _i32_array(L_per_sample)
+    bs, pb = _f64_array(betas)
+    h = _vp()
+    _check(_lib.sl_batch_create(d, pL, Ls.size, ntemps, pb, seed, _addr(dev_buf), dev_buf_bytes,
+                                stream, ctypes.byref(h)), "sl_batch_create")
+    return h.value
+
+
+def sl_batch_run(h, nsweeps, seed, dev_E):
+    _check(_lib.sl_batch_run(h, nsweeps, seed, _addr(dev_E)), "sl_batch_run")
+
+
+def sl_batch_get(h, sample, slot, dst):
+    k = _int()
+    _check(_lib.sl_batch_get(h, sample, slot, _addr(dst), ctypes.byref(k)), "sl_batch_get")
+    return k.value
+
+
+def sl_batch_get_bonds(h, sample, dst):
+    _check(_lib.sl_batch_get_bonds(h, sample, _addr(dst)), "sl_batch_get_bonds")
+
+
+def sl_batch_sweeps_done(h):
+    t = _i64()
+    _check(_lib.sl_batch_sweeps_done(h, ctypes.byref(t)), "sl_batch_sweeps_done")
+    return t.value
+
+
+def sl_batch_destroy(h):
+    _lib.sl_batch_destroy(h)
+
+
 # ------------------------------------------------- torch-backed helper ----
 
 _STORAGE_OF_N = {1: SL_STORE_I8, 2: SL_STORE_F32_ANGLE, 3: SL_STORE_F32_VEC}
@@ -215,3 +274,56 @@ class Lattice:
 
     def set_option(self, option, value):
         sl_set_option(self.h, option, value)
+
+
+class Batch:
+    """A batch of Edwards-Anderson samples with replica exchange, its device
+    buffer a torch CUDA tensor."""
+
+    def __init__(self, d, L_per_sample, ntemps, betas, seed=0, stream=None, device="cuda"):
+        import torch
+        self.d = d
+        self.L = [int(x) for x in L_per_sample]
+        self.ntemps = ntemps
+        self.nsamples = len(self.L)
+        nbytes = sl_batch_required_bytes(d, self.L, ntemps, betas)
+        self.buf = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        self.stream = torch.cuda.current_stream(self.buf.device) if stream is None else stream
+        self.h = sl_batch_create(d, self.L, ntemps, betas, seed, self.buf, nbytes,
+                                 self.stream.cuda_stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            sl_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, nsweeps, seed, series=False):
+        """Run sweeps; with series=True return the energies as a torch float64
+        tensor of shape (nsamples, nsweeps, ntemps)."""
+        import torch
+        E = None
+        if series:
+            E = torch.empty((self.nsamples, nsweeps, self.ntemps), dtype=torch.float64,
+                            device=self.buf.device)
+        sl_batch_run(self.h, nsweeps, seed, E)
+        return E
+
+    def get(self, sample, slot):
+        """(spins of the slot in natural order, temperature index it holds)."""
+        out = np.empty(self.L[sample] ** self.d, np.int8)
+        k = sl_batch_get(self.h, sample, slot, out)
+        return out, k
+
+    def bonds(self, sample):
+        out = np.empty((self.d, self.L[sample] ** self.d), np.int8)
+        sl_batch_get_bonds(self.h, sample, out)
+        return out
+
+    def sweeps_done(self):
+        return sl_batch_sweeps_done(self.h)
