@@ -60,9 +60,10 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def kernel_source_hash():
+def kernel_source_hash(files):
+    """Hash of the sources a profiled kernel is built from."""
     h = hashlib.sha256()
-    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1107_5463_gb300", "csrc"))):
+    for f in files:
         with open(os.path.join(ROOT, "paper_1107_5463_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -77,7 +78,7 @@ def recorded_traffic(workload):
     with open(p) as f:
         j = json.load(f)
     e = j.get(workload)
-    if not e or e.get("source_hash") != kernel_source_hash():
+    if not e or e.get("source_hash") != kernel_source_hash(e.get("source_files", [])):
         return None
     return e.get("dram_bytes_per_launch")
 

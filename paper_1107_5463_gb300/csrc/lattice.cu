@@ -456,8 +456,13 @@ int sl_set_option(sl_lattice* h, int option, int64_t value)
         if (value < 0 || value > 2) return fail(SL_EINVAL, "kernel must be 0, 1 or 2");
         if (value == 1 && h->storage == SL_STORE_BITS)
             return fail(SL_EINVAL, "bit storage has only the streaming kernel");
-        if (value == 2 && (h->W % 16 != 0 || h->bonds_have_zero))
+        if (value == 2 && h->n == 1 && (h->W % 16 != 0 || h->bonds_have_zero))
             return fail(SL_EINVAL, "the streaming kernel needs L %% 32 == 0 and +-1 couplings");
+        if (value == 2 && h->n > 1 &&
+            (h->j_layout != SL_J_UNIFORM || (h->n == 3 && h->W % 32 != 0) ||
+             (h->n == 2 && (h->d != 2 || h->W % 64 != 0))))
+            return fail(SL_EINVAL, "the streaming kernel needs uniform J and L %% 64 == 0 "
+                                   "(Heisenberg) or a 2D lattice with L %% 128 == 0 (XY)");
         h->kernel = (int)value;
         return SL_OK;
     case SL_OPT_ROWS:

@@ -27,7 +27,7 @@ struct OnArgs {
     const float* oth;
     const float* Jown[3];
     const float* Joth[3];
-    int d, L, W, c;
+    int d, L, W, c, R;
     long long H, N;
     uint32_t replica;
     RoundKeys rk;
@@ -229,6 +229,289 @@ __global__ void __launch_bounds__(128) on_generic(const OnArgs a)
     finish_pass(a.ctrl, a.partials, mine, [&](const Partial& tot) { on_finish(a, tot); });
 }
 
+// ------------------------------------------------------------ streaming ----
+//
+// Uniform coupling, W % 32 == 0 (Heisenberg) or W % 64 == 0 (XY): a warp owns
+// 32 consecutive columns of one row and marches along the last axis (y in 2D,
+// z in 3D) through R rows, keeping the other colour's rows behind, at and
+// ahead of the current one in registers (for XY as cos/sin, computed once per
+// value).  The x neighbours come from the adjacent lane by a shuffle (the two
+// warp-edge lanes load theirs).  Loads for the next row are issued one row
+// ahead.
+
+struct V3 {
+    float x, y, z;
+};
+
+__device__ __forceinline__ V3 ld3(const float* p, long long H, long long i)
+{
+    V3 v;
+    v.x = __ldg(p + i);
+    v.y = __ldg(p + H + i);
+    v.z = __ldg(p + 2 * H + i);
+    return v;
+}
+
+__device__ __forceinline__ V3 shfl3_up(V3 v)
+{
+    V3 r;
+    r.x = __shfl_up_sync(0xffffffffu, v.x, 1);
+    r.y = __shfl_up_sync(0xffffffffu, v.y, 1);
+    r.z = __shfl_up_sync(0xffffffffu, v.z, 1);
+    return r;
+}
+
+__device__ __forceinline__ V3 shfl3_down(V3 v)
+{
+    V3 r;
+    r.x = __shfl_down_sync(0xffffffffu, v.x, 1);
+    r.y = __shfl_down_sync(0xffffffffu, v.y, 1);
+    r.z = __shfl_down_sync(0xffffffffu, v.z, 1);
+    return r;
+}
+
+template <int D, bool FAST>
+__global__ void __launch_bounds__(256) heis_stream(const OnArgs a)
+{
+    __shared__ double red[32];
+    const unsigned long long t64 = a.ctrl->t;
+    const uint32_t t = (uint32_t)t64;
+    const bool renorm = a.update && a.renorm_every > 0 &&
+                        (t64 + 1) % (unsigned long long)a.renorm_every == 0;
+    const int L = a.L, W = a.W, R = a.R;
+    const long long H = a.H;
+    const int lane = threadIdx.x & 31;
+    const long long nitems = (long long)W * (D == 3 ? L : 1) * (L / R);
+    const float J = a.J;
+    float pe = 0.f, pmx = 0.f, pmy = 0.f, pmz = 0.f;
+    for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < nitems;
+         it += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(it % W);
+        const long long rest = it / W;
+        const int y3 = D == 3 ? (int)(rest % L) : 0;
+        const int m0 = (int)(D == 3 ? rest / L : rest) * R;
+        auto rowid = [&](int m) -> long long { return D == 3 ? (long long)m * L + y3 : m; };
+        const int mprev = m0 == 0 ? L - 1 : m0 - 1;
+        V3 prev = ld3(a.oth, H, rowid(mprev) * W + k);
+        V3 cur = ld3(a.oth, H, rowid(m0) * W + k);
+        V3 nxt_pf = ld3(a.oth, H, rowid(m0 == L - 1 ? 0 : m0 + 1) * W + k);
+        V3 own_pf = ld3(a.own, H, rowid(m0) * W + k);
+        for (int r = 0; r < R; ++r) {
+            const int m = m0 + r;
+            const long long row = rowid(m);
+            const int yy = D == 3 ? y3 : m, zz = D == 3 ? m : 0;
+            const int p = (yy + zz + a.c) & 1;
+            const long long j = row * W + k;
+            const V3 nxt = nxt_pf;
+            V3 s = own_pf;
+            if (r + 1 < R) {
+                const int m2 = m + 2 >= L ? m + 2 - L : m + 2;
+                nxt_pf = ld3(a.oth, H, rowid(m2) * W + k);
+                own_pf = ld3(a.own, H, rowid(m + 1) * W + k);
+            }
+            // x neighbours: p = 0 -> (k-1, k), p = 1 -> (k, k+1)
+            V3 xm, xp;
+            if (p == 0) {
+                xm = shfl3_up(cur);
+                if (lane == 0) xm = ld3(a.oth, H, row * W + (k == 0 ? W - 1 : k - 1));
+                xp = cur;
+            } else {
+                xm = cur;
+                xp = shfl3_down(cur);
+                if (lane == 31) xp = ld3(a.oth, H, row * W + (k == W - 1 ? 0 : k + 1));
+            }
+            float hx = xm.x + xp.x + prev.x + nxt.x;
+            float hy = xm.y + xp.y + prev.y + nxt.y;
+            float hz = xm.z + xp.z + prev.z + nxt.z;
+            if (D == 3) {
+                const long long rym = (long long)m * L + (y3 == 0 ? L - 1 : y3 - 1);
+                const long long ryp = (long long)m * L + (y3 == L - 1 ? 0 : y3 + 1);
+                const V3 vm = ld3(a.oth, H, rym * W + k), vp = ld3(a.oth, H, ryp * W + k);
+                hx += vm.x + vp.x;
+                hy += vm.y + vp.y;
+                hz += vm.z + vp.z;
+            }
+            hx *= J;
+            hy *= J;
+            hz *= J;
+            if (a.update) {
+                const uint4 rnd = philox4x32_10(
+                    make_uint4((uint32_t)j, t, a.replica, (kSweep << 1) | (uint32_t)a.c), a.rk);
+                const float u = u24(rnd.x);
+                const float3 v = sphere_point<FAST>(rnd.y, rnd.z);
+                const float dE = -((v.x - s.x) * hx + (v.y - s.y) * hy + (v.z - s.z) * hz);
+                bool changed = false;
+                if (dE <= 0.f || u < boltzmann<FAST>(-a.beta * dE)) {
+                    s.x = v.x;
+                    s.y = v.y;
+                    s.z = v.z;
+                    changed = true;
+                }
+                if (renorm) {
+                    const float inv = rsqrtf(s.x * s.x + s.y * s.y + s.z * s.z);
+                    s.x *= inv;
+                    s.y *= inv;
+                    s.z *= inv;
+                    changed = true;
+                }
+                if (changed) {
+                    a.own[j] = s.x;
+                    a.own[H + j] = s.y;
+                    a.own[2 * H + j] = s.z;
+                }
+            }
+            if (a.measure) {
+                pe -= s.x * hx + s.y * hy + s.z * hz;
+                pmx += s.x + cur.x;
+                pmy += s.y + cur.y;
+                pmz += s.z + cur.z;
+            }
+            prev = cur;
+            cur = nxt;
+        }
+    }
+    if (!a.measure) return;
+    Partial mine;
+    mine.i0 = mine.i1 = 0;
+    mine.f[0] = block_sum((double)pe, red);
+    mine.f[1] = block_sum((double)pmx, red);
+    mine.f[2] = block_sum((double)pmy, red);
+    mine.f[3] = block_sum((double)pmz, red);
+    finish_pass(a.ctrl, a.partials, mine, [&](const Partial& tot) { on_finish(a, tot); });
+}
+
+struct CS2 {
+    float c0, s0, c1, s1;  // cos / sin of the two columns of a pair
+};
+
+template <bool FAST>
+__device__ __forceinline__ CS2 cs_pair(const float* p, long long i)
+{
+    const float2 th = __ldg(reinterpret_cast<const float2*>(p + i));
+    CS2 r;
+    sincos_angle<FAST>(th.x, &r.s0, &r.c0);
+    sincos_angle<FAST>(th.y, &r.s1, &r.c1);
+    return r;
+}
+
+// XY, 2D: each thread owns the column pair (2q, 2q+1), whose sites share one
+// Philox block (group j >> 1).
+template <bool FAST>
+__global__ void __launch_bounds__(256) xy_stream(const OnArgs a)
+{
+    __shared__ double red[32];
+    const uint32_t t = (uint32_t)a.ctrl->t;
+    const int L = a.L, W = a.W, R = a.R;
+    const int WP = W / 2;
+    const int lane = threadIdx.x & 31;
+    const long long nitems = (long long)WP * (L / R);
+    const float J = a.J;
+    float pe = 0.f, pmx = 0.f, pmy = 0.f;
+    for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < nitems;
+         it += (long long)gridDim.x * blockDim.x) {
+        const int q = (int)(it % WP);
+        const int m0 = (int)(it / WP) * R;
+        const int k0 = 2 * q;
+        const int mprev = m0 == 0 ? L - 1 : m0 - 1;
+        CS2 prev = cs_pair<FAST>(a.oth, (long long)mprev * W + k0);
+        CS2 cur = cs_pair<FAST>(a.oth, (long long)m0 * W + k0);
+        float2 nxt_pf = __ldg(reinterpret_cast<const float2*>(
+            a.oth + (long long)(m0 == L - 1 ? 0 : m0 + 1) * W + k0));
+        float2 own_pf = *reinterpret_cast<const float2*>(a.own + (long long)m0 * W + k0);
+        for (int r = 0; r < R; ++r) {
+            const int m = m0 + r;
+            const int p = (m + a.c) & 1;
+            const long long j = (long long)m * W + k0;
+            CS2 nxt;
+            sincos_angle<FAST>(nxt_pf.x, &nxt.s0, &nxt.c0);
+            sincos_angle<FAST>(nxt_pf.y, &nxt.s1, &nxt.c1);
+            float2 th = own_pf;
+            if (r + 1 < R) {
+                const int m2 = m + 2 >= L ? m + 2 - L : m + 2;
+                nxt_pf = __ldg(reinterpret_cast<const float2*>(a.oth + (long long)m2 * W + k0));
+                own_pf = *reinterpret_cast<const float2*>(a.own + (long long)(m + 1) * W + k0);
+            }
+            // x neighbours of column 2q and 2q+1:
+            //   p = 0: (2q-1, 2q) and (2q, 2q+1);  p = 1: (2q, 2q+1) and (2q+1, 2q+2)
+            float ec, es;  // cos / sin of column 2q-1 (p = 0) or 2q+2 (p = 1)
+            if (p == 0) {
+                ec = __shfl_up_sync(0xffffffffu, cur.c1, 1);
+                es = __shfl_up_sync(0xffffffffu, cur.s1, 1);
+                if (lane == 0) {
+                    const float e = __ldg(a.oth + (long long)m * W + (k0 == 0 ? W - 1 : k0 - 1));
+                    sincos_angle<FAST>(e, &es, &ec);
+                }
+            } else {
+                ec = __shfl_down_sync(0xffffffffu, cur.c0, 1);
+                es = __shfl_down_sync(0xffffffffu, cur.s0, 1);
+                if (lane == 31) {
+                    const float e = __ldg(a.oth + (long long)m * W + (k0 + 2 == W ? 0 : k0 + 2));
+                    sincos_angle<FAST>(e, &es, &ec);
+                }
+            }
+            float hx0, hy0, hx1, hy1;
+            if (p == 0) {
+                hx0 = ec + cur.c0;
+                hy0 = es + cur.s0;
+                hx1 = cur.c0 + cur.c1;
+                hy1 = cur.s0 + cur.s1;
+            } else {
+                hx0 = cur.c0 + cur.c1;
+                hy0 = cur.s0 + cur.s1;
+                hx1 = cur.c1 + ec;
+                hy1 = cur.s1 + es;
+            }
+            hx0 = J * (hx0 + prev.c0 + nxt.c0);
+            hy0 = J * (hy0 + prev.s0 + nxt.s0);
+            hx1 = J * (hx1 + prev.c1 + nxt.c1);
+            hy1 = J * (hy1 + prev.s1 + nxt.s1);
+            float sx0, sy0, sx1, sy1;
+            sincos_angle<FAST>(th.x, &sy0, &sx0);
+            sincos_angle<FAST>(th.y, &sy1, &sx1);
+            if (a.update) {
+                const uint4 rnd = philox4x32_10(
+                    make_uint4((uint32_t)(j >> 1), t, a.replica, (kSweep << 1) | (uint32_t)a.c),
+                    a.rk);
+                const float n0 = kTwoPiF * u24(rnd.y), n1 = kTwoPiF * u24(rnd.w);
+                float nx0, ny0, nx1, ny1;
+                sincos_angle<FAST>(n0, &ny0, &nx0);
+                sincos_angle<FAST>(n1, &ny1, &nx1);
+                const float dE0 = -((nx0 - sx0) * hx0 + (ny0 - sy0) * hy0);
+                const float dE1 = -((nx1 - sx1) * hx1 + (ny1 - sy1) * hy1);
+                bool ch = false;
+                if (dE0 <= 0.f || u24(rnd.x) < boltzmann<FAST>(-a.beta * dE0)) {
+                    th.x = n0;
+                    sx0 = nx0;
+                    sy0 = ny0;
+                    ch = true;
+                }
+                if (dE1 <= 0.f || u24(rnd.z) < boltzmann<FAST>(-a.beta * dE1)) {
+                    th.y = n1;
+                    sx1 = nx1;
+                    sy1 = ny1;
+                    ch = true;
+                }
+                if (ch) *reinterpret_cast<float2*>(a.own + j) = th;
+            }
+            if (a.measure) {
+                pe -= sx0 * hx0 + sy0 * hy0 + sx1 * hx1 + sy1 * hy1;
+                pmx += sx0 + sx1 + cur.c0 + cur.c1;
+                pmy += sy0 + sy1 + cur.s0 + cur.s1;
+            }
+            prev = cur;
+            cur = nxt;
+        }
+    }
+    if (!a.measure) return;
+    Partial mine;
+    mine.i0 = mine.i1 = 0;
+    mine.f[0] = block_sum((double)pe, red);
+    mine.f[1] = block_sum((double)pmx, red);
+    mine.f[2] = block_sum((double)pmy, red);
+    mine.f[3] = 0.0;
+    finish_pass(a.ctrl, a.partials, mine, [&](const Partial& tot) { on_finish(a, tot); });
+}
+
 template <int NC>
 __global__ void on_init_kernel(float* s0, float* s1, long long H, uint32_t replica, RoundKeys rk)
 {
@@ -324,17 +607,53 @@ OnArgs make_args(const sl_lattice* h, int c)
     a.partials = h->partials;
     a.measure = c == 1;
     a.update = 1;
+    a.R = 1;
     a.renorm_every = h->renorm_every;
     return a;
 }
 
-template <int NC>
-cudaError_t launch_on(const sl_lattice* h, const OnArgs& a, cudaStream_t s)
+bool on_stream_ok(const sl_lattice* h)
 {
+    if (h->bonds[0][0] != nullptr || h->kernel == 1) return false;
+    if (h->n == 3) return h->W % 32 == 0;
+    return h->d == 2 && h->W % 64 == 0;
+}
+
+int on_rows(const sl_lattice* h, long long cols)
+{
+    if (h->rows > 0) return h->rows;
+    const long long cross = h->d == 3 ? h->L : 1;
+    int R = 32;
+    while (R > 1 && (h->L % R != 0 || cols * cross * (h->L / R) < 152LL * 1024)) R >>= 1;
+    return R;
+}
+
+template <int NC>
+cudaError_t launch_on(const sl_lattice* h, OnArgs a, cudaStream_t s)
+{
+    const bool fast = h->fast_math != 0;
+    if (on_stream_ok(h)) {
+        const long long cols = NC == 3 ? h->W : h->W / 2;
+        a.R = on_rows(h, cols);
+        const long long items = cols * (h->d == 3 ? h->L : 1) * (h->L / a.R);
+        const int grid = grid_for(items, 256);
+        if (NC == 3) {
+            if (h->d == 2) {
+                if (fast) heis_stream<2, true><<<grid, 256, 0, s>>>(a);
+                else heis_stream<2, false><<<grid, 256, 0, s>>>(a);
+            } else {
+                if (fast) heis_stream<3, true><<<grid, 256, 0, s>>>(a);
+                else heis_stream<3, false><<<grid, 256, 0, s>>>(a);
+            }
+        } else {
+            if (fast) xy_stream<true><<<grid, 256, 0, s>>>(a);
+            else xy_stream<false><<<grid, 256, 0, s>>>(a);
+        }
+        return cudaGetLastError();
+    }
     const long long rows = (long long)h->L * (h->d == 3 ? h->L : 1);
     int grid = (int)(rows < 152LL * 8 ? rows : 152LL * 8);
     if (grid > kMaxBlocks) grid = kMaxBlocks;
-    const bool fast = h->fast_math != 0;
     if (h->d == 2) {
         if (fast) on_generic<NC, 2, true><<<grid, 128, 0, s>>>(a);
         else on_generic<NC, 2, false><<<grid, 128, 0, s>>>(a);
@@ -402,7 +721,7 @@ cudaError_t on_measure(const sl_lattice* h, cudaStream_t s)
     a.measure = 1;
     memset(&a.rk, 0, sizeof a.rk);
     a.beta = 0.f;
-    return h->n == 2 ? launch_on<2>(h, a, s) : launch_on<3>(h, a, s);
+    return h->n == 2 ? launch_on<2>(h, a, s) : launch_on<3>(h, a, s);  // update = 0 is safe in both
 }
 
 }  // namespace spinmc

@@ -65,11 +65,13 @@ class Pair:
     2 (t' - t) + 2 are excluded from the component check."""
 
     def __init__(self, sm, n, d, L, beta, nsw, seed=3, sweep_seed=11, J=1.0, Jb=None, fast=0,
-                 renorm=16, tie_tol=TIE_TOL):
+                 renorm=16, tie_tol=TIE_TOL, kernel=0):
         N = L ** d
         s32 = start_state(n, d, L, seed)
         lat = sm.Lattice(d, L, n=n, J=J, J_bonds=Jb, seed=seed)
         lat.set_option(sm.SL_OPT_FAST_MATH, fast)
+        if kernel:
+            lat.set_option(sm.SL_OPT_KERNEL, kernel)
         if n == 3:
             lat.set_option(sm.SL_OPT_RENORM_EVERY, renorm)
         lat.set_spins(s32)
@@ -136,6 +138,21 @@ def test_start_configuration_matches_oracle(sm, n, d, L):
                                         (3, 3, 16, 0.693), (3, 2, 32, 1.5), (3, 3, 6, 0.3)])
 def test_parity_first_ten_sweeps(sm, n, d, L, beta):
     Pair(sm, n, d, L, beta, 10).check()
+
+
+@pytest.mark.parametrize("n,d,L,beta", [(3, 3, 64, 0.693), (3, 2, 64, 1.5), (2, 2, 128, 1.12),
+                                        (2, 2, 256, 0.9)])
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_streaming_and_generic_kernels(sm, n, d, L, beta, kernel):
+    """The row-streaming kernels (register window, warp shuffles) and the
+    per-site kernel both match the oracle on sizes the streaming kernels
+    accept; J = -0.8 checks the coupling sign."""
+    Pair(sm, n, d, L, beta, 6, kernel=kernel, J=-0.8 if L == 64 else 1.0).check()
+
+
+@pytest.mark.parametrize("n,d,L,beta", [(3, 3, 64, 0.693), (2, 2, 128, 1.12)])
+def test_streaming_fast_math(sm, n, d, L, beta):
+    Pair(sm, n, d, L, beta, 6, fast=1, tie_tol=TIE_TOL_FAST, kernel=2).check()
 
 
 @pytest.mark.parametrize("n", [2, 3])
