@@ -198,6 +198,57 @@ def time_sweeps(spinmc, wl, steps, warmup, replica, want_clocks, local):
     return ms, cl, e_last
 
 
+def batch_run(spinmc, nsamples=1024, ntemps=32, sweeps=100, plain_lattices=32, plain_sweeps=20):
+    """The batched Edwards-Anderson workload: nsamples 3D +-J samples of sides
+    [8,12,16,24,32][s mod 5], ntemps temperatures geometric in [0.5, 3],
+    exchange after every sweep, one run of `sweeps` sweeps timed with CUDA
+    events.  The plain comparison runs single lattices (the same couplings,
+    one sample x temperature per lattice) through sl_sweep one after another
+    for the same number of sweeps per lattice."""
+    import torch
+    from paper_1107_5463_gb300 import inputs
+    Ls = inputs.ea_sample_sizes(nsamples)
+    betas = inputs.geometric_betas(ntemps)
+    b = spinmc.Batch(3, Ls, ntemps, betas, seed=inputs.DEFAULT_SEED)
+    b.run(2, 1)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(b.stream)
+    b.run(sweeps, 7)
+    ev1.record(b.stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    flips = sum(L ** 3 for L in Ls) * ntemps * sweeps
+    # plain path: the samples of side 32, one lattice per (sample, temperature)
+    lats = []
+    s32 = [s for s, L in enumerate(Ls) if L == 32]
+    for q in range(plain_lattices):
+        s = s32[q // ntemps % len(s32)]
+        lat = spinmc.Lattice(3, 32, J_bonds=b.bonds(s), seed=inputs.DEFAULT_SEED,
+                             replica=s * ntemps + q % ntemps)
+        lats.append((lat, betas[q % ntemps]))
+    for lat, beta in lats:
+        lat.sweep(beta, 2, 7)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ev0.record(torch.cuda.current_stream())
+    for lat, beta in lats:
+        lat.sweep(beta, plain_sweeps, 7)
+    ev1.record(torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    pms = ev0.elapsed_time(ev1)
+    for lat, _ in lats:
+        lat.close()
+    b.close()
+    plain_flips = 32 ** 3 * plain_lattices * plain_sweeps
+    return {"value": flips / (ms * 1e6), "unit": UNIT, "ms": ms, "sweeps": sweeps,
+            "samples": nsamples, "temps": ntemps,
+            "plain_value": plain_flips / (pms * 1e6), "plain_sample":
+                "%d lattices of side 32 x %d sweeps each, sl_sweep per lattice" % (plain_lattices,
+                                                                               plain_sweeps),
+            "batched_over_plain": (flips / ms) / (plain_flips / pms)}
+
+
 def e2e_run(spinmc, wl, jobs, sweeps_per_job, replica):
     """End to end through the public API with host buffers: per job, upload
     the start configuration from pinned host memory, run the sweeps, read the
@@ -355,6 +406,7 @@ def main():
                 gbs = w["bytes"] * (n // 2) / (vms / (2 * k) * 1e-3) / 1e9
                 var[name] = {"value": n * k / (vms * 1e6), "unit": UNIT, "ms_per_step": vms / k,
                              "achieved_gbs": gbs, "hbm_frac": gbs / hbm}
+            var["ea3d_batch_1024x32"] = batch_run(spinmc)
             line["variants"] = var
         print(json.dumps(line), flush=True)
     barrier(world)

@@ -3,7 +3,10 @@
 // scheme of Table 1, "Metro. single": spins in single precision, aggregate
 // quantities such as the total energy in double precision).
 //
-//   XY (n = 2):          one FP32 angle per site, colour arrays theta[c][j];
+//   XY (n = 2):          one FP32 angle per site, colour arrays t[c][j] holding
+//                        the angle in turns (theta / 2 pi, in [0, 1)), so a
+//                        proposal u24 is stored exactly and cos / sin are
+//                        sincospi(2 t) without a large range reduction;
 //   Heisenberg (n = 3):  FP32 unit vectors, colour arrays of components
 //                        s[c][a*H + j] (structure of arrays).
 //
@@ -41,16 +44,17 @@ struct OnArgs {
 
 __device__ __forceinline__ float u24(uint32_t x) { return (float)(x >> 8) * (1.0f / 16777216.0f); }
 
+// sin and cos of an angle given in turns t in [0, 1)
 template <bool FAST>
-__device__ __forceinline__ void sincos_angle(float th, float* s, float* c)
+__device__ __forceinline__ void sincos_angle(float t, float* s, float* c)
 {
     if (FAST) {
-        // sin(th) = -sin(th - pi), cos(th) = -cos(th - pi); th - pi in [-pi, pi)
-        __sincosf(th - kPiF, s, c);
+        // sin(2 pi t) = -sin(2 pi t - pi), likewise cos; the argument is in [-pi, pi)
+        __sincosf(kTwoPiF * t - kPiF, s, c);
         *s = -*s;
         *c = -*c;
     } else {
-        sincosf(th, s, c);
+        sincospif(2.0f * t, s, c);
     }
 }
 
@@ -174,7 +178,7 @@ __global__ void __launch_bounds__(128) on_generic(const OnArgs a)
                     const uint32_t oa = (j & 1) ? r.z : r.x;
                     const uint32_t op = (j & 1) ? r.w : r.y;
                     u = u24(oa);
-                    nth = kTwoPiF * u24(op);
+                    nth = u24(op);
                     sincos_angle<FAST>(nth, &ny, &nx);
                 } else {
                     const uint4 r = philox4x32_10(
@@ -472,7 +476,7 @@ __global__ void __launch_bounds__(256) xy_stream(const OnArgs a)
                 const uint4 rnd = philox4x32_10(
                     make_uint4((uint32_t)(j >> 1), t, a.replica, (kSweep << 1) | (uint32_t)a.c),
                     a.rk);
-                const float n0 = kTwoPiF * u24(rnd.y), n1 = kTwoPiF * u24(rnd.w);
+                const float n0 = u24(rnd.y), n1 = u24(rnd.w);
                 float nx0, ny0, nx1, ny1;
                 sincos_angle<FAST>(n0, &ny0, &nx0);
                 sincos_angle<FAST>(n1, &ny1, &nx1);
@@ -523,7 +527,7 @@ __global__ void on_init_kernel(float* s0, float* s1, long long H, uint32_t repli
         if (NC == 2) {
             const uint4 r = philox4x32_10(
                 make_uint4((uint32_t)(j >> 1), 0u, replica, (kInit << 1) | (uint32_t)c), rk);
-            s[j] = kTwoPiF * u24((j & 1) ? r.w : r.y);
+            s[j] = u24((j & 1) ? r.w : r.y);
         } else {
             const uint4 r =
                 philox4x32_10(make_uint4((uint32_t)j, 0u, replica, (kInit << 1) | (uint32_t)c), rk);
@@ -552,8 +556,13 @@ __global__ void on_layout_kernel(float* s0, float* s1, float* nat, long long N, 
         float* s = colour_of(i, L) ? s1 : s0;
         const long long j = i >> 1;
         if (NC == 2) {
-            if (dir == 0) s[j] = nat[i];
-            else nat[i] = s[j];
+            // natural order holds radians, the colour arrays turns
+            if (dir == 0) {
+                const float tr = nat[i] * (1.0f / kTwoPiF);
+                s[j] = tr - floorf(tr);
+            } else {
+                nat[i] = kTwoPiF * s[j];
+            }
         } else {
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
