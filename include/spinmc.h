@@ -210,6 +210,27 @@ int sl_batch_sweeps_done(sl_batch* b, int64_t* sweeps_done);
 /* Release host metadata (and the buffer if library-owned); synchronises. */
 void sl_batch_destroy(sl_batch* b);
 
+/*
+ * sl_ising_measure_static — energy (Eq. 1 with J_ij = J) and magnetisation of
+ * an Ising configuration, without allocating any device memory.  The paper
+ * has no counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc, such as code running under another framework's device-memory
+ * pool (a raw allocation would bypass its accounting or budget) or a
+ * latency-critical loop that must not pay for an allocation.
+ *   dev_spins  device pointer, N = L^d int8 values +1 / -1 in natural order
+ *              (the layout sl_get_spins writes);
+ *   dev_out    device pointer to two doubles: E, then M = sum_i s_i;
+ *   stream     cudaStream_t (NULL = legacy default stream); asynchronous.
+ * Its reduction scratch is one static device array of about 192 KiB, held by
+ * every GPU that loads the library until the process exits; it serves at
+ * most 2^28 sites (larger lattices return SL_EINVAL).  The first call on a
+ * device looks up that array's device address with the device current, so
+ * make the first call before any stream capture.  All calls share the array:
+ * calls that overlap on the GPU race, calls in order on one stream do not.
+ */
+int sl_ising_measure_static(int d, int L, double J, const int8_t* dev_spins, double* dev_out,
+                            void* stream);
+
 /* sl_strerror — static text for a status code. */
 const char* sl_strerror(int status);
 

@@ -59,6 +59,7 @@ _sig("sl_batch_get", _int, _vp, _int, _int, _vp, ctypes.POINTER(_int))
 _sig("sl_batch_get_bonds", _int, _vp, _int, _vp)
 _sig("sl_batch_sweeps_done", _int, _vp, ctypes.POINTER(_i64))
 _sig("sl_batch_destroy", None, _vp)
+_sig("sl_ising_measure_static", _int, _int, _int, _dbl, _vp, _vp, _vp)
 _sig("sl_strerror", ctypes.c_char_p, _int)
 _sig("sl_last_error", _int, ctypes.c_char_p, _sz)
 
@@ -200,6 +201,13 @@ def sl_batch_sweeps_done(h):
 
 def sl_batch_destroy(h):
     _lib.sl_batch_destroy(h)
+
+
+def sl_ising_measure_static(d, L, J, dev_spins, dev_out, stream):
+    """Energy and magnetisation of a natural-order int8 configuration on the
+    device into dev_out[0:2], with no device allocation (see the header)."""
+    _check(_lib.sl_ising_measure_static(d, L, J, _addr(dev_spins), _addr(dev_out), stream),
+           "sl_ising_measure_static")
 
 
 # ------------------------------------------------- torch-backed helper ----
