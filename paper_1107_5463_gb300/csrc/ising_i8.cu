@@ -232,6 +232,13 @@ __global__ void __launch_bounds__(128) i8_stream(const I8Args a)
         uint4 A_nx = *reinterpret_cast<const uint4*>(a.own + off(yy0, zz0) + k0);
         uint32_t edge_nx =
             (uint8_t)a.oth[off(yy0, zz0) + edge_idx((yy0 + zz0 + a.c) & 1)];
+        // 3D: rows y -/+ 1 of the current plane, also one iteration ahead
+        const int y_m = y3 == 0 ? L - 1 : y3 - 1, y_p = y3 == L - 1 ? 0 : y3 + 1;
+        uint4 ym_nx = make_uint4(0, 0, 0, 0), yp_nx = ym_nx;
+        if (D == 3) {
+            ym_nx = ld_rows(a.oth + off(y_m, zz0) + k0);
+            yp_nx = ld_rows(a.oth + off(y_p, zz0) + k0);
+        }
         for (int r = 0; r < R; ++r) {
             const int m = m0 + r;
             int yy, zz;
@@ -242,6 +249,7 @@ __global__ void __launch_bounds__(128) i8_stream(const I8Args a)
             const uint4 A = A_nx;
             const uint32_t edge = edge_nx;
             const uint4 nxt = next;
+            const uint4 ym = ym_nx, yp = yp_nx;
             if (r + 1 < R) {
                 const int m1 = m + 1;
                 const int m2 = m1 == L - 1 ? 0 : m1 + 1;
@@ -250,15 +258,12 @@ __global__ void __launch_bounds__(128) i8_stream(const I8Args a)
                 next = ld_rows(a.oth + moff(m2) + k0);
                 A_nx = *reinterpret_cast<const uint4*>(a.own + off(y1, z1) + k0);
                 edge_nx = (uint8_t)a.oth[off(y1, z1) + edge_idx((y1 + z1 + a.c) & 1)];
+                if (D == 3) {
+                    ym_nx = ld_rows(a.oth + off(y_m, z1) + k0);
+                    yp_nx = ld_rows(a.oth + off(y_p, z1) + k0);
+                }
             }
             const uint4 S = shift_row(cur, edge, p);
-            uint4 ym = make_uint4(0, 0, 0, 0), yp = ym;
-            if (D == 3) {
-                const int ym_ = yy == 0 ? L - 1 : yy - 1;
-                const int yp_ = yy == L - 1 ? 0 : yy + 1;
-                ym = ld_rows(a.oth + off(ym_, zz) + k0);
-                yp = ld_rows(a.oth + off(yp_, zz) + k0);
-            }
             // couplings (0 = +1, 1 = -1): +x/+y/+z from own forward bonds; -x
             // from the other colour's x bonds (shifted when the -x neighbour is
             // column k-1); -y / -z from the other colour's rows behind.

@@ -275,7 +275,7 @@ __device__ __forceinline__ V3 shfl3_down(V3 v)
 }
 
 template <int D, bool FAST>
-__global__ void __launch_bounds__(256) heis_stream(const OnArgs a)
+__global__ void __launch_bounds__(256, 3) heis_stream(const OnArgs a)
 {
     __shared__ double red[32];
     const unsigned long long t64 = a.ctrl->t;
@@ -283,10 +283,23 @@ __global__ void __launch_bounds__(256) heis_stream(const OnArgs a)
     const bool renorm = a.update && a.renorm_every > 0 &&
                         (t64 + 1) % (unsigned long long)a.renorm_every == 0;
     const int L = a.L, W = a.W, R = a.R;
-    const long long H = a.H;
+    const long long H = a.H;  // < 2^31: every offset below fits in 32 bits
     const int lane = threadIdx.x & 31;
     const long long nitems = (long long)W * (D == 3 ? L : 1) * (L / R);
     const float J = a.J;
+    const float* ox = a.oth;
+    const float* oy = a.oth + H;
+    const float* oz = a.oth + 2 * H;
+    float* sx_ = a.own;
+    float* sy_ = a.own + H;
+    float* sz_ = a.own + 2 * H;
+    auto ld = [&](int i) -> V3 {
+        V3 v;
+        v.x = __ldg(ox + i);
+        v.y = __ldg(oy + i);
+        v.z = __ldg(oz + i);
+        return v;
+    };
     float pe = 0.f, pmx = 0.f, pmy = 0.f, pmz = 0.f;
     for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < nitems;
          it += (long long)gridDim.x * blockDim.x) {
@@ -294,43 +307,58 @@ __global__ void __launch_bounds__(256) heis_stream(const OnArgs a)
         const long long rest = it / W;
         const int y3 = D == 3 ? (int)(rest % L) : 0;
         const int m0 = (int)(D == 3 ? rest / L : rest) * R;
-        auto rowid = [&](int m) -> long long { return D == 3 ? (long long)m * L + y3 : m; };
+        // offset of the colour entry at column k of the row at march index m
+        // (2D: row y = m; 3D: row (y3, z = m)); rows y3 -/+ 1 in the same plane
+        auto off = [&](int m) -> int { return (D == 3 ? m * L + y3 : m) * W + k; };
+        const int dym = (y3 == 0 ? L - 1 : -1) * W, dyp = (y3 == L - 1 ? 1 - L : 1) * W;
         const int mprev = m0 == 0 ? L - 1 : m0 - 1;
-        V3 prev = ld3(a.oth, H, rowid(mprev) * W + k);
-        V3 cur = ld3(a.oth, H, rowid(m0) * W + k);
-        V3 nxt_pf = ld3(a.oth, H, rowid(m0 == L - 1 ? 0 : m0 + 1) * W + k);
-        V3 own_pf = ld3(a.own, H, rowid(m0) * W + k);
+        V3 prev = ld(off(mprev));
+        V3 cur = ld(off(m0));
+        V3 nxt_pf = ld(off(m0 == L - 1 ? 0 : m0 + 1));
+        V3 own_pf;
+        own_pf.x = sx_[off(m0)];
+        own_pf.y = sy_[off(m0)];
+        own_pf.z = sz_[off(m0)];
+        V3 ym_pf = prev, yp_pf = prev;
+        if (D == 3) {
+            ym_pf = ld(off(m0) + dym);
+            yp_pf = ld(off(m0) + dyp);
+        }
         for (int r = 0; r < R; ++r) {
             const int m = m0 + r;
-            const long long row = rowid(m);
             const int yy = D == 3 ? y3 : m, zz = D == 3 ? m : 0;
             const int p = (yy + zz + a.c) & 1;
-            const long long j = row * W + k;
+            const int j = off(m);
             const V3 nxt = nxt_pf;
+            const V3 vm = ym_pf, vp = yp_pf;
             V3 s = own_pf;
             if (r + 1 < R) {
                 const int m2 = m + 2 >= L ? m + 2 - L : m + 2;
-                nxt_pf = ld3(a.oth, H, rowid(m2) * W + k);
-                own_pf = ld3(a.own, H, rowid(m + 1) * W + k);
+                const int j1 = off(m + 1);
+                nxt_pf = ld(off(m2));
+                own_pf.x = sx_[j1];
+                own_pf.y = sy_[j1];
+                own_pf.z = sz_[j1];
+                if (D == 3) {
+                    ym_pf = ld(j1 + dym);
+                    yp_pf = ld(j1 + dyp);
+                }
             }
             // x neighbours: p = 0 -> (k-1, k), p = 1 -> (k, k+1)
             V3 xm, xp;
             if (p == 0) {
                 xm = shfl3_up(cur);
-                if (lane == 0) xm = ld3(a.oth, H, row * W + (k == 0 ? W - 1 : k - 1));
+                if (lane == 0) xm = ld(j - k + (k == 0 ? W - 1 : k - 1));
                 xp = cur;
             } else {
                 xm = cur;
                 xp = shfl3_down(cur);
-                if (lane == 31) xp = ld3(a.oth, H, row * W + (k == W - 1 ? 0 : k + 1));
+                if (lane == 31) xp = ld(j - k + (k == W - 1 ? 0 : k + 1));
             }
             float hx = xm.x + xp.x + prev.x + nxt.x;
             float hy = xm.y + xp.y + prev.y + nxt.y;
             float hz = xm.z + xp.z + prev.z + nxt.z;
             if (D == 3) {
-                const long long rym = (long long)m * L + (y3 == 0 ? L - 1 : y3 - 1);
-                const long long ryp = (long long)m * L + (y3 == L - 1 ? 0 : y3 + 1);
-                const V3 vm = ld3(a.oth, H, rym * W + k), vp = ld3(a.oth, H, ryp * W + k);
                 hx += vm.x + vp.x;
                 hy += vm.y + vp.y;
                 hz += vm.z + vp.z;
@@ -359,9 +387,9 @@ __global__ void __launch_bounds__(256) heis_stream(const OnArgs a)
                     changed = true;
                 }
                 if (changed) {
-                    a.own[j] = s.x;
-                    a.own[H + j] = s.y;
-                    a.own[2 * H + j] = s.z;
+                    sx_[j] = s.x;
+                    sy_[j] = s.y;
+                    sz_[j] = s.z;
                 }
             }
             if (a.measure) {
