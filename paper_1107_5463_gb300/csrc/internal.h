@@ -7,7 +7,7 @@
 #include <stddef.h>
 #include <stdint.h>
 
-#include "../../include/spinmc.h"
+#include "spinmc.h"
 #include "common.cuh"
 
 namespace spinmc {

@@ -324,6 +324,16 @@ __global__ void __launch_bounds__(256, 3) heis_stream(const OnArgs a)
             ym_pf = ld(off(m0) + dym);
             yp_pf = ld(off(m0) + dyp);
         }
+        // the x neighbour a warp-edge lane cannot get by shuffle: column k-1
+        // for lane 0 when p = 0, column k+1 for lane 31 when p = 1
+        const int kl = k == 0 ? W - 1 : k - 1, kr = k == W - 1 ? 0 : k + 1;
+        auto edge_of = [&](int m, int p) -> int { return off(m) - k + (p ? kr : kl); };
+        auto is_edge = [&](int p) -> bool { return p ? lane == 31 : lane == 0; };
+        V3 edge_pf = prev;
+        {
+            const int p0 = ((D == 3 ? y3 : m0) + (D == 3 ? m0 : 0) + a.c) & 1;
+            if (is_edge(p0)) edge_pf = ld(edge_of(m0, p0));
+        }
         for (int r = 0; r < R; ++r) {
             const int m = m0 + r;
             const int yy = D == 3 ? y3 : m, zz = D == 3 ? m : 0;
@@ -331,6 +341,7 @@ __global__ void __launch_bounds__(256, 3) heis_stream(const OnArgs a)
             const int j = off(m);
             const V3 nxt = nxt_pf;
             const V3 vm = ym_pf, vp = yp_pf;
+            const V3 edge = edge_pf;
             V3 s = own_pf;
             if (r + 1 < R) {
                 const int m2 = m + 2 >= L ? m + 2 - L : m + 2;
@@ -343,17 +354,19 @@ __global__ void __launch_bounds__(256, 3) heis_stream(const OnArgs a)
                     ym_pf = ld(j1 + dym);
                     yp_pf = ld(j1 + dyp);
                 }
+                const int p1 = p ^ 1;  // the parity alternates along the marching axis
+                if (is_edge(p1)) edge_pf = ld(edge_of(m + 1, p1));
             }
             // x neighbours: p = 0 -> (k-1, k), p = 1 -> (k, k+1)
             V3 xm, xp;
             if (p == 0) {
                 xm = shfl3_up(cur);
-                if (lane == 0) xm = ld(j - k + (k == 0 ? W - 1 : k - 1));
+                if (lane == 0) xm = edge;
                 xp = cur;
             } else {
                 xm = cur;
                 xp = shfl3_down(cur);
-                if (lane == 31) xp = ld(j - k + (k == W - 1 ? 0 : k + 1));
+                if (lane == 31) xp = edge;
             }
             float hx = xm.x + xp.x + prev.x + nxt.x;
             float hy = xm.y + xp.y + prev.y + nxt.y;
@@ -450,6 +463,15 @@ __global__ void __launch_bounds__(256) xy_stream(const OnArgs a)
         float2 nxt_pf = __ldg(reinterpret_cast<const float2*>(
             a.oth + (long long)(m0 == L - 1 ? 0 : m0 + 1) * W + k0));
         float2 own_pf = *reinterpret_cast<const float2*>(a.own + (long long)m0 * W + k0);
+        // angle of the x neighbour a warp-edge lane cannot get by shuffle:
+        // column 2q-1 for lane 0 when p = 0, column 2q+2 for lane 31 when p = 1
+        const int kl = k0 == 0 ? W - 1 : k0 - 1, kr = k0 + 2 == W ? 0 : k0 + 2;
+        float edge_pf = 0.f;
+        {
+            const int p0 = (m0 + a.c) & 1;
+            if (p0 ? lane == 31 : lane == 0)
+                edge_pf = __ldg(a.oth + (long long)m0 * W + (p0 ? kr : kl));
+        }
         for (int r = 0; r < R; ++r) {
             const int m = m0 + r;
             const int p = (m + a.c) & 1;
@@ -458,10 +480,14 @@ __global__ void __launch_bounds__(256) xy_stream(const OnArgs a)
             sincos_angle<FAST>(nxt_pf.x, &nxt.s0, &nxt.c0);
             sincos_angle<FAST>(nxt_pf.y, &nxt.s1, &nxt.c1);
             float2 th = own_pf;
+            const float edge = edge_pf;
             if (r + 1 < R) {
                 const int m2 = m + 2 >= L ? m + 2 - L : m + 2;
                 nxt_pf = __ldg(reinterpret_cast<const float2*>(a.oth + (long long)m2 * W + k0));
                 own_pf = *reinterpret_cast<const float2*>(a.own + (long long)(m + 1) * W + k0);
+                const int p1 = p ^ 1;
+                if (p1 ? lane == 31 : lane == 0)
+                    edge_pf = __ldg(a.oth + (long long)(m + 1) * W + (p1 ? kr : kl));
             }
             // x neighbours of column 2q and 2q+1:
             //   p = 0: (2q-1, 2q) and (2q, 2q+1);  p = 1: (2q, 2q+1) and (2q+1, 2q+2)
@@ -469,17 +495,11 @@ __global__ void __launch_bounds__(256) xy_stream(const OnArgs a)
             if (p == 0) {
                 ec = __shfl_up_sync(0xffffffffu, cur.c1, 1);
                 es = __shfl_up_sync(0xffffffffu, cur.s1, 1);
-                if (lane == 0) {
-                    const float e = __ldg(a.oth + (long long)m * W + (k0 == 0 ? W - 1 : k0 - 1));
-                    sincos_angle<FAST>(e, &es, &ec);
-                }
+                if (lane == 0) sincos_angle<FAST>(edge, &es, &ec);
             } else {
                 ec = __shfl_down_sync(0xffffffffu, cur.c0, 1);
                 es = __shfl_down_sync(0xffffffffu, cur.s0, 1);
-                if (lane == 31) {
-                    const float e = __ldg(a.oth + (long long)m * W + (k0 + 2 == W ? 0 : k0 + 2));
-                    sincos_angle<FAST>(e, &es, &ec);
-                }
+                if (lane == 31) sincos_angle<FAST>(edge, &es, &ec);
             }
             float hx0, hy0, hx1, hy1;
             if (p == 0) {
