@@ -153,6 +153,13 @@ def dist_setup():
     return world, rank, local
 
 
+def dist_teardown(world):
+    if world > 1:
+        import torch.distributed as dist
+        if dist.is_initialized():
+            dist.destroy_process_group()
+
+
 def barrier(world):
     if world > 1:
         import torch.distributed as dist
@@ -351,6 +358,7 @@ def main():
     world, rank, local = dist_setup()
     if args.impl == "reference":
         reference_arm(args, world, rank)
+        dist_teardown(world)
         return
 
     import __graft_entry__
@@ -410,6 +418,7 @@ def main():
             line["variants"] = var
         print(json.dumps(line), flush=True)
     barrier(world)
+    dist_teardown(world)
 
 
 if __name__ == "__main__":
