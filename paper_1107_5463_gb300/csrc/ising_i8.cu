@@ -454,9 +454,12 @@ bool stream_ok(const sl_lattice* h)
 int pick_rows(const sl_lattice* h)
 {
     if (h->rows > 0) return h->rows;
+    // measured on GB300: 16 rows per thread for 2D, 32 for 3D (the 3D pass
+    // keeps two more row windows per thread); fewer rows only when the grid
+    // would not fill the GPU
     const long long W16 = h->W / 16;
     const long long cross = h->d == 3 ? h->L : 1;
-    int R = 32;
+    int R = h->d == 3 ? 32 : 16;
     while (R > 1 && (h->L % R != 0 || W16 * cross * (h->L / R) < 152LL * 512)) R >>= 1;
     return R;
 }
