@@ -82,19 +82,39 @@ __global__ void __launch_bounds__(128) bits_stream(const BitArgs a)
         uint32_t prev = __ldg(a.oth + mrow(mprev) * WW + w);
         uint32_t cur = __ldg(a.oth + mrow(m0) * WW + w);
         const int wl = w == 0 ? WW - 1 : w - 1, wr = w == WW - 1 ? 0 : w + 1;
+        const int y_m = y3 == 0 ? L - 1 : y3 - 1, y_p = y3 == L - 1 ? 0 : y3 + 1;
         uint32_t i_na = 0, i_flip = 0, i_flipna = 0, i_down = 0;
+        // software pipeline: the next row of the other colour, the own word,
+        // the x-neighbour word and (3D) the y -/+ 1 words are loaded one row ahead
+        auto rowof = [&](int m) -> long long { return D == 3 ? row(y3, m) : row(m, 0); };
+        auto par = [&](int m) -> int { return ((D == 3 ? y3 + m : m) + a.c) & 1; };
+        uint32_t next_nx = __ldg(a.oth + mrow(m0 == L - 1 ? 0 : m0 + 1) * WW + w);
+        uint32_t A_nx = a.own[rowof(m0) * WW + w];
+        uint32_t hw_nx = __ldg(a.oth + rowof(m0) * WW + (par(m0) ? wr : wl));
+        uint32_t ym_nx = 0, yp_nx = 0;
+        if (D == 3) {
+            ym_nx = __ldg(a.oth + row(y_m, m0) * WW + w);
+            yp_nx = __ldg(a.oth + row(y_p, m0) * WW + w);
+        }
         for (int r = 0; r < R; ++r) {
             const int m = m0 + r;
-            const int mnext = m == L - 1 ? 0 : m + 1;
-            const uint32_t next = __ldg(a.oth + mrow(mnext) * WW + w);
             const int yy = D == 3 ? y3 : m;
             const int zz = D == 3 ? m : 0;
             const int p = (yy + zz + a.c) & 1;
             const long long rr = row(yy, zz);
-            const uint32_t A = a.own[rr * WW + w];
+            const uint32_t next = next_nx, A = A_nx, hw = hw_nx, ym = ym_nx, yp = yp_nx;
+            if (r + 1 < R) {
+                const int m1 = m + 1, m2 = m1 == L - 1 ? 0 : m1 + 1;
+                next_nx = __ldg(a.oth + mrow(m2) * WW + w);
+                A_nx = a.own[rowof(m1) * WW + w];
+                hw_nx = __ldg(a.oth + rowof(m1) * WW + (par(m1) ? wr : wl));
+                if (D == 3) {
+                    ym_nx = __ldg(a.oth + row(y_m, m1) * WW + w);
+                    yp_nx = __ldg(a.oth + row(y_p, m1) * WW + w);
+                }
+            }
             // -x / +x neighbours of column k are other-colour columns
             // k-1 / k (p = 0) or k / k+1 (p = 1)
-            const uint32_t hw = __ldg(a.oth + rr * WW + (p ? wr : wl));
             const uint32_t S = p ? __funnelshift_r(cur, hw, 1) : __funnelshift_l(hw, cur, 1);
             uint32_t b0, b1, b2;
             if (D == 2) {
@@ -106,10 +126,6 @@ __global__ void __launch_bounds__(128) bits_stream(const BitArgs a)
                 b1 = c1 ^ k;
                 b2 = c1 & k;
             } else {
-                const int ym_ = yy == 0 ? L - 1 : yy - 1;
-                const int yp_ = yy == L - 1 ? 0 : yy + 1;
-                const uint32_t ym = __ldg(a.oth + row(ym_, zz) * WW + w);
-                const uint32_t yp = __ldg(a.oth + row(yp_, zz) * WW + w);
                 uint32_t s1, c1, s2, c2;
                 fadd(A ^ S ^ inv, A ^ cur ^ inv, A ^ prev ^ inv, s1, c1);
                 fadd(A ^ next ^ inv, A ^ ym ^ inv, A ^ yp ^ inv, s2, c2);
