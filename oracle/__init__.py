@@ -39,6 +39,7 @@ def lib():
                                         ctypes.POINTER(_dbl), ctypes.POINTER(_dbl)]
         L.orc_ising_sweeps.argtypes = [_int, _int, _dbl, _vp, _dbl, _u64, _u32, _i64, _i64,
                                        _i8p, _vp, _vp]
+        L.orc_ising_heatbath_sweeps.argtypes = L.orc_ising_sweeps.argtypes
         L.orc_xy_init.argtypes = [_int, _int, _u64, _u32, _f64p]
         L.orc_heis_init.argtypes = [_int, _int, _u64, _u32, _f64p]
         L.orc_xy_measure.argtypes = [_int, _int, _dbl, _vp, _f64p, ctypes.POINTER(_dbl), _f64p]
@@ -119,6 +120,18 @@ def ising_sweeps(d, L, s, beta, seed, t0, nsweeps, J=1.0, Jb=None, replica=0, se
     m = np.empty(nsweeps) if series else None
     lib().orc_ising_sweeps(d, L, J, _ptr(jb), beta, seed, replica, t0, nsweeps, s,
                            _ptr(E), _ptr(m))
+    return E, m
+
+
+def ising_heatbath_sweeps(d, L, s, beta, seed, t0, nsweeps, J=1.0, Jb=None, replica=0,
+                          series=True):
+    """Heat-bath sweeps in place on s; return (E[nsweeps], |m|[nsweeps])."""
+    assert s.dtype == np.int8 and s.flags.c_contiguous
+    jb = _bonds_i8(Jb, d, L)
+    E = np.empty(nsweeps) if series else None
+    m = np.empty(nsweeps) if series else None
+    lib().orc_ising_heatbath_sweeps(d, L, J, _ptr(jb), beta, seed, replica, t0, nsweeps, s,
+                                    _ptr(E), _ptr(m))
     return E, m
 
 

@@ -80,9 +80,40 @@ static int ising_accept(const orc_geom* g, double J, const int8_t* Jb, double be
     return (double)u < exp(-beta * dE) * 4294967296.0;
 }
 
+/* sum_k Jb_k s_k over the 2d neighbours of the site at coordinates x */
+static int ising_field(const orc_geom* g, const int8_t* Jb, const int8_t* s, const int x[3],
+                       int64_t i)
+{
+    int hsum = 0;
+    for (int k = 0; k < 2 * g->d; ++k) {
+        int64_t nb = orc_neighbour_at(g, x, k);
+        int jb = Jb ? Jb[(int64_t)(k >> 1) * g->N + orc_bond_owner_at(g, x, i, k)] : 1;
+        hsum += jb * s[nb];
+    }
+    return hsum;
+}
+
+static void ising_sweeps_rule(int d, int L, double J, const int8_t* Jb, double beta,
+                              uint64_t seed, uint32_t replica, int64_t t0, int64_t nsweeps,
+                              int8_t* s, double* E_out, double* absm_out, int heatbath);
+
 void orc_ising_sweeps(int d, int L, double J, const int8_t* Jb, double beta,
                       uint64_t seed, uint32_t replica, int64_t t0, int64_t nsweeps,
                       int8_t* s, double* E_out, double* absm_out)
+{
+    ising_sweeps_rule(d, L, J, Jb, beta, seed, replica, t0, nsweeps, s, E_out, absm_out, 0);
+}
+
+void orc_ising_heatbath_sweeps(int d, int L, double J, const int8_t* Jb, double beta,
+                               uint64_t seed, uint32_t replica, int64_t t0, int64_t nsweeps,
+                               int8_t* s, double* E_out, double* absm_out)
+{
+    ising_sweeps_rule(d, L, J, Jb, beta, seed, replica, t0, nsweeps, s, E_out, absm_out, 1);
+}
+
+static void ising_sweeps_rule(int d, int L, double J, const int8_t* Jb, double beta,
+                              uint64_t seed, uint32_t replica, int64_t t0, int64_t nsweeps,
+                              int8_t* s, double* E_out, double* absm_out, int heatbath)
 {
     orc_geom g = orc_make_geom(d, L);
     const uint32_t key[2] = {orc_key_lo(seed), orc_key_hi(seed)};
@@ -104,8 +135,14 @@ void orc_ising_sweeps(int d, int L, double J, const int8_t* Jb, double beta,
                                                (uint32_t)(ORC_SWEEP << 1 | c)};
                             orc_philox4x32_10(ctr, key, out);
                         }
-                        if (ising_accept(&g, J, Jb, beta, s, xyz, i, out[j & 3]))
+                        if (heatbath) {
+                            /* P(s_i = +1) = 1 / (1 + exp(-2 beta J h)) */
+                            double a = 2.0 * J * (double)ising_field(&g, Jb, s, xyz, i);
+                            double x = 4294967296.0 / (1.0 + exp(-beta * a));
+                            s[i] = (double)out[j & 3] < x ? 1 : -1;
+                        } else if (ising_accept(&g, J, Jb, beta, s, xyz, i, out[j & 3])) {
                             s[i] = (int8_t)-s[i];
+                        }
                     }
         }
         if (E_out || absm_out) {

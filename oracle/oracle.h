@@ -63,6 +63,14 @@ void orc_ising_sweeps(int d, int L, double J, const int8_t* Jb, double beta,
                       uint64_t seed, uint32_t replica, int64_t t0, int64_t nsweeps,
                       int8_t* s, double* E_out, double* absm_out);
 
+/* Heat-bath sweeps (Section 2: the heat-bath prescription as the alternative
+ * local update).  Same arguments, random stream and measurement as
+ * orc_ising_sweeps; each visited spin is drawn afresh from its conditional
+ * law: s_i = +1 iff u < 2^32 / (1 + exp(-beta a)), a = 2 J sum_k Jb_k s_k. */
+void orc_ising_heatbath_sweeps(int d, int L, double J, const int8_t* Jb, double beta,
+                               uint64_t seed, uint32_t replica, int64_t t0, int64_t nsweeps,
+                               int8_t* s, double* E_out, double* absm_out);
+
 /* ---- O(n) models with continuous spins, n = 2 (XY), n = 3 (Heisenberg) ---
  * XY spins are angles theta (s = (cos theta, sin theta)); Heisenberg spins
  * are unit vectors stored as s[3*i + a].  All arithmetic is FP64. */

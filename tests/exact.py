@@ -74,11 +74,14 @@ def colour_of_site(d, L):
     return c & 1
 
 
-def exact_sweep_matrix(d, L, beta, J=1.0, Jb=None):
+def exact_sweep_matrix(d, L, beta, J=1.0, Jb=None, heatbath=False):
     """Exact transition matrix of one checkerboard sweep (colour 0 then 1).
 
-    Within a half-sweep the sites of one colour flip independently, each with
-    probability min(1, exp(-beta dE)), dE taken from the full Hamiltonian."""
+    Within a half-sweep the sites of one colour are updated independently:
+    Metropolis flips each with probability min(1, exp(-beta dE)); heat-bath
+    sets each to its flipped value with probability
+    exp(-beta E') / (exp(-beta E) + exp(-beta E')), energies E (current) and
+    E' (flipped) taken from the full Hamiltonian."""
     N = L ** d
     S = all_states(N)
     E = roll_energy(S, d, L, J, Jb).astype(np.float64)
@@ -95,7 +98,10 @@ def exact_sweep_matrix(d, L, beta, J=1.0, Jb=None):
                 s2 = S[a].copy()
                 s2[i] = -s2[i]
                 dE = E[index[tuple(s2)]] - E[a]
-                pflip.append(1.0 if dE <= 0 else math.exp(-beta * dE))
+                if heatbath:
+                    pflip.append(1.0 / (1.0 + math.exp(beta * dE)))
+                else:
+                    pflip.append(1.0 if dE <= 0 else math.exp(-beta * dE))
             for flips in itertools.product((0, 1), repeat=len(sites)):
                 s2 = S[a].copy()
                 prob = 1.0

@@ -343,3 +343,61 @@ def test_exchange_keeps_canonical_energies_on_L2_sample():
         ex = exact.enumerate_ising(d, L, b, Jb=jb.astype(np.int64))
         mean, err = exact.binned_mean(E[1000:, k], 40)
         assert abs(mean - ex["E"]) < 3 * err, (k, mean, ex["E"], err)
+
+
+# ------------------------------------------------------------ heat-bath --
+
+@pytest.mark.parametrize("d,beta", [(2, 0.15), (2, 0.6)])
+def test_heatbath_transition_matrix_on_L2(d, beta):
+    """Exact one-sweep matrix of the heat-bath rule (each site of a colour set
+    to its flipped value with probability e^{-beta E'}/(e^{-beta E}+e^{-beta
+    E'}), energies from Eq. 1) against the oracle's empirical transitions;
+    the Boltzmann law is stationary and each half-sweep is reversible."""
+    L = 2
+    T0, T1, S, E = exact.exact_sweep_matrix(d, L, beta, heatbath=True)
+    pi = np.exp(-beta * E)
+    pi /= pi.sum()
+    for T in (T0, T1):
+        np.testing.assert_allclose(pi[:, None] * T, (pi[:, None] * T).T, atol=1e-14)
+    T = T0 @ T1
+    np.testing.assert_allclose(pi @ T, pi, atol=1e-14)
+    M0, M1, _, _ = exact.exact_sweep_matrix(d, L, beta)
+    assert np.abs(T - M0 @ M1).max() > 1e-3  # a different chain from Metropolis
+    index = {tuple(s): k for k, s in enumerate(S)}
+    counts = np.zeros((len(S), len(S)))
+    for a in range(len(S)):
+        for r in range(3000):
+            s = S[a].copy()
+            oracle.ising_heatbath_sweeps(d, L, s, beta, 4321, r, 1, series=False)
+            counts[a, index[tuple(s)]] += 1
+    assert _chi2_rows(counts, T, range(len(S))) > 1e-4
+
+
+def test_heatbath_4x4_equilibrium_matches_enumeration():
+    ex = exact.enumerate_ising(2, 4, BETA_C)
+    s = oracle.ising_init(2, 4, 7)
+    E, m = oracle.ising_heatbath_sweeps(2, 4, s, BETA_C, 8, 0, 200_000)
+    E, m = E[1000:], m[1000:]
+    for obs, ref in ((E, ex["E"]), (E * E, ex["E2"]), (m, ex["absm"])):
+        mean, err = exact.binned_mean(obs, 40)
+        assert abs(mean - ref) < 3 * err, (mean, ref, err)
+
+
+def test_heatbath_two_spin_bond_and_beta_zero():
+    """One bond: <s0 s1> = tanh(beta J).  beta = 0: every spin is +1 exactly
+    when its Philox output is below 2^31, independent of the old state."""
+    d, L = 2, 4
+    jb = inputs.two_spin_bonds(d, L, 0, 0)
+    s = oracle.ising_init(d, L, 5)
+    E, _ = oracle.ising_heatbath_sweeps(d, L, s, 0.9, 6, 0, 40_000, Jb=jb)
+    mean, err = exact.binned_mean(-E[100:], 40)
+    assert abs(mean - math.tanh(0.9)) < 3 * err
+    seed, t = 31, 4
+    s = inputs.ising_spins(d, L, 3)
+    oracle.ising_heatbath_sweeps(d, L, s, 0.0, seed, t, 1, series=False)
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    colour = exact.colour_of_site(d, L)
+    for i in range(L ** d):
+        j = i >> 1
+        out = oracle.philox4x32_10([j >> 2, t, 0, int(colour[i])], key)
+        assert s[i] == (1 if int(out[j & 3]) < 2**31 else -1)
