@@ -38,6 +38,9 @@ WORKLOADS = {
     "ising3d_L512_i8": dict(d=3, L=512, n=1, beta=0.2216546, storage="i8", bytes=3.0,
                             desc="3D Ising ferromagnet J=1, L=512 simple cubic, int8 spins, "
                                  "beta=0.2216546, random start"),
+    "ising2d_L16384_i8_heatbath": dict(d=2, L=16384, n=1, beta=0.440687, storage="i8",
+                                       bytes=3.0, update=1,
+                                       desc="2D Ising, L=16384, int8 spins, heat-bath rule"),
     "ising2d_L16384_bits": dict(d=2, L=16384, n=1, beta=0.440687, storage="bits", bytes=0.375,
                                 desc="2D Ising, L=16384, one bit per spin"),
     "ising3d_L512_bits": dict(d=3, L=512, n=1, beta=0.2216546, storage="bits", bytes=0.375,
@@ -220,6 +223,8 @@ def time_sweeps(spinmc, wl, steps, warmup, replica, want_clocks, local):
     storage = spinmc.SL_STORE_BITS if wl["storage"] == "bits" else None
     lat = spinmc.Lattice(wl["d"], wl["L"], n=wl["n"], seed=inputs.DEFAULT_SEED, replica=replica,
                          storage=storage)
+    if wl.get("update"):
+        lat.set_option(spinmc.SL_OPT_UPDATE, wl["update"])
     E = torch.empty(max(steps, warmup, 1), dtype=torch.float64, device="cuda")
     m = torch.empty_like(E)
     spinmc.sl_sweep_series(lat.h, wl["beta"], warmup, inputs.DEFAULT_SEED, E, m)

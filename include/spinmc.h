@@ -75,6 +75,8 @@ extern "C" {
 #define SL_OPT_KERNEL 3        /* 0 = automatic, 1 = generic per-site kernel, 2 = row-streaming kernel */
 #define SL_OPT_ROWS 4          /* rows each thread marches through in the streaming kernel */
 #define SL_OPT_GRAPH 5         /* 1 = replay sweeps through CUDA graphs (default), 0 = plain launches */
+#define SL_OPT_UPDATE 6        /* 0 = Metropolis (Eq. 2, default); 1 = heat-bath (Ising, byte
+                                  storage): s_i = +1 iff u < 2^32 / (1 + exp(-2 beta J h_i)) */
 
 typedef struct sl_lattice sl_lattice;
 

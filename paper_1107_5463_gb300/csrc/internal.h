@@ -23,6 +23,8 @@ struct IsingTable {
     int ncmp;      // number of classes with dE > 0 (d, or 2d when bonds may be zero)
     int scheme;    // 0: class = unsatisfied bonds (couplings +-1); 1: class = 2d - e
     int sigma_neg; // the scalar J is negative
+    int heatbath;  // 1: heat-bath rule with the thresholds hb[h + 2d], h = sum_k Jb_k s_k
+    uint32_t hb[13];
 };
 
 // Per-sweep parameters common to every model.
@@ -55,7 +57,7 @@ struct sl_lattice {
     spinmc::Partial* partials;
     bool bonds_have_zero;
     // options
-    int renorm_every, fast_math, kernel, rows, use_graph;
+    int renorm_every, fast_math, kernel, rows, use_graph, update;
     // cached graph of kGraphSweeps sweeps
     cudaGraphExec_t graph;
     int graph_sweeps;

@@ -118,7 +118,13 @@ __global__ void __launch_bounds__(256) i8_generic(const I8Args a)
             }
             int s = spin_value(a.own[j]);
             int sh = s * hs;
-            if (a.update) {
+            if (a.update && a.tab.heatbath) {
+                // heat-bath: the new spin from its conditional law alone
+                const int snew = rr[b] <= a.tab.hb[hs + 2 * D] ? 1 : -1;
+                if (snew != s) a.own[j] = (int8_t)(snew < 0);
+                s = snew;
+                sh = s * hs;
+            } else if (a.update) {
                 const int e = a.tab.sigma_neg ? -sh : sh;
                 const int gcls = a.tab.scheme ? (2 * D - e) : ((2 * D - e) >> 1);
                 if (gcls >= q_of(rr[b], a.tab)) {
@@ -187,10 +193,15 @@ __device__ __forceinline__ uint32_t q_bias(const uint4& r, const IsingTable& tab
     return acc;
 }
 
-template <int D, int BONDS, int JNEG>
+template <int D, int BONDS, int JNEG, int HB>
 __global__ void __launch_bounds__(128) i8_stream(const I8Args a)
 {
     __shared__ long long red[32];
+    __shared__ uint32_t s_hb[16];  // heat-bath thresholds by h + 2d
+    if (HB) {
+        if (threadIdx.x < 13) s_hb[threadIdx.x] = a.tab.hb[threadIdx.x];
+        __syncthreads();
+    }
     const uint32_t t = (uint32_t)a.ctrl->t;
     const int W = a.W, L = a.L, R = a.R;
     const int W16 = W >> 4;
@@ -292,6 +303,42 @@ __global__ void __launch_bounds__(128) i8_stream(const I8Args a)
                 const uint32_t nxm = p ? w_of(cur, k) : w_of(S, k);
                 const uint32_t nxp = p ? w_of(S, k) : w_of(cur, k);
                 uint32_t na;  // unsatisfied bonds per byte (ferromagnetic sense)
+                if (HB) {
+                    // heat-bath: na = neighbours with Jb_k s_k = -1, so h = 2d - 2 na;
+                    // the new spin is down iff u > hb[h + 2d]
+                    if (!BONDS) {
+                        na = nxm + nxp + w_of(prev, k) + w_of(nxt, k);
+                        if (D == 3) na += w_of(ym, k) + w_of(yp, k);
+                    } else {
+                        na = (nxm ^ w_of(jx_oth, k)) + (nxp ^ w_of(jx_own, k));
+                        if (D == 2) {
+                            na += (w_of(prev, k) ^ w_of(jy_oth, k)) + (w_of(nxt, k) ^ w_of(jy_own, k));
+                        } else {
+                            na += (w_of(ym, k) ^ w_of(jy_oth, k)) + (w_of(yp, k) ^ w_of(jy_own, k)) +
+                                  (w_of(prev, k) ^ w_of(jz_oth, k)) + (w_of(nxt, k) ^ w_of(jz_own, k));
+                        }
+                    }
+                    const uint4 rnd = philox4x32_10(make_uint4(g0 + k, t, a.replica, ctr_w), a.rk);
+                    const uint32_t u[4] = {rnd.x, rnd.y, rnd.z, rnd.w};
+                    uint32_t down_new = 0;
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        const uint32_t nb = (na >> (8 * b)) & 0xFFu;
+                        if (u[b] > s_hb[4 * D - 2 * nb]) down_new |= 1u << (8 * b);
+                    }
+                    // after the update na' = na + new_down (2d - 2 na), as for a flip
+                    if (k == 0) Anew.x = down_new;
+                    else if (k == 1) Anew.y = down_new;
+                    else if (k == 2) Anew.z = down_new;
+                    else Anew.w = down_new;
+                    if (a.measure) {
+                        i_na = __dp4a(na, ones, i_na);
+                        i_flip = __dp4a(down_new, ones, i_flip);
+                        i_flipna = __dp4a(down_new, na, i_flipna);
+                        i_down = __dp4a(down_new, ones, __dp4a(w_of(cur, k), ones, i_down));
+                    }
+                    continue;
+                }
                 if (!BONDS) {
                     uint32_t nd = nxm + nxp + w_of(prev, k) + w_of(nxt, k);
                     if (D == 3) nd += w_of(ym, k) + w_of(yp, k);
@@ -343,7 +390,7 @@ __global__ void __launch_bounds__(128) i8_stream(const I8Args a)
     // na' = na + flip (2d - 2 na)
     const long long na_after = (long long)s_na + 2 * D * (long long)s_flip - 2 * (long long)s_flipna;
     long long bond = (long long)(2 * D) * (long long)nsite - 2 * na_after;
-    if (JNEG) bond = -bond;
+    if (JNEG && !HB) bond = -bond;
     Partial mine;
     mine.i0 = block_sum(bond, red);
     mine.i1 = block_sum((long long)down, red);
@@ -472,13 +519,19 @@ cudaError_t launch_pass(const sl_lattice* h, I8Args a, cudaStream_t s, bool stre
         const int grid = grid_for(items, 128);
         const bool bonds = a.Jown[0] != nullptr;
         const bool jneg = a.tab.sigma_neg != 0;
-#define SPINMC_LAUNCH(D, B, N) i8_stream<D, B, N><<<grid, 128, 0, s>>>(a)
-        if (h->d == 2) {
-            if (bonds) { if (jneg) SPINMC_LAUNCH(2, 1, 1); else SPINMC_LAUNCH(2, 1, 0); }
-            else { if (jneg) SPINMC_LAUNCH(2, 0, 1); else SPINMC_LAUNCH(2, 0, 0); }
+#define SPINMC_LAUNCH(D, B, N, HB) i8_stream<D, B, N, HB><<<grid, 128, 0, s>>>(a)
+        if (a.tab.heatbath && a.update) {
+            if (h->d == 2) {
+                if (bonds) SPINMC_LAUNCH(2, 1, 0, 1); else SPINMC_LAUNCH(2, 0, 0, 1);
+            } else {
+                if (bonds) SPINMC_LAUNCH(3, 1, 0, 1); else SPINMC_LAUNCH(3, 0, 0, 1);
+            }
+        } else if (h->d == 2) {
+            if (bonds) { if (jneg) SPINMC_LAUNCH(2, 1, 1, 0); else SPINMC_LAUNCH(2, 1, 0, 0); }
+            else { if (jneg) SPINMC_LAUNCH(2, 0, 1, 0); else SPINMC_LAUNCH(2, 0, 0, 0); }
         } else {
-            if (bonds) { if (jneg) SPINMC_LAUNCH(3, 1, 1); else SPINMC_LAUNCH(3, 1, 0); }
-            else { if (jneg) SPINMC_LAUNCH(3, 0, 1); else SPINMC_LAUNCH(3, 0, 0); }
+            if (bonds) { if (jneg) SPINMC_LAUNCH(3, 1, 1, 0); else SPINMC_LAUNCH(3, 1, 0, 0); }
+            else { if (jneg) SPINMC_LAUNCH(3, 0, 1, 0); else SPINMC_LAUNCH(3, 0, 0, 0); }
         }
 #undef SPINMC_LAUNCH
     } else {

@@ -126,7 +126,23 @@ int ising_table(const sl_lattice* h, double beta, IsingTable* tab)
     tab->sigma_neg = h->J < 0.0;
     tab->scheme = h->bonds_have_zero ? 1 : 0;
     tab->ncmp = tab->scheme ? 2 * d : d;
+    tab->heatbath = h->update;
     for (int k = 0; k < 6; ++k) tab->thr[k] = 0xFFFFFFFFu;
+    for (int k = 0; k < 13; ++k) tab->hb[k] = 0u;
+    if (h->update == 1) {
+        // heat-bath: s_i = +1 iff u < 2^32 / (1 + exp(-beta a)), a = 2 J h,
+        // h = sum_k Jb_k s_k in [-2d, 2d]; u <= ceil(x) - 1 is the same test
+        for (int hs = -2 * d; hs <= 2 * d; ++hs) {
+            const double a = 2.0 * h->J * (double)hs;
+            const double x = 4294967296.0 / (1.0 + std::exp(-beta * a));
+            if (!(x > 0.0))
+                return fail(SL_EINVAL, "beta = %g too large for the heat-bath table", beta);
+            double T = std::ceil(x) - 1.0;
+            if (T > 4294967295.0) T = 4294967295.0;
+            tab->hb[hs + 2 * d] = (uint32_t)T;
+        }
+        return SL_OK;
+    }
     for (int k = 0; k < tab->ncmp; ++k) {
         const int e = tab->scheme ? 2 * d - k : 2 * d - 2 * k;
         const int sh = tab->sigma_neg ? -e : e;
@@ -157,7 +173,8 @@ int ensure_graph(sl_lattice* h, const SweepParams& p)
     std::memcpy(&key[0], &p.beta, 8);
     key[1] = p.seed;
     key[2] = ((uint64_t)h->kernel << 48) ^ ((uint64_t)h->rows << 32) ^
-             ((uint64_t)h->fast_math << 24) ^ (uint64_t)h->renorm_every;
+             ((uint64_t)h->fast_math << 24) ^ ((uint64_t)h->update << 40) ^
+             (uint64_t)h->renorm_every;
     key[3] = 0;
     if (h->graph && std::memcmp(key, h->graph_key, sizeof key) == 0) return SL_OK;
     if (h->graph) {
@@ -278,6 +295,7 @@ int sl_create(int d, int L, int n, int j_layout, int storage, double J, const vo
     h->kernel = 0;
     h->rows = 0;
     h->use_graph = 1;
+    h->update = 0;
     h->graph = nullptr;
     h->graph_sweeps = 0;
     h->owned_buf = owned;
@@ -473,6 +491,12 @@ int sl_set_option(sl_lattice* h, int option, int64_t value)
     case SL_OPT_GRAPH:
         if (value != 0 && value != 1) return fail(SL_EINVAL, "graph must be 0 or 1");
         h->use_graph = (int)value;
+        return SL_OK;
+    case SL_OPT_UPDATE:
+        if (value != 0 && value != 1) return fail(SL_EINVAL, "update must be 0 or 1");
+        if (value == 1 && h->storage != SL_STORE_I8)
+            return fail(SL_EINVAL, "the heat-bath rule is available for Ising byte storage");
+        h->update = (int)value;
         return SL_OK;
     default:
         return fail(SL_EINVAL, "unknown option %d", option);
