@@ -41,6 +41,10 @@ WORKLOADS = {
     "ising2d_L16384_i8_heatbath": dict(d=2, L=16384, n=1, beta=0.440687, storage="i8",
                                        bytes=3.0, update=1,
                                        desc="2D Ising, L=16384, int8 spins, heat-bath rule"),
+    "ising2d_L16384_i8_k100": dict(d=2, L=16384, n=1, beta=0.440687, storage="i8", bytes=0.0,
+                                   multihit=100, tile=16, paper_flips_per_ns=1 / 0.034,
+                                   desc="2D Ising, L=16384, int8 spins, k=100 multi-hit in "
+                                        "16x16 tiles (the mode of the paper's Table 1)"),
     "ising2d_L16384_bits": dict(d=2, L=16384, n=1, beta=0.440687, storage="bits", bytes=0.375,
                                 desc="2D Ising, L=16384, one bit per spin"),
     "ising3d_L512_bits": dict(d=3, L=512, n=1, beta=0.2216546, storage="bits", bytes=0.375,
@@ -225,6 +229,9 @@ def time_sweeps(spinmc, wl, steps, warmup, replica, want_clocks, local):
                          storage=storage)
     if wl.get("update"):
         lat.set_option(spinmc.SL_OPT_UPDATE, wl["update"])
+    if wl.get("multihit"):
+        lat.set_option(spinmc.SL_OPT_TILE, wl["tile"])
+        lat.set_option(spinmc.SL_OPT_MULTIHIT, wl["multihit"])
     E = torch.empty(max(steps, warmup, 1), dtype=torch.float64, device="cuda")
     m = torch.empty_like(E)
     spinmc.sl_sweep_series(lat.h, wl["beta"], warmup, inputs.DEFAULT_SEED, E, m)
@@ -474,12 +481,17 @@ def main():
             for name, w in WORKLOADS.items():
                 if name == args.workload or w["storage"] == "batch":
                     continue
-                k = 300
-                vms, _, _ = time_sweeps(spinmc, w, k, 5, rank, False, local)
+                k = 10 if w.get("multihit") else 300
+                vms, _, _ = time_sweeps(spinmc, w, k, 3 if w.get("multihit") else 5, rank,
+                                        False, local)
                 n = w["L"] ** w["d"]
+                hits = w.get("multihit") or 1
                 gbs = w["bytes"] * (n // 2) / (vms / (2 * k) * 1e-3) / 1e9
-                var[name] = {"value": n * k / (vms * 1e6), "unit": UNIT, "ms_per_step": vms / k,
-                             "achieved_gbs": gbs, "hbm_frac": gbs / hbm}
+                var[name] = {"value": n * k * hits / (vms * 1e6), "unit": UNIT,
+                             "ms_per_step": vms / k, "achieved_gbs": gbs, "hbm_frac": gbs / hbm}
+                if w.get("paper_flips_per_ns"):
+                    var[name]["paper_gtx480_flips_per_ns"] = w["paper_flips_per_ns"]
+                    var[name]["over_paper_gtx480"] = var[name]["value"] / w["paper_flips_per_ns"]
             var["ea3d_batch_1024x32"] = batch_run(spinmc)
             line["variants"] = var
         print(json.dumps(line), flush=True)

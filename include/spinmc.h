@@ -77,6 +77,10 @@ extern "C" {
 #define SL_OPT_GRAPH 5         /* 1 = replay sweeps through CUDA graphs (default), 0 = plain launches */
 #define SL_OPT_UPDATE 6        /* 0 = Metropolis (Eq. 2, default); 1 = heat-bath (Ising, byte
                                   storage): s_i = +1 iff u < 2^32 / (1 + exp(-2 beta J h_i)) */
+#define SL_OPT_MULTIHIT 7      /* k > 0: k-fold multi-hit sweeps in big tiles (Ising bytes,
+                                  uniform J, Metropolis); 0 = plain sweeps (default) */
+#define SL_OPT_TILE 8          /* big-tile side T for multi-hit sweeps: 8, 16 (default), 32 or
+                                  64 in 2D, 8 or 16 in 3D; L % 2T == 0 */
 
 typedef struct sl_lattice sl_lattice;
 

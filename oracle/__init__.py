@@ -40,6 +40,8 @@ def lib():
         L.orc_ising_sweeps.argtypes = [_int, _int, _dbl, _vp, _dbl, _u64, _u32, _i64, _i64,
                                        _i8p, _vp, _vp]
         L.orc_ising_heatbath_sweeps.argtypes = L.orc_ising_sweeps.argtypes
+        L.orc_ising_multihit_sweeps.argtypes = [_int, _int, _int, _int, _dbl, _vp, _dbl, _u64,
+                                                _u32, _i64, _i64, _i8p, _vp, _vp]
         L.orc_xy_init.argtypes = [_int, _int, _u64, _u32, _f64p]
         L.orc_heis_init.argtypes = [_int, _int, _u64, _u32, _f64p]
         L.orc_xy_measure.argtypes = [_int, _int, _dbl, _vp, _f64p, ctypes.POINTER(_dbl), _f64p]
@@ -132,6 +134,19 @@ def ising_heatbath_sweeps(d, L, s, beta, seed, t0, nsweeps, J=1.0, Jb=None, repl
     m = np.empty(nsweeps) if series else None
     lib().orc_ising_heatbath_sweeps(d, L, J, _ptr(jb), beta, seed, replica, t0, nsweeps, s,
                                     _ptr(E), _ptr(m))
+    return E, m
+
+
+def ising_multihit_sweeps(d, L, T, k, s, beta, seed, t0, nsweeps, J=1.0, Jb=None, replica=0,
+                          series=True):
+    """k-fold multi-hit sweeps in tiles of side T, in place on s."""
+    assert s.dtype == np.int8 and s.flags.c_contiguous
+    assert T % 2 == 0 and L % (2 * T) == 0
+    jb = _bonds_i8(Jb, d, L)
+    E = np.empty(nsweeps) if series else None
+    m = np.empty(nsweeps) if series else None
+    lib().orc_ising_multihit_sweeps(d, L, T, k, J, _ptr(jb), beta, seed, replica, t0, nsweeps,
+                                    s, _ptr(E), _ptr(m))
     return E, m
 
 

@@ -153,3 +153,39 @@ static void ising_sweeps_rule(int d, int L, double J, const int8_t* Jb, double b
         }
     }
 }
+
+void orc_ising_multihit_sweeps(int d, int L, int T, int k, double J, const int8_t* Jb,
+                               double beta, uint64_t seed, uint32_t replica, int64_t t0,
+                               int64_t nsweeps, int8_t* s, double* E_out, double* absm_out)
+{
+    orc_geom g = orc_make_geom(d, L);
+    const uint32_t key[2] = {orc_key_lo(seed), orc_key_hi(seed)};
+    const int Lz = d == 3 ? L : 1;
+    for (int64_t step = 0; step < nsweeps; ++step) {
+        const int64_t t = t0 + step;
+        for (int tc = 0; tc < 2; ++tc)          /* tile colour */
+            for (int h = 0; h < k; ++h)           /* hit */
+                for (int c = 0; c < 2; ++c)       /* site colour */
+                    for (int z = 0; z < Lz; ++z)
+                        for (int y = 0; y < L; ++y)
+                            for (int x = (c + y + z) & 1; x < L; x += 2) {
+                                int tile_colour = (x / T + y / T + (d == 3 ? z / T : 0)) & 1;
+                                if (tile_colour != tc) continue;
+                                int xyz[3] = {x, y, z};
+                                int64_t i = orc_index(&g, xyz);
+                                int64_t j = i >> 1;
+                                uint32_t ctr[4] = {(uint32_t)(j >> 2), (uint32_t)(t * k + h),
+                                                   replica, (uint32_t)(ORC_MULTIHIT << 1 | c)};
+                                uint32_t out[4];
+                                orc_philox4x32_10(ctr, key, out);
+                                if (ising_accept(&g, J, Jb, beta, s, xyz, i, out[j & 3]))
+                                    s[i] = (int8_t)-s[i];
+                            }
+        if (E_out || absm_out) {
+            double E, M;
+            orc_ising_measure(d, L, J, Jb, s, &E, &M);
+            if (E_out) E_out[step] = E;
+            if (absm_out) absm_out[step] = fabs(M) / (double)g.N;
+        }
+    }
+}

@@ -71,6 +71,19 @@ void orc_ising_heatbath_sweeps(int d, int L, double J, const int8_t* Jb, double 
                                uint64_t seed, uint32_t replica, int64_t t0, int64_t nsweeps,
                                int8_t* s, double* E_out, double* absm_out);
 
+/* k-fold multi-hit sweeps in big tiles (Section 2: the lattice is cut into
+ * big tiles of side T forming a checkerboard; for tile colour 0 and then 1,
+ * every tile of that colour receives k updates of all its spins, each an
+ * inner checkerboard pass over site colour 0 and then 1, while the
+ * neighbouring tiles stay fixed).  T must be even and L % (2T) == 0 so the
+ * tile checkerboard closes under the periodic wrap.  Hit h of sweep t
+ * draws output j & 3 of Philox(ctr = (j >> 2, t*k + h, replica,
+ * 4 << 1 | colour)); acceptance as in orc_ising_sweeps.  E_out / absm_out
+ * receive the energy and |m| after each full sweep. */
+void orc_ising_multihit_sweeps(int d, int L, int T, int k, double J, const int8_t* Jb,
+                               double beta, uint64_t seed, uint32_t replica, int64_t t0,
+                               int64_t nsweeps, int8_t* s, double* E_out, double* absm_out);
+
 /* ---- O(n) models with continuous spins, n = 2 (XY), n = 3 (Heisenberg) ---
  * XY spins are angles theta (s = (cos theta, sin theta)); Heisenberg spins
  * are unit vectors stored as s[3*i + a].  All arithmetic is FP64. */

@@ -58,6 +58,7 @@ struct sl_lattice {
     bool bonds_have_zero;
     // options
     int renorm_every, fast_math, kernel, rows, use_graph, update;
+    int multihit, tile;      // k-fold multi-hit sweeps in tiles of side `tile` (0 = off)
     // cached graph of kGraphSweeps sweeps
     cudaGraphExec_t graph;
     int graph_sweeps;
@@ -80,6 +81,12 @@ cudaError_t ising_bonds_scatter(const sl_lattice* h, const int8_t* nat, unsigned
 cudaError_t ising_i8_sweeps(const sl_lattice* h, const SweepParams& p, int64_t count,
                             cudaStream_t s);
 cudaError_t ising_i8_measure(const sl_lattice* h, cudaStream_t s);
+// measurement that also closes a sweep (series entry, sweep counter + 1)
+cudaError_t ising_i8_measure_advance(const sl_lattice* h, cudaStream_t s);
+
+// ---- Ising multi-hit sweeps in big tiles (ising_tile.cu) ----
+bool tile_size_ok(int d, int L, int T);
+cudaError_t ising_tile_sweep(const sl_lattice* h, const SweepParams& p, cudaStream_t s);
 
 // ---- Ising bit-packed (ising_bits.cu) ----
 cudaError_t ising_bits_init(const sl_lattice* h, cudaStream_t s);

@@ -43,6 +43,7 @@ struct I8Args {
     double J;
     int measure;  // accumulate E and M and finish the pass
     int update;   // 0: standalone measurement (no moves, no sweep advance)
+    int advance;  // a measurement that closes a sweep: write the series, t + 1
 };
 
 __device__ __forceinline__ void i8_finish(const I8Args& a, const Partial& tot)
@@ -54,7 +55,7 @@ __device__ __forceinline__ void i8_finish(const I8Args& a, const Partial& tot)
     C->obs[1] = M;
     C->obs[2] = 0.0;
     C->obs[3] = 0.0;
-    if (a.update) {
+    if (a.update || a.advance) {
         const long long k = (long long)C->t - C->series_base;
         if (C->series_E) C->series_E[k] = E;
         if (C->series_absm) C->series_absm[k] = fabs(M) / (double)a.N;
@@ -490,6 +491,7 @@ I8Args make_args(const sl_lattice* h, int c)
     a.J = h->J;
     a.measure = c == 1;
     a.update = 1;
+    a.advance = 0;
     return a;
 }
 
@@ -580,6 +582,14 @@ cudaError_t ising_bonds_scatter(const sl_lattice* h, const int8_t* nat, unsigned
 cudaError_t ising_i8_sweeps(const sl_lattice* h, const SweepParams& p, int64_t count,
                             cudaStream_t s)
 {
+    if (h->multihit > 0) {
+        for (int64_t k = 0; k < count; ++k) {
+            cudaError_t e = ising_tile_sweep(h, p, s);
+            if (e == cudaSuccess) e = ising_i8_measure_advance(h, s);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
     const bool stream = h->kernel == 2 || (h->kernel == 0 && stream_ok(h));
     for (int64_t k = 0; k < count; ++k) {
         for (int c = 0; c < 2; ++c) {
@@ -591,6 +601,17 @@ cudaError_t ising_i8_sweeps(const sl_lattice* h, const SweepParams& p, int64_t c
         }
     }
     return cudaSuccess;
+}
+
+cudaError_t ising_i8_measure_advance(const sl_lattice* h, cudaStream_t s)
+{
+    I8Args a = make_args(h, 1);
+    a.update = 0;
+    a.measure = 1;
+    a.advance = 1;
+    memset(&a.tab, 0, sizeof(a.tab));
+    memset(&a.rk, 0, sizeof(a.rk));
+    return launch_pass(h, a, s, false);
 }
 
 cudaError_t ising_i8_measure(const sl_lattice* h, cudaStream_t s)

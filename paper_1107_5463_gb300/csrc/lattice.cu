@@ -175,7 +175,7 @@ int ensure_graph(sl_lattice* h, const SweepParams& p)
     key[2] = ((uint64_t)h->kernel << 48) ^ ((uint64_t)h->rows << 32) ^
              ((uint64_t)h->fast_math << 24) ^ ((uint64_t)h->update << 40) ^
              (uint64_t)h->renorm_every;
-    key[3] = 0;
+    key[3] = ((uint64_t)h->multihit << 16) ^ (uint64_t)h->tile;
     if (h->graph && std::memcmp(key, h->graph_key, sizeof key) == 0) return SL_OK;
     if (h->graph) {
         cudaGraphExecDestroy(h->graph);
@@ -296,6 +296,8 @@ int sl_create(int d, int L, int n, int j_layout, int storage, double J, const vo
     h->rows = 0;
     h->use_graph = 1;
     h->update = 0;
+    h->multihit = 0;
+    h->tile = 16;
     h->graph = nullptr;
     h->graph_sweeps = 0;
     h->owned_buf = owned;
@@ -348,6 +350,8 @@ int sl_sweep_series(sl_lattice* h, double beta, int64_t nsweeps, uint64_t seed, 
         return fail(SL_EINVAL, "beta must be finite and >= 0 (got %g)", beta);
     if (h->sweeps_done + nsweeps > 4294967296LL)
         return fail(SL_EINVAL, "sweep index would exceed 2^32");
+    if (h->multihit > 0 && (h->sweeps_done + nsweeps) * (int64_t)h->multihit > 4294967296LL)
+        return fail(SL_EINVAL, "multi-hit index t*k would exceed 2^32");
     if (nsweeps == 0) return SL_OK;
     SweepParams p;
     std::memset(&p, 0, sizeof p);
@@ -496,7 +500,25 @@ int sl_set_option(sl_lattice* h, int option, int64_t value)
         if (value != 0 && value != 1) return fail(SL_EINVAL, "update must be 0 or 1");
         if (value == 1 && h->storage != SL_STORE_I8)
             return fail(SL_EINVAL, "the heat-bath rule is available for Ising byte storage");
+        if (value == 1 && h->multihit > 0)
+            return fail(SL_EINVAL, "multi-hit sweeps use the Metropolis rule");
         h->update = (int)value;
+        return SL_OK;
+    case SL_OPT_MULTIHIT:
+        if (value < 0 || value > 65536) return fail(SL_EINVAL, "multihit must be in [0, 65536]");
+        if (value > 0 && (h->storage != SL_STORE_I8 || h->j_layout != SL_J_UNIFORM ||
+                          h->update != 0))
+            return fail(SL_EINVAL, "multi-hit sweeps need Ising bytes, uniform J and Metropolis");
+        if (value > 0 && !tile_size_ok(h->d, h->L, h->tile))
+            return fail(SL_EINVAL, "tile side %d does not fit L = %d (L %% 2T == 0)", h->tile,
+                        h->L);
+        h->multihit = (int)value;
+        return SL_OK;
+    case SL_OPT_TILE:
+        if (!tile_size_ok(h->d, h->L, (int)value))
+            return fail(SL_EINVAL, "tile side must be 8, 16, 32, 64 (2D) or 8, 16 (3D) with "
+                                   "L %% 2T == 0");
+        h->tile = (int)value;
         return SL_OK;
     default:
         return fail(SL_EINVAL, "unknown option %d", option);

@@ -21,7 +21,7 @@ SL_OK, SL_EINVAL, SL_ENOMEM, SL_ECUDA, SL_ETIMEOUT, SL_EDEVICE = 0, -1, -2, -3, 
 SL_J_UNIFORM, SL_J_BONDS = 0, 1
 SL_STORE_I8, SL_STORE_BITS, SL_STORE_F32_ANGLE, SL_STORE_F32_VEC = 0, 1, 2, 3
 SL_OPT_RENORM_EVERY, SL_OPT_FAST_MATH, SL_OPT_KERNEL, SL_OPT_ROWS, SL_OPT_GRAPH = 1, 2, 3, 4, 5
-SL_OPT_UPDATE = 6
+SL_OPT_UPDATE, SL_OPT_MULTIHIT, SL_OPT_TILE = 6, 7, 8
 
 if not os.path.exists(LIB_PATH):
     raise ImportError("libspinmc.so is not built at %s; run paper_1107_5463_gb300.build.build()"

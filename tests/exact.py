@@ -116,6 +116,40 @@ def exact_sweep_matrix(d, L, beta, J=1.0, Jb=None, heatbath=False):
     return mats[0], mats[1], S, E
 
 
+def multihit_sweep_distribution(d, L, T, k, beta, start, J=1.0):
+    """Exact distribution over all 2^N states after one k-fold multi-hit
+    sweep from `start`: for tile colour 0 then 1, k times, site colour 0 then
+    1, every site of that tile colour and site colour flips independently
+    with min(1, exp(-beta dE)), dE from the full Eq. (1).  States are encoded
+    with bit i set for s_i = -1."""
+    N = L ** d
+    S = all_states(N)
+    E = roll_energy(S, d, L, J).astype(np.float64)
+    colour = colour_of_site(d, L)
+    i = np.arange(N)
+    tcol = (i % L) // T + ((i // L) % L) // T
+    if d == 3:
+        tcol = tcol + (i // (L * L)) // T
+    tcol &= 1
+    states = np.arange(2 ** N, dtype=np.int64)
+    p = np.zeros(2 ** N)
+    p[int(sum(1 << q for q in range(N) if start[q] < 0))] = 1.0
+    for tc in (0, 1):
+        for _ in range(k):
+            for c in (0, 1):
+                sites = np.nonzero((colour == c) & (tcol == tc))[0]
+                pf = [np.minimum(1.0, np.exp(-beta * (E[states ^ (1 << q)] - E))) for q in sites]
+                new = np.zeros_like(p)
+                for flips in itertools.product((0, 1), repeat=len(sites)):
+                    mask = sum(1 << q for f, q in zip(flips, sites) if f)
+                    w = p.copy()
+                    for f, pq in zip(flips, pf):
+                        w *= pq if f else 1.0 - pq
+                    np.add.at(new, states ^ mask, w)
+                p = new
+    return p
+
+
 # ------------------------------------------------------- Kaufman 1949 ----
 
 def _ln2cosh(x):

@@ -401,3 +401,48 @@ def test_heatbath_two_spin_bond_and_beta_zero():
         j = i >> 1
         out = oracle.philox4x32_10([j >> 2, t, 0, int(colour[i])], key)
         assert s[i] == (1 if int(out[j & 3]) < 2**31 else -1)
+
+
+# ------------------------------------------------------------ multi-hit --
+
+@pytest.mark.parametrize("k,beta", [(1, 0.35), (2, 0.2)])
+def test_multihit_one_sweep_distribution_on_4x4(k, beta):
+    """The tile schedule of the k-fold multi-hit sweep (tiles of side 2 on the
+    4x4 torus): the exact distribution of the state after one sweep from a
+    fixed start (all 2^16 states propagated through the tile / hit / colour
+    sub-steps) against the oracle's empirical outcomes (chi-square)."""
+    d, L, T = 2, 4, 2
+    start = inputs.ising_spins(d, L, 12)
+    p = exact.multihit_sweep_distribution(d, L, T, k, beta, start)
+    assert abs(p.sum() - 1) < 1e-12
+    reps = 20000
+    counts = np.zeros(p.size)
+    weights = 1 << np.arange(L * L)
+    for r in range(reps):
+        s = start.copy()
+        oracle.ising_multihit_sweeps(d, L, T, k, s, beta, 99, r, 1, series=False)
+        counts[int(((s < 0) * weights).sum())] += 1
+    big = reps * p >= 5
+    assert counts[p == 0].sum() == 0, "an outcome with zero exact probability"
+    obs = np.append(counts[big], counts[~big].sum())
+    exp_ = np.append(reps * p[big], reps * p[~big].sum())
+    keep = exp_ > 0
+    chi2 = ((obs[keep] - exp_[keep]) ** 2 / exp_[keep]).sum()
+    assert stats.chi2.sf(chi2, keep.sum() - 1) > 1e-4
+    # a schedule with one tile (the plain checkerboard) is a different chain
+    q = exact.multihit_sweep_distribution(d, L, 4, k, beta, start)
+    assert np.abs(p - q).max() > 1e-3
+
+
+def test_multihit_equilibrium_and_beta_zero():
+    ex = exact.enumerate_ising(2, 4, BETA_C)
+    s = oracle.ising_init(2, 4, 3)
+    E, m = oracle.ising_multihit_sweeps(2, 4, 2, 3, s, BETA_C, 4, 0, 60_000)
+    for obs, ref in ((E[500:], ex["E"]), (m[500:], ex["absm"])):
+        mean, err = exact.binned_mean(obs, 40)
+        assert abs(mean - ref) < 3 * err, (mean, ref, err)
+    for k in (1, 2, 5):
+        s0 = inputs.ising_spins(3, 8, k)
+        s = s0.copy()
+        oracle.ising_multihit_sweeps(3, 8, 4, k, s, 0.0, 1, 0, 1, series=False)
+        np.testing.assert_array_equal(s, s0 * (-1) ** k)
