@@ -42,6 +42,9 @@ def lib():
         L.orc_ising_heatbath_sweeps.argtypes = L.orc_ising_sweeps.argtypes
         L.orc_ising_multihit_sweeps.argtypes = [_int, _int, _int, _int, _dbl, _vp, _dbl, _u64,
                                                 _u32, _i64, _i64, _i8p, _vp, _vp]
+        L.orc_ising_sw_sweeps.argtypes = [_int, _int, _dbl, _dbl, _u64, _u32, _i64, _i64, _i8p,
+                                          _vp, _vp, _vp, _vp]
+        L.orc_ising_sw_sweeps.restype = _int
         L.orc_xy_init.argtypes = [_int, _int, _u64, _u32, _f64p]
         L.orc_heis_init.argtypes = [_int, _int, _u64, _u32, _f64p]
         L.orc_xy_measure.argtypes = [_int, _int, _dbl, _vp, _f64p, ctypes.POINTER(_dbl), _f64p]
@@ -147,6 +150,26 @@ def ising_multihit_sweeps(d, L, T, k, s, beta, seed, t0, nsweeps, J=1.0, Jb=None
     m = np.empty(nsweeps) if series else None
     lib().orc_ising_multihit_sweeps(d, L, T, k, J, _ptr(jb), beta, seed, replica, t0, nsweeps,
                                     s, _ptr(E), _ptr(m))
+    return E, m
+
+
+def ising_sw_sweeps(d, L, s, beta, seed, t0, nsweeps, J=1.0, replica=0, series=True,
+                    clusters=False):
+    """Swendsen-Wang updates in place on s; return (E, |m|), plus, with
+    clusters=True, the last update's active bonds (d, N) and cluster labels
+    (smallest site of each site's cluster, N)."""
+    assert s.dtype == np.int8 and s.flags.c_contiguous
+    N = nsites(d, L)
+    E = np.empty(nsweeps) if series else None
+    m = np.empty(nsweeps) if series else None
+    act = np.zeros((d, N), np.uint8) if clusters else None
+    lab = np.zeros(N, np.int64) if clusters else None
+    rc = lib().orc_ising_sw_sweeps(d, L, J, beta, seed, replica, t0, nsweeps, s, _ptr(E),
+                                   _ptr(m), _ptr(act), _ptr(lab))
+    if rc != 0:
+        raise MemoryError("oracle Swendsen-Wang update: out of memory")
+    if clusters:
+        return E, m, act, lab
     return E, m
 
 

@@ -84,6 +84,7 @@ static inline uint32_t orc_key_hi(uint64_t seed) { return (uint32_t)(seed >> 32)
  * in FP32 and FP64). */
 static inline double orc_u24(uint32_t x) { return (double)(x >> 8) * (1.0 / 16777216.0); }
 
-enum { ORC_SWEEP = 0, ORC_INIT = 1, ORC_COUPLING = 2, ORC_EXCHANGE = 3, ORC_MULTIHIT = 4 };
+enum { ORC_SWEEP = 0, ORC_INIT = 1, ORC_COUPLING = 2, ORC_EXCHANGE = 3, ORC_MULTIHIT = 4,
+       ORC_SW_BOND = 5, ORC_SW_FLIP = 6 };
 
 #endif

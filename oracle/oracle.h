@@ -26,7 +26,8 @@
  *     key = (seed & 0xffffffff, seed >> 32), counter
  *       ctr = (group, t, replica, purpose << 1 | colour)
  *     with purpose 0 = sweep, 1 = initial state, 2 = couplings, 3 = replica
- *     exchange.  The group is j >> 2 for Ising (site j uses output j & 3),
+ *     exchange, 4 = multi-hit sweep, 5 = Swendsen-Wang bond, 6 = Swendsen-Wang
+ *     cluster flip.  The group is j >> 2 for Ising (site j uses output j & 3),
  *     j >> 1 for XY (site j uses outputs 2(j&1), 2(j&1)+1), and j for
  *     Heisenberg (outputs 0, 1, 2).
  */
@@ -83,6 +84,21 @@ void orc_ising_heatbath_sweeps(int d, int L, double J, const int8_t* Jb, double 
 void orc_ising_multihit_sweeps(int d, int L, int T, int k, double J, const int8_t* Jb,
                                double beta, uint64_t seed, uint32_t replica, int64_t t0,
                                int64_t nsweeps, int8_t* s, double* E_out, double* absm_out);
+
+/* Swendsen-Wang updates (Section 3: activate satisfied bonds with
+ * p = 1 - exp(-2 beta |J|), form the clusters joined by active bonds, flip each
+ * with probability 1/2), uniform coupling J.  Update t: the forward bond
+ * (i, i + e_mu) is active iff J s_i s_j > 0 and u < p 2^32, u = output
+ * 2 (i & 1) + mu of Philox(ctr = (i >> 1, t, replica, 5 << 1)) in 2D or output
+ * mu of Philox(ctr = (i, t, replica, 5 << 1)) in 3D; the cluster whose
+ * smallest site is r flips iff the top bit of output 0 of
+ * Philox(ctr = (r, t, replica, 6 << 1)) is set.  E_out / absm_out as for
+ * orc_ising_sweeps.  If non-NULL, active_out ([d][N] bytes) and label_out
+ * (N entries, the smallest site of each site's cluster) receive the bonds and
+ * clusters of the last update.  Returns 0, or -1 if memory ran out. */
+int orc_ising_sw_sweeps(int d, int L, double J, double beta, uint64_t seed, uint32_t replica,
+                        int64_t t0, int64_t nsweeps, int8_t* s, double* E_out,
+                        double* absm_out, uint8_t* active_out, int64_t* label_out);
 
 /* ---- O(n) models with continuous spins, n = 2 (XY), n = 3 (Heisenberg) ---
  * XY spins are angles theta (s = (cos theta, sin theta)); Heisenberg spins

@@ -150,6 +150,52 @@ def multihit_sweep_distribution(d, L, T, k, beta, start, J=1.0):
     return p
 
 
+def forward_bonds(d, L):
+    """The d N forward bonds (i, i + e_mu) of the periodic lattice as two
+    arrays of site indices (a multigraph for L = 2)."""
+    N = L ** d
+    i = np.arange(N)
+    coords = [(i // L ** mu) % L for mu in range(d)]
+    a, b = [], []
+    for mu in range(d):
+        nb = i + (((coords[mu] + 1) % L) - coords[mu]) * L ** mu
+        a.append(i)
+        b.append(nb)
+    return np.concatenate(a), np.concatenate(b)
+
+
+def exact_sw_matrix(d, L, beta, J=1.0):
+    """Exact transition matrix of one Swendsen-Wang update (Section 3): every
+    satisfied bond (J s_a s_b > 0) is activated independently with
+    p = 1 - exp(-2 beta |J|), the clusters are the connected components of the
+    active bonds (scipy's connected_components), and every cluster flips
+    independently with probability 1/2.  Summed over all bond subsets."""
+    from scipy.sparse import coo_matrix
+    from scipy.sparse.csgraph import connected_components
+    N = L ** d
+    S = all_states(N)
+    E = roll_energy(S, d, L, J).astype(np.float64)
+    A, B = forward_bonds(d, L)
+    p = 1.0 - math.exp(-2.0 * beta * abs(J))
+    codes = ((S < 0).astype(np.int64) << np.arange(N)).sum(axis=1)
+    row_of = {int(c): k for k, c in enumerate(codes)}
+    T = np.zeros((len(S), len(S)))
+    for a_state, s in enumerate(S):
+        sat = np.nonzero(J * s[A].astype(np.int64) * s[B] > 0)[0]
+        for mask in range(1 << len(sat)):
+            on = [sat[q] for q in range(len(sat)) if (mask >> q) & 1]
+            w = p ** len(on) * (1.0 - p) ** (len(sat) - len(on))
+            if w == 0.0:
+                continue
+            g = coo_matrix((np.ones(len(on)), (A[on], B[on])), shape=(N, N))
+            ncl, comp = connected_components(g, directed=False)
+            for flips in range(1 << ncl):
+                f = (flips >> comp) & 1
+                code = int(codes[a_state] ^ (f << np.arange(N)).sum())
+                T[a_state, row_of[code]] += w / (1 << ncl)
+    return T, S, E
+
+
 # ------------------------------------------------------- Kaufman 1949 ----
 
 def _ln2cosh(x):

@@ -446,3 +446,121 @@ def test_multihit_equilibrium_and_beta_zero():
         s = s0.copy()
         oracle.ising_multihit_sweeps(3, 8, 4, k, s, 0.0, 1, 0, 1, series=False)
         np.testing.assert_array_equal(s, s0 * (-1) ** k)
+
+
+# ------------------------------------------------------ Swendsen-Wang ----
+
+@pytest.mark.parametrize("beta", [0.2, 0.45])
+def test_sw_transition_matrix_on_L2(beta):
+    """Exact matrix of one Swendsen-Wang update on the 2 x 2 torus (Section 3:
+    satisfied bonds activated with 1 - e^{-2 beta J}, connected components by
+    scipy, clusters flipped with probability 1/2, summed over all bond
+    subsets) satisfies detailed balance for the Boltzmann weights of Eq. 1,
+    and the oracle's empirical transitions from every start state follow it."""
+    d, L = 2, 2
+    T, S, E = exact.exact_sw_matrix(d, L, beta)
+    pi = np.exp(-beta * E)
+    pi /= pi.sum()
+    np.testing.assert_allclose(pi[:, None] * T, (pi[:, None] * T).T, atol=1e-15)
+    np.testing.assert_allclose(T.sum(axis=1), 1.0, atol=1e-13)
+    codes = {tuple(s): k for k, s in enumerate(S)}
+    reps = 4000
+    counts = np.zeros((len(S), len(S)))
+    for a in range(len(S)):
+        for r in range(reps):
+            s = S[a].copy()
+            oracle.ising_sw_sweeps(d, L, s, beta, 4321, r, 1, series=False)
+            counts[a, codes[tuple(s)]] += 1
+    assert _chi2_rows(counts, T, range(len(S))) > 1e-4
+
+
+@pytest.mark.parametrize("d,L,beta", [(2, 16, BETA_C), (3, 6, 0.2216546)])
+def test_sw_clusters_are_connected_components(d, L, beta):
+    """The last update's clusters are exactly the connected components of its
+    active bonds (scipy), each named by its smallest site; active bonds join
+    like spins only, a fraction 1 - e^{-2 beta J} of the satisfied bonds is
+    active, every cluster flips as a whole, and about half of them flip."""
+    from scipy.sparse import coo_matrix
+    from scipy.sparse.csgraph import connected_components
+    N = L ** d
+    A, B = exact.forward_bonds(d, L)
+    n_sat = n_act = n_cl = n_flip = 0
+    for t in range(6):
+        s0 = oracle.ising_init(d, L, 11 + t)
+        s = s0.copy()
+        _, _, act, lab = oracle.ising_sw_sweeps(d, L, s, beta, 77, t, 1, series=False,
+                                                clusters=True)
+        on = act.reshape(-1).astype(bool)
+        sat = s0[A] == s0[B]
+        assert not (on & ~sat).any()
+        n_sat += sat.sum()
+        n_act += on.sum()
+        g = coo_matrix((np.ones(on.sum()), (A[on], B[on])), shape=(N, N))
+        ncl, comp = connected_components(g, directed=False)
+        cmin = np.full(ncl, N)
+        np.minimum.at(cmin, comp, np.arange(N))
+        np.testing.assert_array_equal(lab, cmin[comp])
+        flipped = (s != s0)
+        # a cluster flips as a whole
+        per = np.zeros(ncl)
+        np.add.at(per, comp, flipped)
+        sizes = np.bincount(comp, minlength=ncl)
+        assert np.all((per == 0) | (per == sizes))
+        n_cl += ncl
+        n_flip += (per > 0).sum()
+    p = 1.0 - math.exp(-2.0 * beta)
+    assert abs(n_act / n_sat - p) < 5 * math.sqrt(p * (1 - p) / n_sat)
+    assert abs(n_flip / n_cl - 0.5) < 5 * math.sqrt(0.25 / n_cl)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_sw_beta_zero_and_large_beta(d):
+    """beta = 0: no bond is active, every site is its own cluster and flips iff
+    the top bit of output 0 of Philox(i, t, replica, 6 << 1) is set.  Large
+    beta from the ground state: every bond is active, one cluster named 0
+    flips as a whole and the energy stays -d N J."""
+    L = 4
+    N = L ** d
+    s0 = oracle.ising_init(d, L, 5)
+    s = s0.copy()
+    seed, t, rep = 0x1234_5678_9ABC, 7, 3
+    _, _, act, lab = oracle.ising_sw_sweeps(d, L, s, 0.0, seed, t, 1, replica=rep,
+                                            series=False, clusters=True)
+    assert act.sum() == 0
+    np.testing.assert_array_equal(lab, np.arange(N))
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    bits = np.array([oracle.philox4x32_10([i, t, rep, 6 << 1], key)[0] >> 31 for i in range(N)])
+    np.testing.assert_array_equal(s, np.where(bits == 1, -s0, s0))
+    g = np.ones(N, np.int8)
+    flips = 0
+    for t in range(8):
+        E, _, act, lab = oracle.ising_sw_sweeps(d, L, g, 50.0, seed, t, 1, clusters=True)
+        assert act.all() and (lab == 0).all()
+        assert E[0] == -d * N
+        assert abs(int(g.sum())) == N
+        flips += g[0] < 0
+    assert 0 < flips < 8
+
+
+def test_sw_equilibrium_matches_enumeration_and_kaufman():
+    """Swendsen-Wang chains reach the Boltzmann law of Eq. 1: <E>, <E^2> and
+    <|m|> on the 4 x 4 torus at beta_c against exact enumeration, <E> on the
+    2 x 2 x 2 torus at beta = 0.3, and <E>/N on the 16 x 16 torus at beta_c
+    against Kaufman's exact value (all within 3 binned standard errors)."""
+    ex = exact.enumerate_ising(2, 4, BETA_C)
+    s = oracle.ising_init(2, 4, 21)
+    E, m = oracle.ising_sw_sweeps(2, 4, s, BETA_C, 21, 0, 100_000)
+    for obs, ref in ((E, ex["E"]), (E * E, ex["E2"]), (m, ex["absm"])):
+        mean, err = exact.binned_mean(obs[100:], 40)
+        assert abs(mean - ref) < 3 * err, (mean, ref, err)
+    ex3 = exact.enumerate_ising(3, 2, 0.3)
+    s = oracle.ising_init(3, 2, 22)
+    E, _ = oracle.ising_sw_sweeps(3, 2, s, 0.3, 22, 0, 100_000)
+    mean, err = exact.binned_mean(E[100:], 40)
+    assert abs(mean - ex3["E"]) < 3 * err, (mean, ex3["E"], err)
+    L = 16
+    ref = exact.kaufman_energy_per_site(BETA_C, L)
+    s = oracle.ising_init(2, L, 23)
+    E, _ = oracle.ising_sw_sweeps(2, L, s, BETA_C, 23, 0, 20_000)
+    mean, err = exact.binned_mean(E[200:] / L**2, 20)
+    assert abs(mean - ref) < 3 * err, (mean, ref, err)
