@@ -22,7 +22,8 @@
  *     64-bit seed (key = (seed_lo, seed_hi)) with counter
  *     (group, sweep index t, replica, purpose << 1 | colour), purpose 0 for a
  *     sweep, 1 for the initial state, 2 for couplings, 3 for replica
- *     exchange; group = j >> 2 (Ising, site uses output j & 3), j >> 1 (XY,
+ *     exchange, 4 for multi-hit sweeps, 5 and 6 for Swendsen-Wang bonds and
+ *     cluster flips; group = j >> 2 (Ising, site uses output j & 3), j >> 1 (XY,
  *     outputs 2(j&1) accept and 2(j&1)+1 proposal), j (Heisenberg, outputs 0
  *     accept, 1 and 2 proposal).  A run is therefore a pure function of
  *     (seed, sweep indices, start state).
@@ -75,12 +76,18 @@ extern "C" {
 #define SL_OPT_KERNEL 3        /* 0 = automatic, 1 = generic per-site kernel, 2 = row-streaming kernel */
 #define SL_OPT_ROWS 4          /* rows each thread marches through in the streaming kernel */
 #define SL_OPT_GRAPH 5         /* 1 = replay sweeps through CUDA graphs (default), 0 = plain launches */
-#define SL_OPT_UPDATE 6        /* 0 = Metropolis (Eq. 2, default); 1 = heat-bath (Ising, byte
-                                  storage): s_i = +1 iff u < 2^32 / (1 + exp(-2 beta J h_i)) */
+#define SL_OPT_UPDATE 6        /* one of SL_UPDATE_* below (default SL_UPDATE_METROPOLIS) */
 #define SL_OPT_MULTIHIT 7      /* k > 0: k-fold multi-hit sweeps in big tiles (Ising bytes,
                                   uniform J, Metropolis); 0 = plain sweeps (default) */
 #define SL_OPT_TILE 8          /* big-tile side T for multi-hit sweeps: 8, 16 (default), 32 or
                                   64 in 2D, 8 or 16 in 3D; L % 2T == 0 */
+
+/* update rules for SL_OPT_UPDATE */
+#define SL_UPDATE_METROPOLIS 0 /* Eq. 2 */
+#define SL_UPDATE_HEATBATH 1   /* Ising bytes: s_i = +1 iff u < 2^32 / (1 + exp(-2 beta J h_i)) */
+#define SL_UPDATE_SW 2         /* Ising bytes, uniform J, N <= 2^31: Swendsen-Wang cluster
+                                  updates (Section 3), one per sweep index; needs a workspace
+                                  (sl_workspace_bytes / sl_attach_workspace) */
 
 typedef struct sl_lattice sl_lattice;
 
@@ -157,6 +164,34 @@ int sl_set_state(sl_lattice* lat, int64_t sweeps_done);
 /* sl_set_option — set one SL_OPT_* value; SL_EINVAL for unknown options or
  * values out of range. */
 int sl_set_option(sl_lattice* lat, int option, int64_t value);
+
+/*
+ * sl_workspace_bytes — device bytes of workspace an update rule needs on this
+ * lattice: 0 for SL_UPDATE_METROPOLIS and SL_UPDATE_HEATBATH; for
+ * SL_UPDATE_SW, 4 N bytes of cluster labels plus one bit per tile-face bond
+ * (Section 3: clusters are labelled in tiles, then the tiles are joined).
+ * SL_EINVAL for a NULL argument or an unknown rule.
+ */
+int sl_workspace_bytes(const sl_lattice* lat, int update, size_t* bytes);
+
+/*
+ * sl_attach_workspace — hand the lattice a caller-owned device workspace,
+ * 256-byte aligned, of at least sl_workspace_bytes bytes for the update rule
+ * it will use; it must outlive the handle or the next attach.  NULL detaches.
+ * Synchronises the handle's stream first.  Selecting SL_UPDATE_SW without a
+ * large enough workspace fails with SL_EINVAL, except on a lattice whose
+ * buffer the library allocated (sl_create with dev_buf = NULL), where the
+ * library allocates the workspace too.  SL_ENOMEM if the workspace is too
+ * small for the rule in use.
+ *
+ * Swendsen-Wang update t (SL_UPDATE_SW): the forward bond (i, i + e_mu) is
+ * active iff J s_i s_j > 0 and u < (1 - exp(-2 beta |J|)) 2^32, u = output
+ * 2 (i & 1) + mu of Philox(i >> 1, t, replica, 5 << 1) in 2D, output mu of
+ * Philox(i, t, replica, 5 << 1) in 3D; the cluster whose smallest site is r
+ * flips iff the top bit of output 0 of Philox(r, t, replica, 6 << 1) is set.
+ * E and |m| are measured after every update, as after a sweep.
+ */
+int sl_attach_workspace(sl_lattice* lat, void* dev_buf, size_t bytes);
 
 /* sl_destroy — release host metadata (and the buffer if library-owned).
  * Synchronises the handle's stream first. */

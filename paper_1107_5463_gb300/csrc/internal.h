@@ -25,6 +25,8 @@ struct IsingTable {
     int sigma_neg; // the scalar J is negative
     int heatbath;  // 1: heat-bath rule with the thresholds hb[h + 2d], h = sum_k Jb_k s_k
     uint32_t hb[13];
+    uint32_t sw_thr;  // Swendsen-Wang: a satisfied bond is active iff u <= sw_thr
+    int sw_never;     // Swendsen-Wang: no bond can be active (beta = 0)
 };
 
 // Per-sweep parameters common to every model.
@@ -57,13 +59,18 @@ struct sl_lattice {
     spinmc::Partial* partials;
     bool bonds_have_zero;
     // options
-    int renorm_every, fast_math, kernel, rows, use_graph, update;
+    int renorm_every, fast_math, kernel, rows, use_graph;
+    int update;              // SL_UPDATE_METROPOLIS, _HEATBATH or _SW
     int multihit, tile;      // k-fold multi-hit sweeps in tiles of side `tile` (0 = off)
     // cached graph of kGraphSweeps sweeps
     cudaGraphExec_t graph;
     int graph_sweeps;
     uint64_t graph_key[4];
     void* owned_buf;
+    // update workspace (Swendsen-Wang labels), caller-owned unless ws_owned
+    void* ws;
+    size_t ws_bytes;
+    void* ws_owned;
 };
 
 namespace spinmc {
@@ -87,6 +94,11 @@ cudaError_t ising_i8_measure_advance(const sl_lattice* h, cudaStream_t s);
 // ---- Ising multi-hit sweeps in big tiles (ising_tile.cu) ----
 bool tile_size_ok(int d, int L, int T);
 cudaError_t ising_tile_sweep(const sl_lattice* h, const SweepParams& p, cudaStream_t s);
+
+// ---- Ising Swendsen-Wang updates (ising_sw.cu) ----
+size_t sw_workspace_bytes(int d, int L);
+cudaError_t ising_sw_sweeps(const sl_lattice* h, const SweepParams& p, int64_t count,
+                            cudaStream_t s);
 
 // ---- Ising bit-packed (ising_bits.cu) ----
 cudaError_t ising_bits_init(const sl_lattice* h, cudaStream_t s);

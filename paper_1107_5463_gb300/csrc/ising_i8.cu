@@ -582,6 +582,7 @@ cudaError_t ising_bonds_scatter(const sl_lattice* h, const int8_t* nat, unsigned
 cudaError_t ising_i8_sweeps(const sl_lattice* h, const SweepParams& p, int64_t count,
                             cudaStream_t s)
 {
+    if (h->update == SL_UPDATE_SW) return ising_sw_sweeps(h, p, count, s);
     if (h->multihit > 0) {
         for (int64_t k = 0; k < count; ++k) {
             cudaError_t e = ising_tile_sweep(h, p, s);

@@ -126,10 +126,24 @@ int ising_table(const sl_lattice* h, double beta, IsingTable* tab)
     tab->sigma_neg = h->J < 0.0;
     tab->scheme = h->bonds_have_zero ? 1 : 0;
     tab->ncmp = tab->scheme ? 2 * d : d;
-    tab->heatbath = h->update;
+    tab->heatbath = h->update == SL_UPDATE_HEATBATH;
     for (int k = 0; k < 6; ++k) tab->thr[k] = 0xFFFFFFFFu;
     for (int k = 0; k < 13; ++k) tab->hb[k] = 0u;
-    if (h->update == 1) {
+    tab->sw_thr = 0u;
+    tab->sw_never = 1;
+    if (h->update == SL_UPDATE_SW) {
+        // Swendsen-Wang: a satisfied bond is active iff u < (1 - exp(-2 beta |J|)) 2^32,
+        // the same test as u <= ceil(x) - 1 for integer u
+        const double x = (1.0 - std::exp(-2.0 * beta * std::fabs(h->J))) * 4294967296.0;
+        if (x > 0.0) {
+            double T = std::ceil(x) - 1.0;
+            if (T > 4294967295.0) T = 4294967295.0;
+            tab->sw_thr = (uint32_t)T;
+            tab->sw_never = 0;
+        }
+        return SL_OK;
+    }
+    if (h->update == SL_UPDATE_HEATBATH) {
         // heat-bath: s_i = +1 iff u < 2^32 / (1 + exp(-beta a)), a = 2 J h,
         // h = sum_k Jb_k s_k in [-2d, 2d]; u <= ceil(x) - 1 is the same test
         for (int hs = -2 * d; hs <= 2 * d; ++hs) {
@@ -301,6 +315,9 @@ int sl_create(int d, int L, int n, int j_layout, int storage, double J, const vo
     h->graph = nullptr;
     h->graph_sweeps = 0;
     h->owned_buf = owned;
+    h->ws = nullptr;
+    h->ws_bytes = 0;
+    h->ws_owned = nullptr;
     cudaError_t e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         st = cuda_fail(e, "cudaStreamCreate");
@@ -497,11 +514,33 @@ int sl_set_option(sl_lattice* h, int option, int64_t value)
         h->use_graph = (int)value;
         return SL_OK;
     case SL_OPT_UPDATE:
-        if (value != 0 && value != 1) return fail(SL_EINVAL, "update must be 0 or 1");
-        if (value == 1 && h->storage != SL_STORE_I8)
-            return fail(SL_EINVAL, "the heat-bath rule is available for Ising byte storage");
-        if (value == 1 && h->multihit > 0)
+        if (value != SL_UPDATE_METROPOLIS && value != SL_UPDATE_HEATBATH && value != SL_UPDATE_SW)
+            return fail(SL_EINVAL, "update must be 0 (Metropolis), 1 (heat-bath) or 2 "
+                                   "(Swendsen-Wang)");
+        if (value != SL_UPDATE_METROPOLIS && h->storage != SL_STORE_I8)
+            return fail(SL_EINVAL, "heat-bath and Swendsen-Wang updates need Ising byte storage");
+        if (value != SL_UPDATE_METROPOLIS && h->multihit > 0)
             return fail(SL_EINVAL, "multi-hit sweeps use the Metropolis rule");
+        if (value == SL_UPDATE_SW) {
+            if (h->j_layout != SL_J_UNIFORM)
+                return fail(SL_EINVAL, "Swendsen-Wang updates need a uniform coupling J");
+            if (h->N > 2147483648LL)
+                return fail(SL_EINVAL, "Swendsen-Wang updates need N <= 2^31");
+            const size_t need = sw_workspace_bytes(h->d, h->L);
+            if (h->ws_bytes < need) {
+                if (!h->owned_buf)
+                    return fail(SL_EINVAL, "Swendsen-Wang updates need a workspace of %zu bytes "
+                                           "(sl_attach_workspace)", need);
+                void* p = nullptr;
+                const cudaError_t e = cudaMalloc(&p, need);
+                if (e != cudaSuccess)
+                    return fail(SL_ENOMEM, "cudaMalloc(%zu): %s", need, cudaGetErrorString(e));
+                if (h->ws_owned) cudaFree(h->ws_owned);
+                h->ws_owned = p;
+                h->ws = p;
+                h->ws_bytes = need;
+            }
+        }
         h->update = (int)value;
         return SL_OK;
     case SL_OPT_MULTIHIT:
@@ -532,7 +571,40 @@ void sl_destroy(sl_lattice* h)
     if (h->graph) cudaGraphExecDestroy(h->graph);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->owned_buf) cudaFree(h->owned_buf);
+    if (h->ws_owned) cudaFree(h->ws_owned);
     delete h;
+}
+
+int sl_workspace_bytes(const sl_lattice* h, int update, size_t* bytes)
+{
+    if (!h || !bytes) return fail(SL_EINVAL, "NULL argument");
+    if (update != SL_UPDATE_METROPOLIS && update != SL_UPDATE_HEATBATH && update != SL_UPDATE_SW)
+        return fail(SL_EINVAL, "unknown update rule %d", update);
+    *bytes = update == SL_UPDATE_SW ? sw_workspace_bytes(h->d, h->L) : 0;
+    return SL_OK;
+}
+
+int sl_attach_workspace(sl_lattice* h, void* dev_buf, size_t bytes)
+{
+    if (!h) return fail(SL_EINVAL, "lattice is NULL");
+    if (dev_buf && (uintptr_t)dev_buf % kAlign)
+        return fail(SL_EINVAL, "workspace must be %zu-byte aligned", kAlign);
+    if (h->update == SL_UPDATE_SW && bytes < sw_workspace_bytes(h->d, h->L))
+        return fail(SL_ENOMEM, "workspace holds %zu bytes, %zu needed", bytes,
+                    sw_workspace_bytes(h->d, h->L));
+    const cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    if (h->ws_owned) {
+        cudaFree(h->ws_owned);
+        h->ws_owned = nullptr;
+    }
+    h->ws = dev_buf;
+    h->ws_bytes = dev_buf ? bytes : 0;
+    if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    return SL_OK;
 }
 
 const char* sl_strerror(int status)

@@ -22,6 +22,7 @@ SL_J_UNIFORM, SL_J_BONDS = 0, 1
 SL_STORE_I8, SL_STORE_BITS, SL_STORE_F32_ANGLE, SL_STORE_F32_VEC = 0, 1, 2, 3
 SL_OPT_RENORM_EVERY, SL_OPT_FAST_MATH, SL_OPT_KERNEL, SL_OPT_ROWS, SL_OPT_GRAPH = 1, 2, 3, 4, 5
 SL_OPT_UPDATE, SL_OPT_MULTIHIT, SL_OPT_TILE = 6, 7, 8
+SL_UPDATE_METROPOLIS, SL_UPDATE_HEATBATH, SL_UPDATE_SW = 0, 1, 2
 
 if not os.path.exists(LIB_PATH):
     raise ImportError("libspinmc.so is not built at %s; run paper_1107_5463_gb300.build.build()"
@@ -53,6 +54,8 @@ _sig("sl_get_state", _int, _vp, ctypes.POINTER(_u64), ctypes.POINTER(_i64))
 _sig("sl_set_state", _int, _vp, _i64)
 _sig("sl_set_option", _int, _vp, _int, _i64)
 _sig("sl_destroy", None, _vp)
+_sig("sl_workspace_bytes", _int, _vp, _int, ctypes.POINTER(_sz))
+_sig("sl_attach_workspace", _int, _vp, _vp, _sz)
 _sig("sl_batch_required_bytes", _int, _int, _vp, _int, _int, _vp, ctypes.POINTER(_sz))
 _sig("sl_batch_create", _int, _int, _vp, _int, _int, _vp, _u64, _vp, _sz, _vp, ctypes.POINTER(_vp))
 _sig("sl_batch_run", _int, _vp, _i64, _u64, _vp)
@@ -150,6 +153,16 @@ def sl_set_option(h, option, value):
 
 def sl_destroy(h):
     _lib.sl_destroy(h)
+
+
+def sl_workspace_bytes(h, update):
+    out = _sz()
+    _check(_lib.sl_workspace_bytes(h, update, ctypes.byref(out)), "sl_workspace_bytes")
+    return out.value
+
+
+def sl_attach_workspace(h, dev_buf, nbytes):
+    _check(_lib.sl_attach_workspace(h, _addr(dev_buf), nbytes), "sl_attach_workspace")
 
 
 def _i32_array(xs):
@@ -283,6 +296,16 @@ class Lattice:
 
     def set_option(self, option, value):
         sl_set_option(self.h, option, value)
+
+    def set_update(self, rule):
+        """Select an SL_UPDATE_* rule, attaching a torch-allocated workspace
+        first when the rule needs one."""
+        import torch
+        need = sl_workspace_bytes(self.h, rule)
+        if need and (getattr(self, "ws", None) is None or self.ws.numel() < need):
+            self.ws = torch.empty(need, dtype=torch.uint8, device=self.buf.device)
+            sl_attach_workspace(self.h, self.ws, need)
+        sl_set_option(self.h, SL_OPT_UPDATE, rule)
 
 
 class Batch:
