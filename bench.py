@@ -49,6 +49,12 @@ WORKLOADS = {
                                 desc="2D Ising, L=16384, one bit per spin"),
     "ising3d_L512_bits": dict(d=3, L=512, n=1, beta=0.2216546, storage="bits", bytes=0.375,
                               desc="3D Ising, L=512, one bit per spin"),
+    "ising2d_L8192_sw": dict(d=2, L=8192, n=1, beta=0.440687, storage="i8", bytes=16.0,
+                             update=2, paper_flips_per_ns=1 / 4.62,
+                             kernels="sw_local, sw_merge, sw_resolve, sw_flip, measurement",
+                             desc="2D Ising ferromagnet J=1, L=8192, int8 spins, beta_c, "
+                                  "Swendsen-Wang cluster updates (the paper's Table 1 "
+                                  "cluster row)"),
     "heis3d_L256_f32": dict(d=3, L=256, n=3, beta=0.693, storage="vec", bytes=36.0,
                             desc="3D Heisenberg J=1, L=256, FP32 unit vectors, beta=0.693, "
                                  "renormalised every 16 sweeps"),
@@ -220,6 +226,31 @@ def time_batch(spinmc, wl, steps, warmup, want_clocks, local, rank=0, world=1):
     return ms, cl, nclass
 
 
+def launch_shape(wl):
+    """(kernel launches per sweep, name of the dominant kernel) of a workload."""
+    d = wl["d"]
+    if wl.get("update") == 2:
+        return 5, "sw_local<%d> .. sw_flip (Swendsen-Wang)" % d
+    if wl.get("multihit"):
+        return 3, "ising_tile_kernel<%d,%d>" % (d, wl["tile"])
+    if wl["storage"] == "bits":
+        return 2, "bits_stream<%d,0>" % d
+    if wl["storage"] == "vec":
+        return 2, "heis_stream<%d,0>" % d
+    if wl["storage"] == "angle":
+        return 2, "xy_stream<0>"
+    return 2, "i8_stream<%d,0,0,%d>" % (d, 1 if wl.get("update") == 1 else 0)
+
+
+def configure(spinmc, lat, wl):
+    """Apply a workload's update rule and multi-hit options to a lattice."""
+    if wl.get("update"):
+        lat.set_update(wl["update"])
+    if wl.get("multihit"):
+        lat.set_option(spinmc.SL_OPT_TILE, wl["tile"])
+        lat.set_option(spinmc.SL_OPT_MULTIHIT, wl["multihit"])
+
+
 def time_sweeps(spinmc, wl, steps, warmup, replica, want_clocks, local):
     """Device-timed K sweeps of one lattice; returns (ms, clocks)."""
     import torch
@@ -227,11 +258,7 @@ def time_sweeps(spinmc, wl, steps, warmup, replica, want_clocks, local):
     storage = spinmc.SL_STORE_BITS if wl["storage"] == "bits" else None
     lat = spinmc.Lattice(wl["d"], wl["L"], n=wl["n"], seed=inputs.DEFAULT_SEED, replica=replica,
                          storage=storage)
-    if wl.get("update"):
-        lat.set_option(spinmc.SL_OPT_UPDATE, wl["update"])
-    if wl.get("multihit"):
-        lat.set_option(spinmc.SL_OPT_TILE, wl["tile"])
-        lat.set_option(spinmc.SL_OPT_MULTIHIT, wl["multihit"])
+    configure(spinmc, lat, wl)
     E = torch.empty(max(steps, warmup, 1), dtype=torch.float64, device="cuda")
     m = torch.empty_like(E)
     spinmc.sl_sweep_series(lat.h, wl["beta"], warmup, inputs.DEFAULT_SEED, E, m)
@@ -317,6 +344,7 @@ def e2e_run(spinmc, wl, jobs, sweeps_per_job, replica):
     host.numpy()[:] = inputs.ising_spins(d, L, inputs.DEFAULT_SEED + replica)
     out = torch.empty(2 * sweeps_per_job, dtype=torch.float64, pin_memory=True)
     lat = spinmc.Lattice(d, L, n=1, seed=inputs.DEFAULT_SEED, replica=replica)
+    configure(spinmc, lat, wl)
     E = torch.empty(sweeps_per_job, dtype=torch.float64, device="cuda")
     m = torch.empty_like(E)
     # warm: one job
@@ -333,29 +361,59 @@ def e2e_run(spinmc, wl, jobs, sweeps_per_job, replica):
         lat.stream.synchronize()
     dt = time.perf_counter() - t0
     lat.close()
-    flips = N * sweeps_per_job * jobs
+    flips = N * (wl.get("multihit") or 1) * sweeps_per_job * jobs
     return dict(value=flips / (dt * 1e9), unit=UNIT, h2d_bytes_per_step=N,
                 d2h_bytes_per_step=2 * 8 * sweeps_per_job, sweeps_per_step=sweeps_per_job,
                 steps=jobs)
 
 
+def oracle_state(wl, L=None):
+    """The oracle's start state for a workload (natural order)."""
+    import oracle
+    from paper_1107_5463_gb300 import inputs
+    d, L = wl["d"], L or wl["L"]
+    if wl["n"] == 3:
+        return oracle.heis_init(d, L, inputs.DEFAULT_SEED)
+    if wl["n"] == 2:
+        return oracle.xy_init(d, L, inputs.DEFAULT_SEED)
+    return oracle.ising_init(d, L, inputs.DEFAULT_SEED)
+
+
+def oracle_sweep(wl, s, t, L=None):
+    """One oracle sweep (with its E/|m| measurement) of the workload's rule."""
+    import oracle
+    from paper_1107_5463_gb300 import inputs
+    d, L, beta, seed = wl["d"], L or wl["L"], wl["beta"], inputs.DEFAULT_SEED
+    if wl["n"] == 3:
+        oracle.heis_sweeps(d, L, s, beta, seed, t, 1)
+    elif wl["n"] == 2:
+        oracle.xy_sweeps(d, L, s, beta, seed, t, 1)
+    elif wl.get("update") == 2:
+        oracle.ising_sw_sweeps(d, L, s, beta, seed, t, 1)
+    elif wl.get("update") == 1:
+        oracle.ising_heatbath_sweeps(d, L, s, beta, seed, t, 1)
+    elif wl.get("multihit"):
+        oracle.ising_multihit_sweeps(d, L, wl["tile"], wl["multihit"], s, beta, seed, t, 1)
+    else:
+        oracle.ising_sweeps(d, L, s, beta, seed, t, 1)
+
+
 def cpu_baseline(wl, target_s=15.0):
     """The oracle (plain C, single thread) on a bounded sample: whole sweeps
     of the full workload lattice, with the per-sweep measurement."""
-    import oracle
-    from paper_1107_5463_gb300 import inputs
     d, L = wl["d"], wl["L"]
     N = L ** d
-    s = oracle.ising_init(d, L, inputs.DEFAULT_SEED)
+    hits = wl.get("multihit") or 1
+    s = oracle_state(wl)
     t0 = time.perf_counter()
     nsw = 0
     while True:
-        oracle.ising_sweeps(d, L, s, wl["beta"], inputs.DEFAULT_SEED, nsw, 1)
+        oracle_sweep(wl, s, nsw)
         nsw += 1
         if time.perf_counter() - t0 > target_s or nsw >= 50:
             break
     dt = time.perf_counter() - t0
-    return dict(value=N * nsw / (dt * 1e9), unit=UNIT, cores=1, kind="oracle",
+    return dict(value=N * hits * nsw / (dt * 1e9), unit=UNIT, cores=1, kind="oracle",
                 sample="%d full sweep(s) of the %d^%d lattice incl. per-sweep E/|m|, "
                        "single-threaded C oracle, %.1f s" % (nsw, L, d, dt))
 
@@ -446,11 +504,12 @@ def main():
     N = L ** d
     ms, clocks, e_last = time_sweeps(spinmc, wl, args.steps, args.warmup, rank, rank == 0, local)
     ms = max_over_ranks(ms, world)
-    value = N * args.steps * world / (ms * 1e6)
+    hits = wl.get("multihit") or 1
+    value = N * hits * args.steps * world / (ms * 1e6)
 
-    launches_per_step = 2
-    launch_ms = ms / (args.steps * launches_per_step)
-    bytes_per_launch = wl["bytes"] * (N // 2)   # one colour pass
+    launches_per_step, kernel_name = launch_shape(wl)
+    launch_ms = ms / (args.steps * 2)
+    bytes_per_launch = wl["bytes"] * hits * (N // 2)   # half a sweep
     achieved_gbs = bytes_per_launch / (launch_ms * 1e-3) / 1e9
     traffic = recorded_traffic(args.workload)
     line = {
@@ -465,7 +524,7 @@ def main():
                    "parallelism": "replica per GPU" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
                      "frac": achieved_gbs / hbm, "peak_kind": peak_kind,
-                     "traffic": traffic, "kernel": "i8_stream<%d,0>" % d,
+                     "traffic": traffic, "kernel": kernel_name,
                      "bytes_per_launch": bytes_per_launch, "launch_ms": launch_ms},
         "gpu_launches": args.steps * launches_per_step + 1,
         "clocks": clocks,
@@ -473,7 +532,9 @@ def main():
     }
     if rank == 0:
         if args.e2e_jobs > 0:
-            line["e2e"] = e2e_run(spinmc, wl, args.e2e_jobs, 1000, rank)
+            if wl["n"] == 1:
+                per_job = 10 if wl.get("multihit") else (100 if wl.get("update") == 2 else 1000)
+                line["e2e"] = e2e_run(spinmc, wl, args.e2e_jobs, per_job, rank)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(wl)
         if not args.no_variants:
@@ -481,7 +542,7 @@ def main():
             for name, w in WORKLOADS.items():
                 if name == args.workload or w["storage"] == "batch":
                     continue
-                k = 10 if w.get("multihit") else 300
+                k = 10 if w.get("multihit") else (100 if w.get("update") == 2 else 300)
                 vms, _, _ = time_sweeps(spinmc, w, k, 3 if w.get("multihit") else 5, rank,
                                         False, local)
                 n = w["L"] ** w["d"]

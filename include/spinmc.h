@@ -85,7 +85,7 @@ extern "C" {
 /* update rules for SL_OPT_UPDATE */
 #define SL_UPDATE_METROPOLIS 0 /* Eq. 2 */
 #define SL_UPDATE_HEATBATH 1   /* Ising bytes: s_i = +1 iff u < 2^32 / (1 + exp(-2 beta J h_i)) */
-#define SL_UPDATE_SW 2         /* Ising bytes, uniform J, N <= 2^31: Swendsen-Wang cluster
+#define SL_UPDATE_SW 2         /* Ising bytes, uniform J, N <= 2^30: Swendsen-Wang cluster
                                   updates (Section 3), one per sweep index; needs a workspace
                                   (sl_workspace_bytes / sl_attach_workspace) */
 

@@ -4,22 +4,30 @@
 // cluster with probability 1/2; cluster identification in tiles first, then
 // amalgamation of the tiles through a union-and-find structure).
 //
-// One update is four kernels plus the measurement that closes every sweep:
-//   sw_local    one CTA per tile (64 x 32 sites in 2D, 32 x 16 x 16 in 3D):
+// One update is five kernels:
+//   sw_local    one CTA per tile (64 x 32 sites in 2D, 64 x 16 x 8 in 3D):
 //               loads the tile's spins and a one-site halo on its +x/+y/+z
-//               faces into shared memory, draws the bond uniforms, unites the
-//               sites joined by active bonds inside the tile with a
-//               shared-memory union-find (roots hooked smaller-index-wins by
-//               atomicCAS), writes every site's label (the natural index of
-//               its tile-local root, the smallest site of its tile cluster)
-//               and one bit per active bond that leaves the tile;
+//               faces into shared memory (one warp per row, one lane per site
+//               pair), draws the bond uniforms, joins each row's x-runs of
+//               active bonds through warp ballots, then joins the runs along
+//               y and z by rounds of hooking (atomicMin of the larger label
+//               onto the smaller) and pointer jumping in shared memory until
+//               nothing changes, which names every tile cluster by its
+//               smallest site (a y/z bond is skipped when the bond beside it
+//               already joins the same two runs), writes every site's label (the natural index
+//               of its tile root, the smallest site of its tile cluster) and
+//               one bit per active bond that leaves the tile;
 //   sw_merge    one thread per tile-face bond: unites the two labels of each
-//               active face bond in global memory (same hooking rule, finds
-//               with pointer jumping); afterwards the root of every cluster
-//               is its smallest site;
-//   sw_resolve  every site finds its root; roots draw their flip bit and keep
-//               it in bit 31 of their own label;
-//   sw_flip     every site reads its root's bit and flips.
+//               active face bond in global memory (same hooking rule);
+//               afterwards the root of every cluster is its smallest site;
+//   sw_resolve  every tile root points straight at its cluster's root; the
+//               cluster roots draw their flip bit;
+//   sw_flip     every site reads its root's bit (at most two lookups: its
+//               tile root, then the cluster root) and flips;
+//   sw_measure  E and M of the new configuration, closing the sweep.
+// Label words: bits 0-29 the parent (a site index, N <= 2^30), bit 31 marks
+// a tile root, bit 30 is the flip bit of a cluster root.  Every parent is a
+// smaller or equal index and, beyond a site's first step, a tile root.
 // Random numbers: the forward bond (i, i + e_mu) draws output 2 (i & 1) + mu
 // of Philox(i >> 1, t, replica, 5 << 1) in 2D, output mu of
 // Philox(i, t, replica, 5 << 1) in 3D; the cluster rooted at r flips iff the
@@ -34,7 +42,9 @@ namespace spinmc {
 namespace {
 
 constexpr uint32_t kSwBond = 5, kSwFlip = 6;
-constexpr uint32_t kMask = 0x7FFFFFFFu;
+constexpr uint32_t kMask = 0x3FFFFFFFu;     // parent index
+constexpr uint32_t kTileRoot = 0x80000000u;  // the site is a tile root
+constexpr uint32_t kFlipBit = 0x40000000u;   // the cluster rooted here flips
 constexpr int kSwThreads = 512;
 
 template <int D>
@@ -45,7 +55,7 @@ struct SwTile<2> {
 };
 template <>
 struct SwTile<3> {
-    static constexpr int TX = 32, TY = 16, TZ = 16;
+    static constexpr int TX = 64, TY = 16, TZ = 8;
 };
 
 template <int D>
@@ -80,7 +90,6 @@ int grid_for(long long work, int block)
 }
 
 using gref = cuda::atomic_ref<uint32_t, cuda::thread_scope_device>;
-using bref = cuda::atomic_ref<uint32_t, cuda::thread_scope_block>;
 
 __device__ __forceinline__ uint32_t gload(uint32_t* p)
 {
@@ -92,50 +101,24 @@ __device__ __forceinline__ void gstore(uint32_t* p, uint32_t v)
     gref(*p).store(v, cuda::memory_order_relaxed);
 }
 
-// shared-memory union-find over tile-local indices; parents only ever point
-// to smaller indices
-__device__ __forceinline__ uint32_t sfind(uint32_t* par, uint32_t x)
-{
-    while (true) {
-        const uint32_t p = bref(par[x]).load(cuda::memory_order_relaxed);
-        if (p == x) return x;
-        x = p;
-    }
-}
-
-__device__ __forceinline__ void sunion(uint32_t* par, uint32_t a, uint32_t b)
-{
-    a = sfind(par, a);
-    b = sfind(par, b);
-    while (a != b) {
-        if (a < b) {
-            const uint32_t t = a;
-            a = b;
-            b = t;
-        }
-        uint32_t expect = a;
-        if (bref(par[a]).compare_exchange_strong(expect, b, cuda::memory_order_relaxed)) return;
-        a = sfind(par, expect);
-        b = sfind(par, b);
-    }
-}
-
-// global find with pointer jumping: every store writes an ancestor into a
-// non-root entry, so concurrent finds and hooks stay consistent
+// global find with path halving (the same argument as in shared memory); a
+// halving store keeps the entry's tile-root bit
 __device__ __forceinline__ uint32_t gfind(uint32_t* lab, uint32_t x)
 {
-    uint32_t p = gload(lab + x);
-    if (p == x) return x;
-    uint32_t prev = x;
-    while (true) {
-        const uint32_t g = gload(lab + p);
+    uint32_t w = gload(lab + x);
+    uint32_t p = w & kMask;
+    while (p != x) {
+        const uint32_t g = gload(lab + p) & kMask;
         if (g == p) return p;
-        gstore(lab + prev, g);
-        prev = p;
-        p = g;
+        gstore(lab + x, g | (w & kTileRoot));
+        x = g;
+        w = gload(lab + x);
+        p = w & kMask;
     }
+    return x;
 }
 
+// roots are tile roots, so a root's word is r | kTileRoot
 __device__ __forceinline__ void gunion(uint32_t* lab, uint32_t a, uint32_t b)
 {
     a = gfind(lab, a);
@@ -146,18 +129,15 @@ __device__ __forceinline__ void gunion(uint32_t* lab, uint32_t a, uint32_t b)
             a = b;
             b = t;
         }
-        uint32_t expect = a;
-        if (gref(lab[a]).compare_exchange_strong(expect, b, cuda::memory_order_relaxed)) return;
-        a = gfind(lab, expect);
+        uint32_t expect = a | kTileRoot;
+        if (gref(lab[a]).compare_exchange_strong(expect, b | kTileRoot,
+                                                 cuda::memory_order_relaxed))
+            return;
+        a = gfind(lab, expect & kMask);
         b = gfind(lab, b);
     }
 }
 
-__device__ __forceinline__ int8_t spin_at(const SwArgs& a, int x, int y, int z)
-{
-    const long long i = x + (long long)a.L * (y + (long long)a.L * z);
-    return a.s[(x + y + z) & 1][i >> 1];
-}
 
 template <int D>
 __device__ __forceinline__ void tile_origin(const SwArgs& a, long long b, int& X0, int& Y0, int& Z0,
@@ -175,111 +155,246 @@ __device__ __forceinline__ void tile_origin(const SwArgs& a, long long b, int& X
     nz = D == 3 ? min(TZ, a.L - Z0) : 1;
 }
 
+__device__ __forceinline__ bool bond_active(const SwArgs& a, uint8_t s0, uint8_t s1, uint32_t u)
+{
+    return (int)(s0 ^ s1) == a.anti && !a.never && u <= a.thr;
+}
+
 template <int D>
-__global__ void __launch_bounds__(kSwThreads) sw_local(const SwArgs a)
+__global__ void __launch_bounds__(kSwThreads, 2) sw_local(const SwArgs a)
 {
     constexpr int TX = SwTile<D>::TX, TY = SwTile<D>::TY, TZ = SwTile<D>::TZ;
+    static_assert(TX == 64, "one warp lane per site pair of a 64-site row");
     constexpr int NS = TX * TY * TZ;
     constexpr int HX = TX + 2, HY = TY + 1, HZ = D == 3 ? TZ + 1 : 1;  // halo-padded spin tile
     constexpr int WORDS = SwFace<D>::WORDS;
+    constexpr int NW = kSwThreads / 32;
+    constexpr int ROWS = TY * TZ;
+    constexpr int RPW = ROWS / NW;  // rows per warp
     __shared__ uint32_t par[NS];
     __shared__ uint8_t sp[HZ * HY * HX];
     __shared__ uint32_t fm[WORDS];
+    // per row, per lane bit: active in-tile bonds of the lane's even (0) and
+    // odd (1) site along +x, +y and +z
+    __shared__ uint32_t bx[2][ROWS], by[2][ROWS], bz[2][D == 3 ? ROWS : 1];
 
     const long long b = blockIdx.x;
     int X0, Y0, Z0, nx, ny, nz;
     tile_origin<D>(a, b, X0, Y0, Z0, nx, ny, nz);
-    const int L = a.L;
+    const uint32_t L = (uint32_t)a.L;
     const uint32_t t = (uint32_t)a.ctrl->t;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lx0 = 2 * lane;
+    const bool ex = lx0 < nx;  // the lane's site pair lies in the tile
 
-    for (int l = threadIdx.x; l < NS; l += blockDim.x) par[l] = (uint32_t)l;
     for (int w = threadIdx.x; w < WORDS; w += blockDim.x) fm[w] = 0u;
-    // the tile's spins plus the +x column, +y row and +z plane (no edges)
-    for (int q = threadIdx.x; q < HZ * HY * (TX / 2 + 1); q += blockDim.x) {
-        const int kx = q % (TX / 2 + 1);
-        const int ly = (q / (TX / 2 + 1)) % HY;
-        const int lz = q / ((TX / 2 + 1) * HY);
-        if (ly > ny || lz > (D == 3 ? nz : 0)) continue;
-        const int hy = ly == ny, hz = D == 3 && lz == nz;
-        const int y = Y0 + ly == L ? 0 : Y0 + ly;
-        const int z = D == 3 ? (Z0 + lz == L ? 0 : Z0 + lz) : 0;
-        if (kx < nx / 2) {
-            if (hy + hz > 1) continue;
-            const int x = X0 + 2 * kx;
-            sp[(lz * HY + ly) * HX + 2 * kx] = (uint8_t)spin_at(a, x, y, z);
-            sp[(lz * HY + ly) * HX + 2 * kx + 1] = (uint8_t)spin_at(a, x + 1, y, z);
-        } else if (kx == TX / 2) {
-            if (hy || hz) continue;
-            const int x = X0 + nx == L ? 0 : X0 + nx;
-            sp[(lz * HY + ly) * HX + nx] = (uint8_t)spin_at(a, x, y, z);
+    // the tile's rows plus the +y row and +z plane (one warp per row), and
+    // the +x column
+    for (int r = warp; r < HY * HZ; r += NW) {
+        const int ly = r % HY, lz = r / HY;
+        if (ly > ny || (D == 3 && lz > nz)) continue;
+        const bool hy = ly == ny, hz = D == 3 && lz == nz;
+        if (hy && hz) continue;
+        const uint32_t y = (uint32_t)(Y0 + ly) == L ? 0u : (uint32_t)(Y0 + ly);
+        const uint32_t z = D == 3 ? ((uint32_t)(Z0 + lz) == L ? 0u : (uint32_t)(Z0 + lz)) : 0u;
+        const uint32_t rowbase = L * (y + L * z);
+        const int ce = (int)((y + z) & 1u);  // colour of the even-x sites
+        uint8_t* dst = sp + (lz * HY + ly) * HX;
+        if (ex) {
+            const uint32_t j = (rowbase + (uint32_t)(X0 + lx0)) >> 1;
+            dst[lx0] = (uint8_t)a.s[ce][j];
+            dst[lx0 + 1] = (uint8_t)a.s[ce ^ 1][j];
+        }
+        if (lane == 0 && !hy && !hz) {
+            const uint32_t x = (uint32_t)(X0 + nx) == L ? 0u : (uint32_t)(X0 + nx);
+            dst[nx] = (uint8_t)a.s[(x + y + z) & 1u][(rowbase + x) >> 1];
         }
     }
     __syncthreads();
 
-    // bond activation; unite inside the tile, record bonds leaving it
-    for (int p = threadIdx.x; p < NS / 2; p += blockDim.x) {
-        const int lx0 = 2 * (p % (TX / 2));
-        const int ly = (p / (TX / 2)) % TY;
-        const int lz = p / ((TX / 2) * TY);
-        if (lx0 >= nx || ly >= ny || lz >= nz) continue;
-        const long long i0 = (X0 + lx0) + (long long)L * ((Y0 + ly) + (long long)L * (Z0 + lz));
-        uint32_t u[2][3];
-        if (D == 2) {
-            const uint4 r = philox4x32_10(
-                make_uint4((uint32_t)(i0 >> 1), t, a.replica, kSwBond << 1), a.rk);
-            u[0][0] = r.x;
-            u[0][1] = r.y;
-            u[1][0] = r.z;
-            u[1][1] = r.w;
-            u[0][2] = u[1][2] = 0u;
-        } else {
+    // Bond activation, one warp per row.  A row splits into x-runs of sites
+    // joined by active bonds; every site's parent becomes the first site of
+    // its run, found from the warp's ballots.  Bonds leaving the tile set
+    // their face bit.
+#pragma unroll
+    for (int k = 0; k < RPW; ++k) {
+        const int row = warp + NW * k;
+        const int ly = row % TY, lz = row / TY;
+        if (ly >= ny || lz >= nz) continue;  // uniform across the warp
+        const int so = (lz * HY + ly) * HX + lx0;
+        bool xb0 = false, xb1 = false, yb[2] = {false, false}, zb[2] = {false, false};
+        if (ex) {
+            const uint32_t i0 = (uint32_t)(X0 + lx0) + L * ((uint32_t)(Y0 + ly) + L * (uint32_t)(Z0 + lz));
+            // uniforms of the x / y / z bonds of the even (e = 0) and odd site
+            uint4 r0, r1;
+            if (D == 2) {
+                r0 = philox4x32_10(make_uint4(i0 >> 1, t, a.replica, kSwBond << 1), a.rk);
+                r1 = make_uint4(r0.z, r0.w, 0u, 0u);
+            } else {
+                r0 = philox4x32_10(make_uint4(i0, t, a.replica, kSwBond << 1), a.rk);
+                r1 = philox4x32_10(make_uint4(i0 + 1, t, a.replica, kSwBond << 1), a.rk);
+            }
+            const uint8_t s0 = sp[so], s1 = sp[so + 1], s2 = sp[so + 2];
+            xb0 = bond_active(a, s0, s1, r0.x);
+            xb1 = bond_active(a, s1, s2, r1.x);
 #pragma unroll
             for (int e = 0; e < 2; ++e) {
-                const uint4 r = philox4x32_10(
-                    make_uint4((uint32_t)(i0 + e), t, a.replica, kSwBond << 1), a.rk);
-                u[e][0] = r.x;
-                u[e][1] = r.y;
-                u[e][2] = r.z;
-            }
-        }
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            const int lx = lx0 + e;
-            const int so = (lz * HY + ly) * HX + lx;
-            const uint8_t own = sp[so];
-            const uint32_t l = (uint32_t)(lx + TX * (ly + TY * lz));
-#pragma unroll
-            for (int mu = 0; mu < D; ++mu) {
-                const int nb_off = mu == 0 ? 1 : (mu == 1 ? HX : HX * HY);
-                const uint8_t nb = sp[so + nb_off];
-                const int sat = (int)(own ^ nb) == a.anti;
-                if (!sat || a.never || u[e][mu] > a.thr) continue;
-                const int crosses = mu == 0 ? lx + 1 == nx : (mu == 1 ? ly + 1 == ny : lz + 1 == nz);
-                if (crosses) {
-                    const int bit = mu == 0 ? ly + TY * lz
-                                            : (mu == 1 ? TY * TZ + lx + TX * lz
-                                                       : TY * TZ + TX * TZ + lx + TX * ly);
-                    atomicOr(&fm[bit >> 5], 1u << (bit & 31));
-                } else {
-                    const uint32_t stride = mu == 0 ? 1u : (mu == 1 ? (uint32_t)TX : (uint32_t)(TX * TY));
-                    sunion(par, l, l + stride);
+                const uint8_t own = e ? s1 : s0;
+                const int lx = lx0 + e;
+                const uint4 re = e ? r1 : r0;
+                if (bond_active(a, own, sp[so + e + HX], re.y)) {
+                    if (ly + 1 == ny) {
+                        const int bit = TY * TZ + lx + TX * lz;
+                        atomicOr(&fm[bit >> 5], 1u << (bit & 31));
+                    } else {
+                        yb[e] = true;
+                    }
+                }
+                if (D == 3 && bond_active(a, own, sp[so + e + HX * HY], re.z)) {
+                    if (lz + 1 == nz) {
+                        const int bit = TY * TZ + TX * TZ + lx + TX * ly;
+                        atomicOr(&fm[bit >> 5], 1u << (bit & 31));
+                    } else {
+                        zb[e] = true;
+                    }
                 }
             }
         }
+        const bool xcross = xb1 && lx0 + 2 == nx;
+        if (xcross) {
+            const int bit = ly + TY * lz;
+            atomicOr(&fm[bit >> 5], 1u << (bit & 31));
+        }
+        const uint32_t B0 = __ballot_sync(0xFFFFFFFFu, xb0);
+        const uint32_t B1 = __ballot_sync(0xFFFFFFFFu, xb1 && !xcross);
+        const uint32_t Y0b = __ballot_sync(0xFFFFFFFFu, yb[0]);
+        const uint32_t Y1b = __ballot_sync(0xFFFFFFFFu, yb[1]);
+        uint32_t Z0b = 0u, Z1b = 0u;
+        if (D == 3) {
+            Z0b = __ballot_sync(0xFFFFFFFFu, zb[0]);
+            Z1b = __ballot_sync(0xFFFFFFFFu, zb[1]);
+        }
+        if (lane == 0) {
+            bx[0][row] = B0;
+            bx[1][row] = B1;
+            by[0][row] = Y0b;
+            by[1][row] = Y1b;
+            if (D == 3) {
+                bz[0][D == 3 ? row : 0] = Z0b;
+                bz[1][D == 3 ? row : 0] = Z1b;
+            }
+        }
+        if (ex) {
+            // run starts: the even site starts a run unless the bond from the
+            // previous lane's odd site is active, the odd site unless xb0 is
+            const uint32_t R0 = ~(B1 << 1);
+            const uint32_t R1 = ~B0;
+            int rs0 = 2 * (31 - __clz(R0 & ((2u << lane) - 1u)));
+            const uint32_t m1 = R1 & ((1u << lane) - 1u);
+            if (m1) rs0 = max(rs0, 2 * (31 - __clz(m1)) + 1);
+            const int rs1 = xb0 ? rs0 : lx0 + 1;
+            const int base = TX * (ly + TY * lz);
+            par[base + lx0] = (uint32_t)(base + rs0);
+            par[base + lx0 + 1] = (uint32_t)(base + rs1);
+        }
     }
     __syncthreads();
-    for (int l = threadIdx.x; l < NS; l += blockDim.x) par[l] = sfind(par, (uint32_t)l);
-    __syncthreads();
 
-    // labels: the natural index of each site's tile root
-    for (int l = threadIdx.x; l < NS; l += blockDim.x) {
-        const int lx = l % TX, ly = (l / TX) % TY, lz = l / (TX * TY);
-        if (lx >= nx || ly >= ny || lz >= nz) continue;
-        const uint32_t r = par[l];
-        const int rx = (int)(r % TX), ry = (int)((r / TX) % TY), rz = (int)(r / (TX * TY));
-        const long long i = (X0 + lx) + (long long)L * ((Y0 + ly) + (long long)L * (Z0 + lz));
-        const long long ri = (X0 + rx) + (long long)L * ((Y0 + ry) + (long long)L * (Z0 + rz));
-        a.lab[i] = (uint32_t)ri;
+    // Join the runs along y and z by rounds of hooking and pointer jumping:
+    // every bond (u, v) whose ends carry different labels lowers the larger
+    // label's entry to the smaller (atomicMin), then every site follows its
+    // parents to a root and keeps it, until a round changes nothing.  Labels
+    // only decrease and stay inside the cluster, so the fixed point names
+    // every tile cluster by its smallest site.  A bond is left out when the
+    // bond at x - 1 is active and x - 1, x are joined in both rows (the same
+    // two runs).
+    uint32_t pend = 0;  // bit (k, e, mu): y/z bond of row k, site e, direction mu
+    if (ex) {
+#pragma unroll
+        for (int k = 0; k < RPW; ++k) {
+            const int row = warp + NW * k;
+            const int ly = row % TY, lz = row / TY;
+            if (ly >= ny || lz >= nz) continue;
+#pragma unroll
+            for (int mu = 1; mu < D; ++mu) {
+                const int nrow = mu == 1 ? row + 1 : row + TY;
+                const uint32_t c0 = mu == 1 ? by[0][row] : bz[0][D == 3 ? row : 0];
+                const uint32_t c1 = mu == 1 ? by[1][row] : bz[1][D == 3 ? row : 0];
+                // even site 2k: its left neighbour is lane k-1's odd site
+                bool p0 = (c0 >> lane) & 1u;
+                if (p0 && lane > 0 && ((c1 >> (lane - 1)) & 1u) &&
+                    ((bx[1][row] >> (lane - 1)) & 1u) && ((bx[1][nrow] >> (lane - 1)) & 1u))
+                    p0 = false;
+                // odd site 2k+1: its left neighbour is lane k's even site
+                bool p1 = (c1 >> lane) & 1u;
+                if (p1 && ((c0 >> lane) & 1u) && ((bx[0][row] >> lane) & 1u) &&
+                    ((bx[0][nrow] >> lane) & 1u))
+                    p1 = false;
+                const int base = k * 2 * (D - 1) + (mu - 1);
+                if (p0) pend |= 1u << base;
+                if (p1) pend |= 1u << (base + (D - 1));
+            }
+        }
+    }
+    volatile uint32_t* vp = par;
+    while (true) {
+        bool changed = false;
+        for (uint32_t bits = pend; bits; bits &= bits - 1) {
+            const int bit = __ffs(bits) - 1;
+            const int k = bit / (2 * (D - 1));
+            const int e = (bit / (D - 1)) & 1;
+            const int mu = 1 + bit % (D - 1);
+            const uint32_t u = (uint32_t)(lx0 + e + TX * (warp + NW * k));
+            const uint32_t v = u + (mu == 1 ? (uint32_t)TX : (uint32_t)(TX * TY));
+            const uint32_t pu = vp[u], pv = vp[v];
+            if (pu != pv) {
+                atomicMin(par + max(pu, pv), min(pu, pv));
+                changed = true;
+            }
+        }
+        __syncthreads();
+        if (ex) {
+#pragma unroll
+            for (int k = 0; k < RPW; ++k) {
+                const int row = warp + NW * k;
+                const int ly = row % TY, lz = row / TY;
+                if (ly >= ny || lz >= nz) continue;
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const uint32_t l = (uint32_t)(lx0 + e + TX * row);
+                    uint32_t p = vp[l];
+                    while (true) {
+                        const uint32_t q = vp[p];
+                        if (q == p) break;
+                        p = q;
+                    }
+                    vp[l] = p;
+                }
+            }
+        }
+        if (!__syncthreads_or(changed)) break;
+    }
+
+    // labels: the natural index of each site's tile root; tile roots marked
+    if (ex) {
+#pragma unroll
+        for (int k = 0; k < RPW; ++k) {
+            const int row = warp + NW * k;
+            const int ly = row % TY, lz = row / TY;
+            if (ly >= ny || lz >= nz) continue;
+            const uint32_t l0 = (uint32_t)(lx0 + TX * row);
+            uint32_t w[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const uint32_t m = par[l0 + e];  // smallest site of the tile cluster
+                const uint32_t rx = m % TX, rrow = m / TX;
+                const uint32_t ry = rrow % TY, rz = rrow / TY;
+                w[e] = ((uint32_t)X0 + rx) + L * (((uint32_t)Y0 + ry) + L * ((uint32_t)Z0 + rz));
+                if (m == l0 + e) w[e] |= kTileRoot;
+            }
+            const uint32_t i0 = (uint32_t)(X0 + lx0) + L * ((uint32_t)(Y0 + ly) + L * (uint32_t)(Z0 + lz));
+            *reinterpret_cast<uint2*>(a.lab + i0) = make_uint2(w[0], w[1]);
+        }
     }
     for (int w = threadIdx.x; w < WORDS; w += blockDim.x) a.face[b * WORDS + w] = fm[w];
 }
@@ -323,61 +438,171 @@ __global__ void __launch_bounds__(256) sw_merge(const SwArgs a)
         if (mu == 0) xn = x + 1 == L ? 0 : x + 1;
         if (mu == 1) yn = y + 1 == L ? 0 : y + 1;
         if (mu == 2) zn = z + 1 == L ? 0 : z + 1;
-        const uint32_t i = (uint32_t)(x + (long long)L * (y + (long long)L * z));
-        const uint32_t j = (uint32_t)(xn + (long long)L * (yn + (long long)L * zn));
+        const uint32_t i = (uint32_t)x + (uint32_t)L * ((uint32_t)y + (uint32_t)L * (uint32_t)z);
+        const uint32_t j = (uint32_t)xn + (uint32_t)L * ((uint32_t)yn + (uint32_t)L * (uint32_t)zn);
         gunion(a.lab, i, j);
     }
 }
 
+// Every tile root is pointed straight at its cluster's root; cluster roots
+// draw the flip bit.  A thread owns four consecutive labels and is their only
+// writer here (non-tile-root labels are not touched), so it loads and stores
+// them as one vector.
 __global__ void __launch_bounds__(256) sw_resolve(const SwArgs a)
 {
     const uint32_t t = (uint32_t)a.ctrl->t;
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < a.N;
+    const long long n4 = a.N >> 2;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n4;
          q += (long long)gridDim.x * blockDim.x) {
-        const uint32_t i = (uint32_t)q;
-        const uint32_t p0 = gload(a.lab + i) & kMask;
-        if (p0 == i) {
-            const uint4 r = philox4x32_10(make_uint4(i, t, a.replica, kSwFlip << 1), a.rk);
-            gstore(a.lab + i, i | (r.x & 0x80000000u));
-            continue;
+        const uint4 v = __ldcg(reinterpret_cast<const uint4*>(a.lab) + q);
+        uint32_t w[4] = {v.x, v.y, v.z, v.w};
+        if (!((w[0] | w[1] | w[2] | w[3]) & kTileRoot)) continue;
+        bool changed = false;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            if (!(w[e] & kTileRoot)) continue;
+            const uint32_t i = (uint32_t)(4 * q + e);
+            const uint32_t p0 = w[e] & kMask;
+            if (p0 == i) {
+                const uint4 r = philox4x32_10(make_uint4(i, t, a.replica, kSwFlip << 1), a.rk);
+                if (r.x >> 31) {
+                    w[e] |= kFlipBit;
+                    changed = true;
+                }
+                continue;
+            }
+            uint32_t p = p0;
+            while (true) {
+                const uint32_t g = gload(a.lab + p) & kMask;
+                if (g == p) break;
+                p = g;
+            }
+            if (p != p0) {
+                w[e] = p | kTileRoot;
+                changed = true;
+            }
         }
-        uint32_t p = p0;
-        while (true) {
-            const uint32_t g = gload(a.lab + p) & kMask;
-            if (g == p) break;
-            p = g;
-        }
-        if (p != p0) gstore(a.lab + i, p);
+        if (changed)
+            __stcg(reinterpret_cast<uint4*>(a.lab) + q, make_uint4(w[0], w[1], w[2], w[3]));
     }
 }
 
+// flip bit of site i's cluster from its label word l: the parent is the site
+// itself (a cluster root), a cluster root, or a tile root whose word names
+// the cluster root
+__device__ __forceinline__ uint32_t root_bit(const SwArgs& a, uint32_t i, uint32_t l)
+{
+    uint32_t r = l & kMask, word = l;
+    while (r != i) {
+        word = __ldg(a.lab + r);
+        const uint32_t g = word & kMask;
+        if (g == r) break;
+        i = r;
+        r = g;
+    }
+    return (word & kFlipBit) ? 1u : 0u;
+}
+
+// Every site flips iff its cluster's root drew the flip bit.  A thread takes
+// four site pairs (x even, x + 1): eight labels and one 32-bit word of each
+// colour array.
 __global__ void __launch_bounds__(256) sw_flip(const SwArgs a)
 {
     const long long H = a.N >> 1;
+    const long long nq = (H + 3) >> 2;
     const int L = a.L;
-    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < H;
-         j += (long long)gridDim.x * blockDim.x) {
-        const long long i0 = 2 * j;
-        const long long row = i0 / L;  // y + L z
-        const int c0 = (int)((row % L + row / L) & 1);
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nq;
+         q += (long long)gridDim.x * blockDim.x) {
+        const long long j0 = 4 * q;
+        if (j0 + 4 <= H) {
+            const uint4 la = __ldg(reinterpret_cast<const uint4*>(a.lab) + 2 * q);
+            const uint4 lb = __ldg(reinterpret_cast<const uint4*>(a.lab) + 2 * q + 1);
+            const uint32_t lw[8] = {la.x, la.y, la.z, la.w, lb.x, lb.y, lb.z, lb.w};
+            uint32_t fl0 = 0u, fl1 = 0u;  // flips of colour 0 / colour 1 bytes
 #pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            const uint32_t i = (uint32_t)(i0 + e);
-            const uint32_t l = gload(a.lab + i);
-            uint32_t r = l & kMask, root_word = l;
-            if (r != i) {
-                while (true) {
-                    root_word = gload(a.lab + r);
-                    const uint32_t g = root_word & kMask;
-                    if (g == r) break;
-                    r = g;
+            for (int e = 0; e < 4; ++e) {
+                const long long i0 = 2 * (j0 + e);
+                const long long row = i0 / L;
+                const bool c0 = ((row % L + row / L) & 1) != 0;  // colour of the even site
+                const uint32_t fe = root_bit(a, (uint32_t)i0, lw[2 * e]) << (8 * e);
+                const uint32_t fo = root_bit(a, (uint32_t)i0 + 1, lw[2 * e + 1]) << (8 * e);
+                fl0 |= c0 ? fo : fe;
+                fl1 |= c0 ? fe : fo;
+            }
+            if (fl0) reinterpret_cast<uint32_t*>(a.s[0])[q] ^= fl0;
+            if (fl1) reinterpret_cast<uint32_t*>(a.s[1])[q] ^= fl1;
+        } else {
+            for (long long j = j0; j < H; ++j) {
+                const long long i0 = 2 * j;
+                const long long row = i0 / L;
+                const int c0 = (int)((row % L + row / L) & 1);
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const uint32_t i = (uint32_t)(i0 + e);
+                    const int8_t f = (int8_t)root_bit(a, i, __ldg(a.lab + i));
+                    int8_t* sp = a.s[c0 ^ e] + j;
+                    *sp = (int8_t)(*sp ^ f);
                 }
             }
-            const int8_t f = (int8_t)(root_word >> 31);
-            int8_t* sp = a.s[c0 ^ e] + j;
-            *sp = (int8_t)(*sp ^ f);
         }
     }
+}
+
+// E and M after an update, streaming 32-bit words (four colour-1 sites) of
+// every colour-1 row against the colour-0 rows around it; closes the sweep
+// like every other measured pass (series entry, sweep counter + 1).  Needs
+// L % 8 == 0.  Every bond touches exactly one colour-1 site, so the bond sum
+// is sum over colour-1 sites of 2d - 2 (unlike neighbours).
+template <int D>
+__global__ void __launch_bounds__(256) sw_measure(const SwArgs a, Partial* partials, double J)
+{
+    __shared__ long long red[32];
+    const int L = a.L, W = L / 2, Q = W / 4;
+    const long long rows = (long long)L * (D == 3 ? L : 1);
+    const long long items = rows * Q;
+    const uint32_t* own = reinterpret_cast<const uint32_t*>(a.s[1]);
+    const uint32_t* oth = reinterpret_cast<const uint32_t*>(a.s[0]);
+    const uint32_t ones = 0x01010101u;
+    long long bond = 0, down = 0;
+    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < items;
+         it += (long long)gridDim.x * blockDim.x) {
+        const int q = (int)(it % Q);
+        const long long row = it / Q;
+        const int y = (int)(row % L), z = D == 3 ? (int)(row / L) : 0;
+        const int p = (y + z + 1) & 1;
+        const long long base = row * Q;
+        const uint32_t A = __ldcs(own + base + q);
+        const uint32_t cur = __ldg(oth + base + q);
+        const uint32_t S = p ? __funnelshift_r(cur, __ldg(oth + base + (q + 1 == Q ? 0 : q + 1)), 8)
+                             : __funnelshift_l(__ldg(oth + base + (q == 0 ? Q - 1 : q - 1)), cur, 8);
+        const long long ym = row - y + (y == 0 ? L - 1 : y - 1);
+        const long long yp = row - y + (y == L - 1 ? 0 : y + 1);
+        uint32_t nd = cur + S + __ldg(oth + ym * Q + q) + __ldg(oth + yp * Q + q);
+        if (D == 3) {
+            const long long zm = (z == 0 ? L - 1 : z - 1), zp = (z == L - 1 ? 0 : z + 1);
+            nd += __ldg(oth + (zm * L + y) * Q + q) + __ldg(oth + (zp * L + y) * Q + q);
+        }
+        const uint32_t na = (nd ^ (A * 7u)) - A * (uint32_t)(7 - 2 * D);
+        bond += 8 * D - 2 * (long long)__dp4a(na, ones, 0u);
+        down += (long long)__dp4a(A, ones, __dp4a(cur, ones, 0u));
+    }
+    Partial mine;
+    mine.i0 = block_sum(bond, red);
+    mine.i1 = block_sum(down, red);
+    mine.f[0] = mine.f[1] = mine.f[2] = mine.f[3] = 0.0;
+    finish_pass(a.ctrl, partials, mine, [&](const Partial& tot) {
+        Ctrl* C = a.ctrl;
+        const double E = -J * (double)tot.i0;
+        const double M = (double)(a.N - 2 * tot.i1);
+        C->obs[0] = E;
+        C->obs[1] = M;
+        C->obs[2] = 0.0;
+        C->obs[3] = 0.0;
+        const long long k = (long long)C->t - C->series_base;
+        if (C->series_E) C->series_E[k] = E;
+        if (C->series_absm) C->series_absm[k] = fabs(M) / (double)a.N;
+        C->t = C->t + 1;
+    });
 }
 
 template <int D>
@@ -396,8 +621,8 @@ cudaError_t sw_update(const SwArgs& a0, cudaStream_t s)
     const long long mergers = a.ntiles * SwFace<D>::WORDS * 32;
     sw_local<D><<<(unsigned)a.ntiles, kSwThreads, 0, s>>>(a);
     sw_merge<D><<<grid_for(mergers, 256), 256, 0, s>>>(a);
-    sw_resolve<<<grid_for(a.N, 256), 256, 0, s>>>(a);
-    sw_flip<<<grid_for(a.N / 2, 256), 256, 0, s>>>(a);
+    sw_resolve<<<grid_for(a.N / 4, 256), 256, 0, s>>>(a);
+    sw_flip<<<grid_for((a.N / 2 + 3) / 4, 256), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -432,7 +657,16 @@ cudaError_t ising_sw_sweeps(const sl_lattice* h, const SweepParams& p, int64_t c
     a.ctrl = h->ctrl;
     for (int64_t k = 0; k < count; ++k) {
         cudaError_t e = h->d == 2 ? sw_update<2>(a, s) : sw_update<3>(a, s);
-        if (e == cudaSuccess) e = ising_i8_measure_advance(h, s);
+        if (e == cudaSuccess) {
+            if (h->L % 8 == 0) {
+                const long long items = (long long)h->L * (h->d == 3 ? h->L : 1) * (h->L / 8);
+                if (h->d == 2) sw_measure<2><<<grid_for(items, 256), 256, 0, s>>>(a, h->partials, h->J);
+                else sw_measure<3><<<grid_for(items, 256), 256, 0, s>>>(a, h->partials, h->J);
+                e = cudaGetLastError();
+            } else {
+                e = ising_i8_measure_advance(h, s);
+            }
+        }
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

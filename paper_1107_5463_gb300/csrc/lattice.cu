@@ -524,8 +524,8 @@ int sl_set_option(sl_lattice* h, int option, int64_t value)
         if (value == SL_UPDATE_SW) {
             if (h->j_layout != SL_J_UNIFORM)
                 return fail(SL_EINVAL, "Swendsen-Wang updates need a uniform coupling J");
-            if (h->N > 2147483648LL)
-                return fail(SL_EINVAL, "Swendsen-Wang updates need N <= 2^31");
+            if (h->N > 1073741824LL)
+                return fail(SL_EINVAL, "Swendsen-Wang updates need N <= 2^30");
             const size_t need = sw_workspace_bytes(h->d, h->L);
             if (h->ws_bytes < need) {
                 if (!h->owned_buf)
