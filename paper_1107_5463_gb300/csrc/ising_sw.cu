@@ -161,7 +161,7 @@ __device__ __forceinline__ bool bond_active(const SwArgs& a, uint8_t s0, uint8_t
 }
 
 template <int D>
-__global__ void __launch_bounds__(kSwThreads, 2) sw_local(const SwArgs a)
+__global__ void __launch_bounds__(kSwThreads, 3) sw_local(const SwArgs a)
 {
     constexpr int TX = SwTile<D>::TX, TY = SwTile<D>::TY, TZ = SwTile<D>::TZ;
     static_assert(TX == 64, "one warp lane per site pair of a 64-site row");
