@@ -45,6 +45,18 @@ def lib():
         L.orc_ising_sw_sweeps.argtypes = [_int, _int, _dbl, _dbl, _u64, _u32, _i64, _i64, _i8p,
                                           _vp, _vp, _vp, _vp]
         L.orc_ising_sw_sweeps.restype = _int
+        L.orc_walker_init.argtypes = [_int, _int, _int, _u64, _u32, _i8p, ctypes.POINTER(_int)]
+        L.orc_walker_init.restype = _int
+        L.orc_wl_sweeps.argtypes = [_int, _int, _int, _u64, _u32, _i64, _i64, _int, _int, _i8p,
+                                    ctypes.POINTER(_int), _i64p, _u32p,
+                                    ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(_int), _dbl]
+        L.orc_wl_sweeps.restype = _i64
+        L.orc_muca_sweeps.argtypes = [_int, _int, _int, _f64p, _u64, _u32, _i64, _i64, _i8p,
+                                      ctypes.POINTER(_int),
+                                      np.ctypeslib.ndpointer(np.uint64, flags="C_CONTIGUOUS")]
+        L.orc_dos_glue.argtypes = [_int, _int, _i32p, _i32p, _f64p, _int,
+                                   np.ctypeslib.ndpointer(np.uint64, flags="C_CONTIGUOUS"), _f64p]
+        L.orc_dos_glue.restype = _int
         L.orc_xy_init.argtypes = [_int, _int, _u64, _u32, _f64p]
         L.orc_heis_init.argtypes = [_int, _int, _u64, _u32, _f64p]
         L.orc_xy_measure.argtypes = [_int, _int, _dbl, _vp, _f64p, ctypes.POINTER(_dbl), _f64p]
@@ -171,6 +183,64 @@ def ising_sw_sweeps(d, L, s, beta, seed, t0, nsweeps, J=1.0, replica=0, series=T
     if clusters:
         return E, m, act, lab
     return E, m
+
+
+class Walker:
+    """One windowed MUCA / Wang-Landau walker of the 2D Ising model (oracle
+    state: natural-order +-1 spins, level, and the per-window arrays)."""
+
+    def __init__(self, L, klo, khi, seed, walker):
+        assert L >= 4 and L & (L - 1) == 0, "L must be a power of two"
+        self.L, self.klo, self.khi, self.seed, self.walker = L, klo, khi, seed, walker
+        self.K = khi - klo + 1
+        self.s = np.empty(L * L, np.int8)
+        lev = _int()
+        rc = lib().orc_walker_init(L, klo, khi, seed, walker, self.s, ctypes.byref(lev))
+        if rc != 0:
+            raise RuntimeError("walker %d did not reach levels [%d, %d]" % (walker, klo, khi))
+        self.level = lev.value
+        self.S = np.zeros(self.K, np.int64)
+        self.H = np.zeros(self.K, np.uint32)
+        self.visited = 0
+        self.stage = 0
+        self.t = 0
+
+    def wl(self, nsweeps, final_stage, flat_percent=80, tie_tol=0.0, seed=None):
+        lev, vis, st = _int(self.level), ctypes.c_uint64(self.visited), _int(self.stage)
+        ties = lib().orc_wl_sweeps(self.L, self.klo, self.khi,
+                                   self.seed if seed is None else seed, self.walker, self.t,
+                                   nsweeps, final_stage, flat_percent, self.s, ctypes.byref(lev),
+                                   self.S, self.H, ctypes.byref(vis), ctypes.byref(st), tie_tol)
+        self.level, self.visited, self.stage = lev.value, vis.value, st.value
+        self.t += nsweeps
+        return ties
+
+    def muca(self, Sw, nsweeps, seed=None):
+        """Multicanonical sweeps with weights Sw (ln W over the window levels);
+        returns the histogram of this run."""
+        Sw = np.ascontiguousarray(Sw, np.float64)
+        assert Sw.size == self.K
+        H = np.zeros(self.K, np.uint64)
+        lev = _int(self.level)
+        lib().orc_muca_sweeps(self.L, self.klo, self.khi, Sw, self.seed if seed is None else seed,
+                              self.walker, self.t, nsweeps, self.s, ctypes.byref(lev), H)
+        self.level = lev.value
+        self.t += nsweeps
+        return H
+
+
+def dos_glue(N, klo, khi, S, visited):
+    """Glue window estimates S[w, :] into ln g over levels 0..N (NaN where
+    no window visited)."""
+    klo = np.ascontiguousarray(klo, np.int32)
+    khi = np.ascontiguousarray(khi, np.int32)
+    S = np.ascontiguousarray(S, np.float64)
+    out = np.empty(N + 1)
+    rc = lib().orc_dos_glue(N, len(klo), klo, khi, S, S.shape[1],
+                            np.ascontiguousarray(visited, np.uint64), out)
+    if rc != 0:
+        raise ValueError("windows do not share their edge levels")
+    return out
 
 
 # --------------------------------------------------------------- O(n) -----

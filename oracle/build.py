@@ -8,7 +8,7 @@ import os
 import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SOURCES = ["philox.c", "ising.c", "sw.c", "on.c", "ea_pt.c"]
+SOURCES = ["philox.c", "ising.c", "sw.c", "wl.c", "on.c", "ea_pt.c"]
 HEADERS = ["oracle.h", "lattice.h"]
 LIB = os.path.join(HERE, "liboracle.so")
 

@@ -100,6 +100,34 @@ int orc_ising_sw_sweeps(int d, int L, double J, double beta, uint64_t seed, uint
                         int64_t t0, int64_t nsweeps, int8_t* s, double* E_out,
                         double* absm_out, uint8_t* active_out, int64_t* label_out);
 
+/* ---- Windowed multicanonical and Wang-Landau walkers (Section 4), 2D
+ * Ising, J = 1, L x L torus with L a power of two; energies in levels
+ * k = (E + 2N) / 4; a walker
+ * lives in the window [klo, khi] and its arrays are indexed by k - klo (see
+ * wl.c for every rule and counter).  s is natural order, +-1. */
+
+/* Start state in the window: a nearest ground state raised (or lowered) by
+ * flips of randomly drawn spins.  Returns 0, or -1 if 1000 N attempts did
+ * not reach the window. */
+int orc_walker_init(int L, int klo, int khi, uint64_t seed, uint32_t walker, int8_t* s, int* level);
+
+/* Wang-Landau sweeps t0 .. t0+nsweeps-1 with ln g in fixed point (units of
+ * 2^-32) in S, histogram H, visited-level mask and stage (ln f = 2^-stage);
+ * returns the number of decisions within tie_tol of the threshold. */
+int64_t orc_wl_sweeps(int L, int klo, int khi, uint64_t seed, uint32_t walker, int64_t t0,
+                      int64_t nsweeps, int final_stage, int flat_percent, int8_t* s, int* level,
+                      int64_t* S, uint32_t* H, uint64_t* visited, int* stage, double tie_tol);
+
+/* Multicanonical sweeps with fixed weights Sw (ln W per window level);
+ * H[k - klo] counts the level after every attempt. */
+void orc_muca_sweeps(int L, int klo, int khi, const double* Sw, uint64_t seed, uint32_t walker,
+                     int64_t t0, int64_t nsweeps, int8_t* s, int* level, uint64_t* H);
+
+/* Glue window estimates (row w of S, stride entries apart) into S over the
+ * levels 0..N by matching consecutive windows at their shared edge level. */
+int orc_dos_glue(int N, int nwin, const int* klo, const int* khi, const double* S, int stride,
+                 const uint64_t* visited, double* out);
+
 /* ---- O(n) models with continuous spins, n = 2 (XY), n = 3 (Heisenberg) ---
  * XY spins are angles theta (s = (cos theta, sin theta)); Heisenberg spins
  * are unit vectors stored as s[3*i + a].  All arithmetic is FP64. */

@@ -196,6 +196,41 @@ def exact_sw_matrix(d, L, beta, J=1.0):
     return T, S, E
 
 
+def ising_dos_enumerated(L):
+    """Density of states g[k] of the L x L torus by enumeration, levels
+    k = (E + 2N) / 4 (E from Eq. 1 with J = 1)."""
+    N = L * L
+    E = roll_energy(all_states(N), 2, L).astype(np.int64)
+    return np.bincount((E + 2 * N) // 4, minlength=N + 1).astype(np.float64)
+
+
+def ising_dos_transfer(L):
+    """Density of states g[k] of the L x L torus from the row transfer
+    matrix: T(r, r') = y^(unlike bonds inside row r' + unlike bonds between
+    rows r and r'), Z(y) = Tr T^L = sum over configurations of y^(unlike
+    bonds) = sum_k g[k] y^(2k); Z is evaluated at the 2N+1 complex roots of
+    unity and its coefficients recovered by an inverse DFT.  For L <= 6 the
+    counts are below 2^53 and round to the exact integers; beyond, the
+    rounding error of the largest coefficients swamps the smallest, so larger
+    L is refused."""
+    if L > 6:
+        raise ValueError("exact only for L <= 6")
+    N = L * L
+    R = np.arange(2 ** L)
+    bits = (R[:, None] >> np.arange(L)) & 1
+    within = (bits != np.roll(bits, -1, axis=1)).sum(axis=1)          # periodic row
+    between = np.array([[bin(a ^ b).count("1") for b in R] for a in R])
+    expo = between + within[None, :]
+    M = 2 * N + 1
+    Z = np.empty(M, complex)
+    for j in range(M):
+        y = np.exp(2j * np.pi * j / M)
+        T = y ** expo
+        Z[j] = np.trace(np.linalg.matrix_power(T, L))
+    coef = np.real(np.fft.fft(Z)) / M   # Z[j] = sum_m c_m w^(jm), w = e^(2 pi i / M)
+    return np.round(coef[0::2][: N + 1])
+
+
 # ------------------------------------------------------- Kaufman 1949 ----
 
 def _ln2cosh(x):

@@ -564,3 +564,163 @@ def test_sw_equilibrium_matches_enumeration_and_kaufman():
     E, _ = oracle.ising_sw_sweeps(2, L, s, BETA_C, 23, 0, 20_000)
     mean, err = exact.binned_mean(E[200:] / L**2, 20)
     assert abs(mean - ref) < 3 * err, (mean, ref, err)
+
+
+# ------------------------------------------- multicanonical / Wang-Landau ----
+
+def test_exact_dos_methods_agree():
+    """The transfer-matrix density of states equals enumeration on 4x4 and
+    sums to 2^36 on 6x6; g is symmetric (k <-> N - k by flipping a
+    sublattice), g(0) = 2 and level 1 (one broken bond pair) is empty."""
+    g4 = exact.ising_dos_enumerated(4)
+    np.testing.assert_array_equal(exact.ising_dos_transfer(4), g4)
+    g6 = exact.ising_dos_transfer(6)
+    assert g6.sum() == 2.0 ** 36
+    for g in (g4, g6):
+        np.testing.assert_array_equal(g, g[::-1])
+        assert g[0] == 2 and g[1] == 0
+
+
+@pytest.mark.parametrize("klo,khi", [(0, 4), (10, 14), (30, 34), (50, 54), (60, 64)])
+def test_walker_init_reaches_window(klo, khi):
+    """Start states (8x8): every walker lands inside its window, its level is
+    the Eq. 1 energy of its spins, and the bottom (top) window starts in a
+    ferromagnetic (Neel) ground state."""
+    L = 8
+    N = L * L
+    for w in range(8):
+        wk = oracle.Walker(L, klo, khi, 77, w)
+        assert klo <= wk.level <= khi
+        E = exact.roll_energy(wk.s, 2, L)
+        assert (E + 2 * N) // 4 == wk.level
+        if klo == 0:
+            assert abs(int(wk.s.sum())) == N
+        if khi == N:
+            x, y = np.meshgrid(np.arange(L), np.arange(L))
+            neel = np.where((x + y) % 2 == 0, 1, -1).reshape(-1)
+            assert abs(int((wk.s * neel).sum())) == N
+
+
+def test_muca_with_exact_weights_is_flat():
+    """Multicanonical sampling with W = the exact density of states (4x4,
+    levels 2..8) visits every level equally often (within 5%)."""
+    g = exact.ising_dos_enumerated(4)
+    klo, khi = 2, 8
+    Sw = np.log(g[klo:khi + 1])
+    H = np.zeros(khi - klo + 1)
+    for w in range(4):
+        wk = oracle.Walker(4, klo, khi, 9, w)
+        H += wk.muca(Sw, 20_000)
+    frac = H / H.sum()
+    assert np.abs(frac * len(frac) - 1).max() < 0.05, frac
+
+
+def test_muca_canonical_weights_reproduce_boltzmann():
+    """W(E) = exp(beta E) over all levels turns the multicanonical rule into
+    Metropolis at beta: <E> on the 4x4 torus at beta = 0.3 matches
+    enumeration within 3 standard errors over 8 walkers."""
+    L, beta = 4, 0.3
+    N = L * L
+    ex = exact.enumerate_ising(2, L, beta)
+    k = np.arange(N + 1)
+    Sw = beta * (4 * k - 2 * N)
+    means = []
+    for w in range(8):
+        wk = oracle.Walker(L, 0, N, 11, w)
+        wk.muca(Sw, 500)
+        H = wk.muca(Sw, 20_000)
+        means.append(((4 * k - 2 * N) * H).sum() / H.sum())
+    m, err = np.mean(means), np.std(means, ddof=1) / np.sqrt(len(means))
+    assert abs(m - ex["E"]) < 3 * err + 1e-3, (m, ex["E"], err)
+
+
+def test_wl_bookkeeping_is_exact():
+    """Fixed-point Wang-Landau: with flatness never reached, every attempt
+    adds exactly 2^32 (ln f = 1) to its level and one count to H; the level
+    is the energy of the spins.  After a flat stage the minimum over the
+    visited levels is 0 and H restarts."""
+    L, klo, khi = 4, 2, 8
+    wk = oracle.Walker(L, klo, khi, 12, 0)
+    wk.wl(37, final_stage=5, flat_percent=101)
+    assert int(wk.H.sum()) == 37 * 16
+    assert int(wk.S.sum()) == 37 * 16 * 2 ** 32
+    assert wk.stage == 0
+    assert (exact.roll_energy(wk.s, 2, L) + 32) // 4 == wk.level
+    vis = np.array([(wk.visited >> q) & 1 for q in range(wk.K)], bool)
+    assert ((wk.H > 0) == vis).all()
+    wk2 = oracle.Walker(L, klo, khi, 12, 1)
+    wk2.wl(2000, final_stage=1, flat_percent=50)
+    assert wk2.stage >= 1
+    vis = np.array([(wk2.visited >> q) & 1 for q in range(wk2.K)], bool)
+    assert wk2.S[vis].min() >= 0
+
+
+def test_wl_converges_to_exact_dos():
+    """Wang-Landau on the whole 4x4 range (levels 0..16, final ln f = 2^-14,
+    80% flatness): ln g relative to level 0, averaged over 4 walkers, is
+    within 0.1 of the exact ln g on every possible level; the two empty
+    levels are never visited."""
+    g = exact.ising_dos_enumerated(4)
+    N = 16
+    ok = g > 0
+    est = []
+    for w in range(4):
+        wk = oracle.Walker(4, 0, N, 13, w)
+        wk.wl(400_000, final_stage=14)
+        assert wk.stage == 15
+        vis = np.array([(wk.visited >> q) & 1 for q in range(wk.K)], bool)
+        np.testing.assert_array_equal(vis, ok)
+        S = wk.S.astype(np.float64) / 2 ** 32
+        est.append(S - S[0])
+    lng = np.log(np.where(ok, g, 1.0)) - np.log(g[0])
+    diff = np.abs(np.mean(est, axis=0) - lng)[ok]
+    assert diff.max() < 0.1, diff
+
+
+def test_dos_glue_of_exact_windows():
+    """Gluing windows that hold the exact ln g plus arbitrary per-window
+    offsets returns ln g up to one constant (6x6, windows of 5 levels
+    sharing their edge level)."""
+    g = exact.ising_dos_transfer(6)
+    N = 36
+    lng = np.log(np.where(g > 0, g, 1.0))
+    klo = np.arange(0, N - 3, 4)
+    khi = klo + 4
+    rng = np.random.default_rng(5)
+    S = np.zeros((len(klo), 5))
+    vis = np.zeros(len(klo), np.uint64)
+    for w, (a, b) in enumerate(zip(klo, khi)):
+        S[w] = lng[a:b + 1] + rng.normal() * 10
+        vis[w] = sum(1 << q for q in range(5) if g[a + q] > 0)
+    out = oracle.dos_glue(N, klo, khi, S, vis)
+    ok = g > 0
+    np.testing.assert_allclose((out - out[0])[ok], (lng - lng[0])[ok], atol=1e-9)
+    assert np.isnan(out[~ok]).all()
+
+
+def test_wl_windows_glue_to_exact_dos():
+    """Windowed Wang-Landau on 4x4 (four windows of 5 levels sharing edge
+    levels, eight walkers each, final ln f = 2^-14), the walkers' estimates
+    averaged per window and glued: ln g within 0.15 of the exact values
+    (about 0.09 is the bias of 80%-flat stages at window edges)."""
+    g = exact.ising_dos_enumerated(4)
+    N = 16
+    ok = g > 0
+    klo = np.arange(0, N - 3, 4)
+    khi = klo + 4
+    S = np.zeros((len(klo), 5))
+    vis = np.zeros(len(klo), np.uint64)
+    for w, (a, b) in enumerate(zip(klo, khi)):
+        acc = []
+        for r in range(8):
+            wk = oracle.Walker(4, int(a), int(b), 14, 100 * w + r)
+            wk.wl(400_000, final_stage=14)
+            assert wk.stage == 15
+            Sw = wk.S.astype(np.float64) / 2 ** 32
+            acc.append(Sw - Sw[0])
+            vis[w] = wk.visited
+        S[w] = np.mean(acc, axis=0)
+    out = oracle.dos_glue(N, klo, khi, S, vis)
+    lng = np.log(np.where(ok, g, 1.0))
+    diff = np.abs((out - out[0]) - (lng - lng[0]))[ok]
+    assert diff.max() < 0.15, diff
