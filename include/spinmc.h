@@ -272,6 +272,90 @@ void sl_batch_destroy(sl_batch* b);
 int sl_ising_measure_static(int d, int L, double J, const int8_t* dev_spins, double* dev_out,
                             void* stream);
 
+/* ---- Windowed multicanonical and Wang-Landau walkers (2D Ising) ---------
+ *
+ * Section 4 of the paper: every thread runs its own copy of the L x L Ising
+ * torus (J = 1) inside a fixed energy window, the walkers of a window share a
+ * block, histograms and ln g estimates sit in shared memory, and the window
+ * estimates are glued into S(E) afterwards.  Energies are counted in levels
+ * k = (E + 2N) / 4, 0 <= k <= N; window w spans the levels klo[w] .. khi[w]
+ * (at least 3, at most 64) and a walker's arrays are indexed by k - klo.
+ * L is a power of two in [4, 128]; walkers_per_window is a multiple of 32;
+ * walker j lives in window j / walkers_per_window.
+ *
+ * Random numbers (Philox4x32-10 keyed by the seed of each call): every sweep
+ * visits each site once, all walkers in the same order, step q of sweep t at
+ * site (a q + b) mod N with a = (x mod N) | 1, b = y mod N, (x, y) = outputs
+ * 0, 1 of Philox(0, t, 0, 11 << 1); step q draws output q & 3 of
+ * Philox(q >> 2, t, walker, 9 << 1) (Wang-Landau) or (..., 10 << 1)
+ * (multicanonical).  A move that leaves the window is rejected.  The sweep
+ * index t continues across calls on one walker set.
+ */
+typedef struct sl_walkers sl_walkers;
+
+/* sl_walkers_required_bytes — device bytes of a walker set (spins bit-packed
+ * 32 walkers per word, levels, stages, visited masks, ln g and histograms). */
+int sl_walkers_required_bytes(int L, int nwin, const int* klo, const int* khi,
+                              int walkers_per_window, size_t* bytes);
+
+/* sl_walkers_create — place every walker in its window: a nearest ground
+ * state (ferromagnetic if the window's middle level is <= N/2, else Neel;
+ * the copy with spin 0 down iff the top bit of output 0 of
+ * Philox(0, 1, walker, 8 << 1) under `seed` is set), then attempt a flips
+ * site (u N) >> 32, u = output 0 of Philox(a, 0, walker, 8 << 1), iff that
+ * moves the energy towards the window without passing its far edge.
+ * Synchronises; SL_EDEVICE if a walker did not arrive within 1000 N
+ * attempts.  dev_buf as for sl_create (NULL: library-owned). */
+int sl_walkers_create(int L, int nwin, const int* klo, const int* khi, int walkers_per_window,
+                      uint64_t seed, void* dev_buf, size_t dev_buf_bytes, void* stream,
+                      sl_walkers** out);
+
+/* sl_wl_run — nsweeps Wang-Landau sweeps of every walker (asynchronous).
+ * ln g is kept per walker in fixed point (units of 2^-32, ln f = 2^-stage):
+ * a move k -> k' is accepted iff D >= 0 or u < exp(D 2^-32) 2^32,
+ * D = S(k) - S(k'); after every attempt S(k) += 2^(32 - stage), H(k) += 1.
+ * After every sweep a walker whose visited levels all hold
+ * H(k) nvisited 100 >= flat_percent sum(H) advances a stage (H = 0, S lowered
+ * by its minimum over the visited levels); walkers past final_stage (<= 32)
+ * stop moving. */
+int sl_wl_run(sl_walkers* w, int64_t nsweeps, int final_stage, int flat_percent, uint64_t seed);
+
+/* sl_muca_run — nsweeps multicanonical sweeps with fixed weights lnW (host,
+ * [nwin][kmax] doubles, kmax from sl_walkers_info, entry q of row w the
+ * level klo[w] + q): a move k -> k' is accepted iff
+ * u < exp(lnW(k) - lnW(k')) 2^32 (exact integer thresholds built on the
+ * host in FP64).  The histograms restart at 0 and count the level after every
+ * attempt.  Synchronises to upload the thresholds; the sweeps are
+ * asynchronous.  SL_EINVAL for non-finite weights. */
+int sl_muca_run(sl_walkers* w, const double* lnW, int64_t nsweeps, uint64_t seed);
+
+/* sl_walkers_read — synchronise and copy to host: S ([walker][kmax] int64,
+ * ln g in units of 2^-32), H ([walker][kmax]), level, stage, visited-level
+ * masks ([walker]); any pointer may be NULL. */
+int sl_walkers_read(sl_walkers* w, int64_t* S, uint32_t* H, int32_t* level, int32_t* stage,
+                    uint64_t* visited);
+
+/* sl_walkers_get_spins — one walker's spins in natural order as int8 +-1
+ * (host or device pointer, N entries).  Synchronises. */
+int sl_walkers_get_spins(sl_walkers* w, int walker, int8_t* dst);
+
+/* sl_walkers_info — number of walkers, levels per walker array (kmax) and
+ * sweeps done. */
+int sl_walkers_info(const sl_walkers* w, int* nwalk, int* kmax, int64_t* sweeps_done);
+
+/* sl_walkers_destroy — release host metadata (and the buffer if
+ * library-owned); synchronises first. */
+void sl_walkers_destroy(sl_walkers* w);
+
+/* sl_dos_glue — glue per-window estimates (row w of S, `stride` doubles
+ * apart, level klo[w] + q in entry q) into S over the levels 0..N of the
+ * L x L torus (host only): window 0 as it is, window w + 1 shifted so that
+ * its first level, which must be window w's last, matches; levels no window
+ * visited (visited[w] bit q) are NaN.  SL_EINVAL if consecutive windows do
+ * not share their edge level or it was not visited in both. */
+int sl_dos_glue(int L, int nwin, const int* klo, const int* khi, const double* S, int stride,
+                const uint64_t* visited, double* out);
+
 /* sl_strerror — static text for a status code. */
 const char* sl_strerror(int status);
 

@@ -64,6 +64,17 @@ _sig("sl_batch_get_bonds", _int, _vp, _int, _vp)
 _sig("sl_batch_sweeps_done", _int, _vp, ctypes.POINTER(_i64))
 _sig("sl_batch_destroy", None, _vp)
 _sig("sl_ising_measure_static", _int, _int, _int, _dbl, _vp, _vp, _vp)
+_sig("sl_walkers_required_bytes", _int, _int, _int, _vp, _vp, _int, ctypes.POINTER(_sz))
+_sig("sl_walkers_create", _int, _int, _int, _vp, _vp, _int, _u64, _vp, _sz, _vp,
+     ctypes.POINTER(_vp))
+_sig("sl_wl_run", _int, _vp, _i64, _int, _int, _u64)
+_sig("sl_muca_run", _int, _vp, _vp, _i64, _u64)
+_sig("sl_walkers_read", _int, _vp, _vp, _vp, _vp, _vp, _vp)
+_sig("sl_walkers_get_spins", _int, _vp, _int, _vp)
+_sig("sl_walkers_info", _int, _vp, ctypes.POINTER(_int), ctypes.POINTER(_int),
+     ctypes.POINTER(_i64))
+_sig("sl_walkers_destroy", None, _vp)
+_sig("sl_dos_glue", _int, _int, _int, _vp, _vp, _vp, _int, _vp, _vp)
 _sig("sl_strerror", ctypes.c_char_p, _int)
 _sig("sl_last_error", _int, ctypes.c_char_p, _sz)
 
@@ -224,6 +235,73 @@ def sl_ising_measure_static(d, L, J, dev_spins, dev_out, stream):
            "sl_ising_measure_static")
 
 
+def sl_walkers_required_bytes(L, klo, khi, walkers_per_window):
+    lo, plo = _i32_array(klo)
+    hi, phi = _i32_array(khi)
+    out = _sz()
+    _check(_lib.sl_walkers_required_bytes(L, lo.size, plo, phi, walkers_per_window,
+                                          ctypes.byref(out)), "sl_walkers_required_bytes")
+    return out.value
+
+
+def sl_walkers_create(L, klo, khi, walkers_per_window, seed, dev_buf, dev_buf_bytes, stream):
+    lo, plo = _i32_array(klo)
+    hi, phi = _i32_array(khi)
+    h = _vp()
+    _check(_lib.sl_walkers_create(L, lo.size, plo, phi, walkers_per_window, seed, _addr(dev_buf),
+                                  dev_buf_bytes, stream, ctypes.byref(h)), "sl_walkers_create")
+    return h.value
+
+
+def sl_wl_run(h, nsweeps, final_stage, flat_percent, seed):
+    _check(_lib.sl_wl_run(h, nsweeps, final_stage, flat_percent, seed), "sl_wl_run")
+
+
+def sl_muca_run(h, lnW, nsweeps, seed):
+    W, pW = _f64_array(lnW)
+    _check(_lib.sl_muca_run(h, pW, nsweeps, seed), "sl_muca_run")
+
+
+def sl_walkers_info(h):
+    n, k, t = _int(), _int(), _i64()
+    _check(_lib.sl_walkers_info(h, ctypes.byref(n), ctypes.byref(k), ctypes.byref(t)),
+           "sl_walkers_info")
+    return n.value, k.value, t.value
+
+
+def sl_walkers_read(h):
+    """(S int64 [walker][kmax], H uint32 [walker][kmax], level, stage, visited)."""
+    n, k, _ = sl_walkers_info(h)
+    S = np.empty((n, k), np.int64)
+    H = np.empty((n, k), np.uint32)
+    lev = np.empty(n, np.int32)
+    st = np.empty(n, np.int32)
+    vis = np.empty(n, np.uint64)
+    _check(_lib.sl_walkers_read(h, S.ctypes.data, H.ctypes.data, lev.ctypes.data, st.ctypes.data,
+                                vis.ctypes.data), "sl_walkers_read")
+    return S, H, lev, st, vis
+
+
+def sl_walkers_get_spins(h, walker, dst):
+    _check(_lib.sl_walkers_get_spins(h, walker, _addr(dst)), "sl_walkers_get_spins")
+
+
+def sl_walkers_destroy(h):
+    _lib.sl_walkers_destroy(h)
+
+
+def sl_dos_glue(L, klo, khi, S, visited):
+    """Glue window estimates S[w, q] (level klo[w] + q) into ln g over 0..N."""
+    lo, plo = _i32_array(klo)
+    hi, phi = _i32_array(khi)
+    S = np.ascontiguousarray(S, np.float64)
+    vis = np.ascontiguousarray(visited, np.uint64)
+    out = np.empty(L * L + 1)
+    _check(_lib.sl_dos_glue(L, lo.size, plo, phi, S.ctypes.data, S.shape[1], vis.ctypes.data,
+                            out.ctypes.data), "sl_dos_glue")
+    return out
+
+
 # ------------------------------------------------- torch-backed helper ----
 
 _STORAGE_OF_N = {1: SL_STORE_I8, 2: SL_STORE_F32_ANGLE, 3: SL_STORE_F32_VEC}
@@ -306,6 +384,52 @@ class Lattice:
             self.ws = torch.empty(need, dtype=torch.uint8, device=self.buf.device)
             sl_attach_workspace(self.h, self.ws, need)
         sl_set_option(self.h, SL_OPT_UPDATE, rule)
+
+
+class Walkers:
+    """Windowed multicanonical / Wang-Landau walkers, the device buffer a
+    torch CUDA tensor."""
+
+    def __init__(self, L, klo, khi, walkers_per_window, seed=0, stream=None, device="cuda"):
+        import torch
+        self.L = L
+        self.N = L * L
+        self.klo = np.asarray(klo, np.int32)
+        self.khi = np.asarray(khi, np.int32)
+        self.wpw = walkers_per_window
+        nbytes = sl_walkers_required_bytes(L, self.klo, self.khi, walkers_per_window)
+        self.buf = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        self.stream = torch.cuda.current_stream(self.buf.device) if stream is None else stream
+        self.h = sl_walkers_create(L, self.klo, self.khi, walkers_per_window, seed, self.buf,
+                                   nbytes, self.stream.cuda_stream)
+        self.nwalk, self.kmax, _ = sl_walkers_info(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            sl_walkers_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def wl(self, nsweeps, final_stage, flat_percent=80, seed=0):
+        sl_wl_run(self.h, nsweeps, final_stage, flat_percent, seed)
+
+    def muca(self, lnW, nsweeps, seed=0):
+        lnW = np.ascontiguousarray(lnW, np.float64)
+        assert lnW.shape == (len(self.klo), self.kmax)
+        sl_muca_run(self.h, lnW, nsweeps, seed)
+
+    def read(self):
+        return sl_walkers_read(self.h)
+
+    def spins(self, walker):
+        out = np.empty(self.N, np.int8)
+        sl_walkers_get_spins(self.h, walker, out)
+        return out
 
 
 class Batch:
