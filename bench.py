@@ -55,6 +55,16 @@ WORKLOADS = {
                              desc="2D Ising ferromagnet J=1, L=8192, int8 spins, beta_c, "
                                   "Swendsen-Wang cluster updates (the paper's Table 1 "
                                   "cluster row)"),
+    "wl2d_L64_windows": dict(d=2, L=64, n=1, beta=None, storage="walkers", bytes=0.0,
+                             kind="wl", wpw=128, width=4, paper_flips_per_ns=1 / 0.94,
+                             desc="2D Ising L=64, Wang-Landau walkers in 1023 windows of 5 "
+                                  "levels (dE = 16) sharing edge levels, 128 walkers each "
+                                  "(the paper's Table 1 Wang-Landau row)"),
+    "muca2d_L64_windows": dict(d=2, L=64, n=1, beta=None, storage="walkers", bytes=0.0,
+                               kind="muca", wpw=128, width=4, paper_flips_per_ns=1 / 0.33,
+                               desc="2D Ising L=64, multicanonical walkers in 1023 windows of 5 "
+                                    "levels sharing edge levels, 128 walkers each, weights from "
+                                    "a Wang-Landau run (the paper's Table 1 multicanonical row)"),
     "heis3d_L256_f32": dict(d=3, L=256, n=3, beta=0.693, storage="vec", bytes=36.0,
                             desc="3D Heisenberg J=1, L=256, FP32 unit vectors, beta=0.693, "
                                  "renormalised every 16 sweeps"),
@@ -280,6 +290,41 @@ def time_sweeps(spinmc, wl, steps, warmup, replica, want_clocks, local):
     return ms, cl, e_last
 
 
+def walkers_run(spinmc, wl, sweeps=10):
+    """Windowed Wang-Landau or multicanonical walkers of the 2D Ising model:
+    windows of width + 1 levels sharing edge levels over the whole range,
+    wpw walkers each; `sweeps` sweeps of every walker timed with CUDA events.
+    Multicanonical weights come from a short Wang-Landau run."""
+    import numpy as np
+    import torch
+    L = wl["L"]
+    N = L * L
+    klo = np.arange(0, N - wl["width"] + 1, wl["width"]).astype(np.int32)
+    khi = (klo + wl["width"]).astype(np.int32)
+    w = spinmc.Walkers(L, klo, khi, wl["wpw"], seed=1)
+    w.wl(3, final_stage=32, seed=2)
+    if wl["kind"] == "muca":
+        S = w.read()[0]
+        lnW = S[::wl["wpw"]].astype(np.float64) / 2 ** 32
+        w.muca(lnW, 2, seed=3)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(w.stream)
+    if wl["kind"] == "muca":
+        w.muca(lnW, sweeps, seed=3)
+    else:
+        w.wl(sweeps, final_stage=32, seed=2)
+    ev1.record(w.stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    flips = w.nwalk * N * sweeps
+    w.close()
+    return {"value": flips / (ms * 1e6), "unit": UNIT, "ms_per_step": ms / sweeps,
+            "walkers": int(len(klo) * wl["wpw"]), "windows": int(len(klo)),
+            "paper_gtx480_flips_per_ns": wl["paper_flips_per_ns"],
+            "over_paper_gtx480": flips / (ms * 1e6) / wl["paper_flips_per_ns"]}
+
+
 def batch_run(spinmc, nsamples=1024, ntemps=32, sweeps=100, plain_lattices=32, plain_sweeps=20):
     """The batched Edwards-Anderson workload: nsamples 3D +-J samples of sides
     [8,12,16,24,32][s mod 5], ntemps temperatures geometric in [0.5, 3],
@@ -501,6 +546,33 @@ def main():
         barrier(world)
         dist_teardown(world)
         return
+    if wl["storage"] == "walkers":
+        # windowed walkers: every rank runs the full walker set (independent
+        # runs), the line reports the sum
+        clocks = Clocks(local) if rank == 0 else None
+        if clocks:
+            clocks.start()
+        r = walkers_run(spinmc, wl, sweeps=args.steps)
+        cl = clocks.stop() if clocks else None
+        ms = max_over_ranks(r["ms_per_step"] * args.steps, world)
+        flips = r["walkers"] * L * L * args.steps * world
+        line = {
+            "metric": METRIC, "value": flips / (ms * 1e6), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u32 walker bit-planes, int64 fixed-point ln g", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": wl["desc"],
+                       "step": "one sweep of every walker",
+                       "l2": "64 MB of walker lattices, L2-resident by design",
+                       "parallelism": "replica per GPU" if world > 1 else "single GPU"},
+            "roofline": None, "gpu_launches": 1, "clocks": cl,
+            "over_paper_gtx480": r["over_paper_gtx480"],
+        }
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        barrier(world)
+        dist_teardown(world)
+        return
     N = L ** d
     ms, clocks, e_last = time_sweeps(spinmc, wl, args.steps, args.warmup, rank, rank == 0, local)
     ms = max_over_ranks(ms, world)
@@ -541,6 +613,9 @@ def main():
             var = {}
             for name, w in WORKLOADS.items():
                 if name == args.workload or w["storage"] == "batch":
+                    continue
+                if w["storage"] == "walkers":
+                    var[name] = walkers_run(spinmc, w)
                     continue
                 k = 10 if w.get("multihit") else (100 if w.get("update") == 2 else 300)
                 vms, _, _ = time_sweeps(spinmc, w, k, 3 if w.get("multihit") else 5, rank,

@@ -339,6 +339,14 @@ int sl_walkers_read(sl_walkers* w, int64_t* S, uint32_t* H, int32_t* level, int3
  * (host or device pointer, N entries).  Synchronises. */
 int sl_walkers_get_spins(sl_walkers* w, int walker, int8_t* dst);
 
+/* sl_walkers_set_option — SL_WOPT_SPINS_SMEM: 1 keeps each warp's 32
+ * lattices in shared memory for the length of a run, 0 (default) reads and
+ * writes them in place in global memory (L2).  The results do not depend on
+ * it.
+ * SL_EINVAL for unknown options or values. */
+#define SL_WOPT_SPINS_SMEM 1
+int sl_walkers_set_option(sl_walkers* w, int option, int64_t value);
+
 /* sl_walkers_info — number of walkers, levels per walker array (kmax) and
  * sweeps done. */
 int sl_walkers_info(const sl_walkers* w, int* nwalk, int* kmax, int64_t* sweeps_done);

@@ -23,6 +23,7 @@ SL_STORE_I8, SL_STORE_BITS, SL_STORE_F32_ANGLE, SL_STORE_F32_VEC = 0, 1, 2, 3
 SL_OPT_RENORM_EVERY, SL_OPT_FAST_MATH, SL_OPT_KERNEL, SL_OPT_ROWS, SL_OPT_GRAPH = 1, 2, 3, 4, 5
 SL_OPT_UPDATE, SL_OPT_MULTIHIT, SL_OPT_TILE = 6, 7, 8
 SL_UPDATE_METROPOLIS, SL_UPDATE_HEATBATH, SL_UPDATE_SW = 0, 1, 2
+SL_WOPT_SPINS_SMEM = 1
 
 if not os.path.exists(LIB_PATH):
     raise ImportError("libspinmc.so is not built at %s; run paper_1107_5463_gb300.build.build()"
@@ -74,6 +75,7 @@ _sig("sl_walkers_get_spins", _int, _vp, _int, _vp)
 _sig("sl_walkers_info", _int, _vp, ctypes.POINTER(_int), ctypes.POINTER(_int),
      ctypes.POINTER(_i64))
 _sig("sl_walkers_destroy", None, _vp)
+_sig("sl_walkers_set_option", _int, _vp, _int, _i64)
 _sig("sl_dos_glue", _int, _int, _int, _vp, _vp, _vp, _int, _vp, _vp)
 _sig("sl_strerror", ctypes.c_char_p, _int)
 _sig("sl_last_error", _int, ctypes.c_char_p, _sz)
@@ -290,6 +292,10 @@ def sl_walkers_destroy(h):
     _lib.sl_walkers_destroy(h)
 
 
+def sl_walkers_set_option(h, option, value):
+    _check(_lib.sl_walkers_set_option(h, option, value), "sl_walkers_set_option")
+
+
 def sl_dos_glue(L, klo, khi, S, visited):
     """Glue window estimates S[w, q] (level klo[w] + q) into ln g over 0..N."""
     lo, plo = _i32_array(klo)
@@ -414,6 +420,9 @@ class Walkers:
             self.close()
         except Exception:
             pass
+
+    def set_option(self, option, value):
+        sl_walkers_set_option(self.h, option, value)
 
     def wl(self, nsweeps, final_stage, flat_percent=80, seed=0):
         sl_wl_run(self.h, nsweeps, final_stage, flat_percent, seed)

@@ -61,13 +61,16 @@ def test_walker_start_states(sm, L):
     w.close()
 
 
-@pytest.mark.parametrize("L,nwin", [(4, None), (8, None), (16, 12), (32, 6)])
-def test_wang_landau_parity(sm, L, nwin):
+@pytest.mark.parametrize("L,nwin,smem", [(4, None, 1), (8, None, 1), (8, None, 0), (16, 12, 1),
+                                          (32, 6, 0)])
+def test_wang_landau_parity(sm, L, nwin, smem):
     """Two runs (the sweep counter continues) with stage advances: every
-    sampled walker matches the oracle exactly."""
+    sampled walker matches the oracle exactly, with the lattices held in
+    shared memory or in global memory during a run."""
     N = L * L
     klo, khi = windows(N, 4, first=N // 4 if nwin else 0, count=nwin)
     w = sm.Walkers(L, klo, khi, 32, seed=5)
+    w.set_option(sm.SL_WOPT_SPINS_SMEM, smem)
     pick = list(range(0, w.nwalk, 5 if L <= 8 else 9))
     refs = oracle_walkers(L, klo, khi, 32, 5, pick)
     for nsw, fs in ((30, 6), (45, 9)):
@@ -103,6 +106,7 @@ def test_multicanonical_parity(sm):
     N = L * L
     klo, khi = windows(N, 6)
     w = sm.Walkers(L, klo, khi, 32, seed=9)
+    w.set_option(sm.SL_WOPT_SPINS_SMEM, 0)
     w.wl(60, final_stage=8, seed=1)
     S, _, _, _, _ = w.read()
     lnW = np.zeros((len(klo), w.kmax))
