@@ -74,7 +74,8 @@ WORKLOADS = {
                                samples=1024, temps=32,
                                desc="3D Edwards-Anderson +-J, 1024 samples of sides "
                                     "[8,12,16,24,32][s mod 5] x 32 temperatures geometric in "
-                                    "[0.5, 3], replica exchange every sweep, one launch per side"),
+                                    "[0.5, 3], replica exchange every sweep, one persistent graph-captured "
+                                    "launch, samples per CTA chosen by the autotuner"),
 }
 HEADLINE = "ising2d_L16384_i8"
 
@@ -231,9 +232,9 @@ def time_batch(spinmc, wl, steps, warmup, want_clocks, local, rank=0, world=1):
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
     cl = clocks.stop() if clocks else None
-    nclass = len(set(Ls))
+    tuning = b.tuning()
     b.close()
-    return ms, cl, nclass
+    return ms, cl, tuning
 
 
 def launch_shape(wl):
@@ -522,7 +523,7 @@ def main():
     hbm, peak_kind = peaks()
     barrier(world)
     if wl["storage"] == "batch":
-        ms, clocks, nclass = time_batch(spinmc, wl, args.steps, args.warmup, rank == 0, local,
+        ms, clocks, tuning = time_batch(spinmc, wl, args.steps, args.warmup, rank == 0, local,
                                         rank, world)
         ms = max_over_ranks(ms, world)
         flips = batch_sites(wl) * args.steps  # all ranks together
@@ -538,7 +539,9 @@ def main():
                        "parallelism": "samples split across ranks" if world > 1 else
                        "single GPU"},
             "roofline": None,
-            "gpu_launches": nclass,
+            "gpu_launches": 1,
+            "tuning": [{"L": L, "samples_per_cta": k, "ms_per_sample_sweep": c}
+                       for L, k, c in tuning],
             "clocks": clocks,
         }
         if rank == 0:

@@ -237,6 +237,26 @@ int sl_batch_create(int d, const int* L_per_sample, int nsamples, int ntemps,
  * [(s * nsweeps + i) * ntemps + k].  Asynchronous. */
 int sl_batch_run(sl_batch* b, int64_t nsweeps, uint64_t seed, double* dev_E);
 
+/*
+ * sl_batch_set_option — SL_BOPT_AUTOTUNE: 1 (default) times, before the first
+ * run, 2-sweep trials of every pack size k in {1, 2, 4, 8} that fits a CTA's
+ * shared memory for each sample size (on a copy of the state, which is then
+ * restored) and keeps the combination whose largest-first schedule over the
+ * GPU's CTAs finishes first; 0 packs as many samples per CTA as fit.
+ * SL_BOPT_PACK: 0 (default) uses the tuned or fitted pack sizes, 1/2/4/8
+ * forces that pack size (capped by what fits).  Results never depend on
+ * either option.  Both take effect at the next sl_batch_run.
+ */
+#define SL_BOPT_AUTOTUNE 1
+#define SL_BOPT_PACK 2
+int sl_batch_set_option(sl_batch* b, int option, int64_t value);
+
+/* sl_batch_tuning — the pack size (samples per CTA) and the measured time of
+ * one sweep of a pack divided by its samples, in ms (0 if untimed), of size
+ * class cls (classes are the distinct sides, largest first); returns the
+ * number of classes or a negative status. */
+int sl_batch_tuning(sl_batch* b, int cls, int* L, int* pack, double* ms_per_sample_sweep);
+
 /* Copy slot `slot` of sample `sample` out in natural order (int8 +-1, host or
  * device dst) and report the temperature index it holds.  Synchronises. */
 int sl_batch_get(sl_batch* b, int sample, int slot, int8_t* dst, int* temp_index);

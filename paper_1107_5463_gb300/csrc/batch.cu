@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <new>
 #include <vector>
 
@@ -33,13 +34,23 @@ struct PairMeta {
     int off;         // offset of the pair's table
 };
 
+// A queue entry: `count` samples of side L (class_samples[first ...]) run
+// side by side, one per sub-group of blockDim / k threads, `stride` bytes of
+// shared memory each.
+struct WorkItem {
+    int first, count, L, k, stride;
+};
+
 struct BatchArgs {
     uint32_t* spins;
     uint8_t* bonds;
     int32_t* perm;  // [sample][kMaxTemps] slot holding temperature k
-    const int* class_samples;
+    const int* class_samples;   // samples grouped by size
+    const WorkItem* items;      // the work queue
+    int nitems;
+    unsigned* counter;          // next queue entry
     const long long* word_off;  // per sample: first spin word (colour 0), colour 1 at + H
-    int d, L, ntemps;
+    int d, ntemps;
     long long t0;
     int nsweeps;
     RoundKeys rk;
@@ -94,12 +105,23 @@ __device__ __forceinline__ void count_planes(const uint32_t (&u)[6], uint32_t& b
     }
 }
 
-template <int D>
-__global__ void __launch_bounds__(1024) ea_pt_kernel(const BatchArgs a)
+// A barrier over the nthr threads of one sample's sub-group: the whole CTA
+// (barrier 0) or named barrier `bar` (1..15) of nthr threads.
+__device__ __forceinline__ void group_sync(int bar, int nthr)
 {
-    extern __shared__ uint4 smem_u4[];
-    const int s = a.class_samples[blockIdx.x];
-    const int L = a.L, nt = a.ntemps;
+    if (bar == 0) __syncthreads();
+    else asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nthr) : "memory");
+}
+
+// All sweeps of one sample by a sub-group of nthr threads (local index tid)
+// whose shared memory starts at base; the sample's couplings and the spins of
+// all its replicas stay in shared memory for the whole run.
+template <int D>
+__device__ void run_sample(const BatchArgs& a, int s, int L, unsigned char* base, int tid,
+                           int nthr, int bar)
+{
+    uint4* smem_u4 = reinterpret_cast<uint4*>(base);
+    const int nt = a.ntemps;
     const int N = D == 3 ? L * L * L : L * L;
     const int H = N / 2, G = H / 4;
     uint32_t* S0 = reinterpret_cast<uint32_t*>(smem_u4);
@@ -110,7 +132,7 @@ __global__ void __launch_bounds__(1024) ea_pt_kernel(const BatchArgs a)
     long long* E_slot = reinterpret_cast<long long*>(thr_slot + kMaxTemps);
     int* unsat = reinterpret_cast<int*>(E_slot + kMaxTemps);
     int* sot = unsat + kMaxTemps;  // slot of temperature
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nthr = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5;
     const uint32_t active = nt == 32 ? 0xFFFFFFFFu : ((1u << nt) - 1u);
 
     // load the sample
@@ -123,12 +145,12 @@ __global__ void __launch_bounds__(1024) ea_pt_kernel(const BatchArgs a)
         unsat[tid] = 0;
         sot[tid] = tid < nt ? a.perm[s * kMaxTemps + tid] : tid;
     }
-    __syncthreads();
+    group_sync(bar, nthr);
     if (tid < nt) {
         const uint4 th = reinterpret_cast<const uint4*>(a.thr_temp)[tid];
         thr_slot[sot[tid]] = th;
     }
-    __syncthreads();
+    group_sync(bar, nthr);
 
     for (int step = 0; step < a.nsweeps; ++step) {
         const long long t = a.t0 + step;
@@ -208,7 +230,7 @@ __global__ void __launch_bounds__(1024) ea_pt_kernel(const BatchArgs a)
                     }
                 }
             }
-            __syncthreads();
+            group_sync(bar, nthr);
         }
         // per-slot unsatisfied bonds: column sums of the counters
         {
@@ -222,7 +244,7 @@ __global__ void __launch_bounds__(1024) ea_pt_kernel(const BatchArgs a)
                 }
             atomicAdd(&unsat[lane], mine);
         }
-        __syncthreads();
+        group_sync(bar, nthr);
         if (warp == 0) {
             const int k = lane;
             // energy of every slot: E = -(dN - 2 unsat)
@@ -252,11 +274,35 @@ __global__ void __launch_bounds__(1024) ea_pt_kernel(const BatchArgs a)
             if (k < nt) thr_slot[sot[k]] = reinterpret_cast<const uint4*>(a.thr_temp)[k];
             unsat[lane] = 0;
         }
-        __syncthreads();
+        group_sync(bar, nthr);
     }
     // write the sample back
     for (int q = tid; q < 2 * H; q += nthr) a.spins[w0 + q] = S0[q];
     if (tid < nt) a.perm[s * kMaxTemps + tid] = sot[tid];
+}
+
+// One persistent launch for the whole batch: every CTA takes work items
+// (packs of k samples of one size, k sub-groups of blockDim / k threads, each
+// with its own named barrier and shared-memory slice) from a queue ordered
+// largest first, until the queue is empty.
+template <int D>
+__global__ void __launch_bounds__(1024) ea_pt_persistent(const BatchArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int item;
+    while (true) {
+        if (threadIdx.x == 0) item = (int)atomicAdd(a.counter, 1u);
+        __syncthreads();
+        const int it = item;
+        if (it >= a.nitems) break;
+        const WorkItem w = a.items[it];
+        const int nthr = blockDim.x / w.k;
+        const int g = threadIdx.x / nthr;
+        if (g < w.count)
+            run_sample<D>(a, a.class_samples[w.first + g], w.L, smem_raw + (size_t)g * w.stride,
+                          threadIdx.x - g * nthr, nthr, w.k == 1 ? 0 : g + 1);
+        __syncthreads();
+    }
 }
 
 __global__ void batch_init_kernel(uint32_t* spins, uint8_t* bonds, int32_t* perm,
@@ -323,13 +369,6 @@ size_t smem_bytes(int d, int L)
            kMaxTemps * 8 + 2 * kMaxTemps * 4;
 }
 
-int threads_for(int d, int L)
-{
-    const int N = d == 3 ? L * L * L : L * L;
-    const int G = N / 8;
-    int t = (G + 31) / 32 * 32;
-    return t > 1024 ? 1024 : t;
-}
 
 }  // namespace
 }  // namespace spinmc
@@ -347,8 +386,6 @@ struct sl_batch {
     uint64_t seed;
     int64_t sweeps_done;
     cudaStream_t stream;
-    cudaStream_t side[8];
-    cudaEvent_t ev_fork, ev_join[8];
     uint32_t* spins;
     uint8_t* bonds;
     int32_t* perm;
@@ -361,13 +398,27 @@ struct sl_batch {
     int8_t* staging;
     long long total_words;
     void* owned_buf;
+    // persistent launch: work queue, per-class pack sizes, graph
+    WorkItem* items_dev;
+    unsigned* counter;
+    uint32_t* backup_spins;
+    int32_t* backup_perm;
+    std::vector<int> class_k;        // samples per CTA for each size class
+    std::vector<double> class_cost;  // measured SM-milliseconds per sample-sweep (0: untimed)
+    int nitems, grid;
+    size_t smem_dyn;
+    int autotune, force_k, tuned;
+    cudaStream_t cap_stream;
+    cudaGraph_t graph_def;       // kept alive: kernel_node belongs to it
+    cudaGraphExec_t graph;
+    cudaGraphNode_t kernel_node;
 };
 
 namespace {
 
 struct BatchLayout {
     size_t off_spins, off_bonds, off_perm, off_Ls, off_woff, off_class, off_thr, off_meta,
-        off_tab, off_staging, total;
+        off_tab, off_staging, off_items, off_counter, off_backup, off_backup_perm, total;
     long long total_words;
     int tab_entries;
 };
@@ -468,22 +519,274 @@ BatchLayout batch_layout(int d, const int* Ls, int nsamples, int ntemps, const d
     for (int s = 0; s < nsamples; ++s)
         maxN = std::max(maxN, (long long)Ls[s] * Ls[s] * (d == 3 ? Ls[s] : 1));
     y.off_staging = take((size_t)d * maxN);
+    y.off_items = take((size_t)nsamples * sizeof(WorkItem));
+    y.off_counter = take(sizeof(unsigned));
+    y.off_backup = take((size_t)words * 4);
+    y.off_backup_perm = take((size_t)nsamples * kMaxTemps * 4);
     y.total = off;
     return y;
 }
 
-template <int D>
-cudaError_t launch_class(const sl_batch* b, int ci, BatchArgs a, cudaStream_t st)
+int dev_attr(cudaDeviceAttr attr, int fallback)
 {
-    const int L = b->class_L[ci];
-    const size_t sm = smem_bytes(b->d, L);
-    cudaError_t e = cudaFuncSetAttribute(ea_pt_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sm);
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, attr, dev) != cudaSuccess)
+        return fallback;
+    return v;
+}
+
+size_t pack_stride(int d, int L) { return (smem_bytes(d, L) + 127) / 128 * 128; }
+
+// packs of k samples for class ci appended to items
+void class_items(const sl_batch* b, int ci, int k, std::vector<WorkItem>& items)
+{
+    const int n = (int)b->class_ids[ci].size();
+    for (int q = 0; q < n; q += k) {
+        WorkItem w;
+        w.first = b->class_dev_off[ci] + q;
+        w.count = std::min(k, n - q);
+        w.L = b->class_L[ci];
+        w.k = k;
+        w.stride = (int)pack_stride(b->d, w.L);
+        items.push_back(w);
+    }
+}
+
+template <int D>
+cudaError_t launch_persistent(const BatchArgs& a, int grid, size_t smem, cudaStream_t st)
+{
+    cudaError_t e = cudaFuncSetAttribute(ea_pt_persistent<D>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    a.L = L;
-    a.class_samples = b->class_dev + b->class_dev_off[ci];
-    ea_pt_kernel<D><<<(int)b->class_ids[ci].size(), threads_for(b->d, L), sm, st>>>(a);
+    e = cudaMemsetAsync(a.counter, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    ea_pt_persistent<D><<<grid, 1024, smem, st>>>(a);
     return cudaGetLastError();
+}
+
+cudaError_t launch_any(const sl_batch* b, const BatchArgs& a, int grid, size_t smem, cudaStream_t st)
+{
+    return b->d == 3 ? launch_persistent<3>(a, grid, smem, st) : launch_persistent<2>(a, grid, smem, st);
+}
+
+BatchArgs base_args(const sl_batch* b)
+{
+    BatchArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.spins = b->spins;
+    a.bonds = b->bonds;
+    a.perm = b->perm;
+    a.word_off = b->word_off_dev;
+    a.class_samples = b->class_dev;
+    a.items = b->items_dev;
+    a.counter = b->counter;
+    a.d = b->d;
+    a.ntemps = b->ntemps;
+    a.thr_temp = b->thr_temp;
+    a.pt_tab = b->pt_tab;
+    a.pt_meta = b->pt_meta;
+    return a;
+}
+
+// The largest pack size k in {1, 2, 4, 8} whose shared memory fits one CTA.
+int max_pack(const sl_batch* b, int ci)
+{
+    const size_t limit = (size_t)dev_attr(cudaDevAttrMaxSharedMemoryPerBlockOptin, 227 * 1024);
+    const size_t st = pack_stride(b->d, b->class_L[ci]);
+    int k = 8;
+    while (k > 1 && (size_t)k * st > limit) k /= 2;
+    return k;
+}
+
+// Makespan of the work queue for pack sizes ks (one per class) when every
+// pack of class ci takes item_ms[ci][log2 k] and nctas CTAs take packs in the
+// queue's order (largest first), each the next one as it frees up.
+double simulate(const sl_batch* b, const std::vector<int>& ks,
+                const std::vector<std::vector<double>>& item_ms, int nctas)
+{
+    std::vector<double> cost;
+    for (size_t ci = 0; ci < ks.size(); ++ci) {
+        int lk = 0;
+        while ((1 << lk) < ks[ci]) ++lk;
+        const int n = (int)b->class_ids[ci].size();
+        for (int q = 0; q < n; q += ks[ci]) cost.push_back(item_ms[ci][lk]);
+    }
+    std::sort(cost.begin(), cost.end(), [](double p, double q) { return p > q; });
+    std::vector<double> busy(std::max(1, nctas), 0.0);  // min-heap of finish times
+    for (double c : cost) {
+        std::pop_heap(busy.begin(), busy.end(), std::greater<double>());
+        busy.back() += c;
+        std::push_heap(busy.begin(), busy.end(), std::greater<double>());
+    }
+    return *std::max_element(busy.begin(), busy.end());
+}
+
+// Autotuner: for every size class, time `trial` sweeps of one pack per CTA
+// for each pack size that fits, on a copy of the state that is restored
+// afterwards (the chain does not depend on the pack size); then choose the
+// pack size of every class that minimises the simulated makespan of the
+// whole queue (coarse packs can leave the last CTAs running alone).
+int autotune(sl_batch* b)
+{
+    const int nsm = dev_attr(cudaDevAttrMultiProcessorCount, 152);
+    const int trial = 2;
+    cudaError_t e = cudaMemcpyAsync(b->backup_spins, b->spins, (size_t)b->total_words * 4,
+                                    cudaMemcpyDeviceToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->backup_perm, b->perm, (size_t)b->nsamples * kMaxTemps * 4,
+                            cudaMemcpyDeviceToDevice, b->stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    const int nc = (int)b->class_L.size();
+    std::vector<std::vector<double>> item_ms(nc, std::vector<double>(4, -1.0));
+    for (int ci = 0; ci < nc && e == cudaSuccess; ++ci) {
+        for (int k = 1; k <= max_pack(b, ci) && e == cudaSuccess; k *= 2) {
+            if (k > 1 && (int)b->class_ids[ci].size() < k) break;
+            std::vector<WorkItem> items;
+            class_items(b, ci, k, items);
+            const int used = std::min((int)items.size(), nsm);
+            items.resize(used);  // one pack per CTA
+            int samples = 0;
+            for (const WorkItem& w : items) samples += w.count;
+            e = cudaMemcpyAsync(b->items_dev, items.data(), items.size() * sizeof(WorkItem),
+                                cudaMemcpyHostToDevice, b->stream);
+            BatchArgs a = base_args(b);
+            a.nitems = used;
+            a.nsweeps = trial;
+            a.rk = make_round_keys(b->seed);
+            const size_t smem = (size_t)k * pack_stride(b->d, b->class_L[ci]);
+            for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // the first run warms up
+                if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+                if (e == cudaSuccess) e = launch_any(b, a, used, smem, b->stream);
+                if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            }
+            float ms = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            int lk = 0;
+            while ((1 << lk) < k) ++lk;
+            item_ms[ci][lk] = (double)ms / trial;
+            (void)samples;
+        }
+    }
+    if (e == cudaSuccess) {
+        // exhaustive search over the timed pack sizes (at most 4^classes)
+        const int nsm = dev_attr(cudaDevAttrMultiProcessorCount, 152);
+        std::vector<int> ks(nc, 1), best_ks(nc, 1);
+        double best = 1e300;
+        std::function<void(int)> rec = [&](int ci) {
+            if (ci == nc) {
+                const double m = simulate(b, ks, item_ms, nsm);
+                if (m < best) {
+                    best = m;
+                    best_ks = ks;
+                }
+                return;
+            }
+            for (int lk = 0; lk < 4; ++lk) {
+                if (item_ms[ci][lk] < 0.0) continue;
+                ks[ci] = 1 << lk;
+                rec(ci + 1);
+            }
+        };
+        rec(0);
+        for (int ci = 0; ci < nc; ++ci) {
+            int lk = 0;
+            while ((1 << lk) < best_ks[ci]) ++lk;
+            b->class_k[ci] = best_ks[ci];
+            b->class_cost[ci] = item_ms[ci][lk] / best_ks[ci];  // ms per sample-sweep on one CTA
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->spins, b->backup_spins, (size_t)b->total_words * 4,
+                            cudaMemcpyDeviceToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->perm, b->backup_perm, (size_t)b->nsamples * kMaxTemps * 4,
+                            cudaMemcpyDeviceToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    return e == cudaSuccess ? SL_OK : cuda_fail(e, "batch autotune");
+}
+
+// Work queue from the chosen pack sizes, most expensive packs first, and the
+// graph of one launch (queue reset + persistent kernel).
+int build_queue(sl_batch* b)
+{
+    const int nc = (int)b->class_L.size();
+    std::vector<WorkItem> items;
+    std::vector<double> cost;
+    for (int ci = 0; ci < nc; ++ci) {
+        const int k = b->force_k > 0 ? std::min(b->force_k, max_pack(b, ci)) : b->class_k[ci];
+        const size_t before = items.size();
+        class_items(b, ci, k, items);
+        // a pack's measured time (class_cost is per sample of a pack of k);
+        // without a timing, a pack costs its sites (the work is per site)
+        const double per_sample = b->class_cost[ci] > 0.0 && b->force_k <= 0
+                                      ? b->class_cost[ci]
+                                      : (double)b->class_L[ci] * b->class_L[ci] *
+                                            (b->d == 3 ? b->class_L[ci] : 1);
+        for (size_t q = before; q < items.size(); ++q) cost.push_back(per_sample * k);
+    }
+    std::vector<int> order(items.size());
+    for (size_t q = 0; q < order.size(); ++q) order[q] = (int)q;
+    std::stable_sort(order.begin(), order.end(), [&](int p, int q) { return cost[p] > cost[q]; });
+    std::vector<WorkItem> sorted;
+    size_t smem = 0;
+    for (int q : order) {
+        sorted.push_back(items[q]);
+        smem = std::max(smem, (size_t)items[q].k * items[q].stride);
+    }
+    const int nsm = dev_attr(cudaDevAttrMultiProcessorCount, 152);
+    const size_t per_sm = (size_t)dev_attr(cudaDevAttrMaxSharedMemoryPerMultiprocessor, 228 * 1024);
+    const int per = std::max(1, std::min(2, (int)(per_sm / (smem + 1024))));  // 1024 threads: <= 2
+    b->grid = std::min((int)sorted.size(), nsm * per);
+    b->nitems = (int)sorted.size();
+    b->smem_dyn = smem;
+    cudaError_t e = cudaMemcpyAsync(b->items_dev, sorted.data(), sorted.size() * sizeof(WorkItem),
+                                    cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "batch work queue");
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    if (b->graph_def) {
+        cudaGraphDestroy(b->graph_def);
+        b->graph_def = nullptr;
+    }
+    BatchArgs a = base_args(b);
+    a.nitems = b->nitems;
+    a.rk = make_round_keys(b->seed);
+    a.nsweeps = 1;
+    e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+    const cudaError_t el = launch_any(b, a, b->grid, b->smem_dyn, b->cap_stream);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(b->cap_stream, &g);
+    if (el != cudaSuccess || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(el != cudaSuccess ? el : e, "batch graph capture");
+    }
+    size_t nnodes = 0;
+    e = cudaGraphGetNodes(g, nullptr, &nnodes);
+    std::vector<cudaGraphNode_t> nodes(nnodes);
+    if (e == cudaSuccess) e = cudaGraphGetNodes(g, nodes.data(), &nnodes);
+    b->kernel_node = nullptr;
+    for (size_t q = 0; q < nnodes && e == cudaSuccess; ++q) {
+        cudaGraphNodeType t;
+        e = cudaGraphNodeGetType(nodes[q], &t);
+        if (e == cudaSuccess && t == cudaGraphNodeTypeKernel) b->kernel_node = nodes[q];
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+    if (e != cudaSuccess || !b->kernel_node) {
+        cudaGraphDestroy(g);
+        b->graph = nullptr;
+        return cuda_fail(e != cudaSuccess ? e : cudaErrorUnknown, "batch graph");
+    }
+    b->graph_def = g;
+    return SL_OK;
 }
 
 }  // namespace
@@ -554,6 +857,20 @@ int sl_batch_create(int d, const int* L_per_sample, int nsamples, int ntemps, co
     b->pt_tab = (uint32_t*)(base + y.off_tab);
     b->staging = (int8_t*)(base + y.off_staging);
     b->owned_buf = owned;
+    b->items_dev = (WorkItem*)(base + y.off_items);
+    b->counter = (unsigned*)(base + y.off_counter);
+    b->backup_spins = (uint32_t*)(base + y.off_backup);
+    b->backup_perm = (int32_t*)(base + y.off_backup_perm);
+    b->nitems = 0;
+    b->grid = 0;
+    b->smem_dyn = 0;
+    b->autotune = 1;
+    b->force_k = 0;
+    b->tuned = 0;
+    b->cap_stream = nullptr;
+    b->graph_def = nullptr;
+    b->graph = nullptr;
+    b->kernel_node = nullptr;
     // size classes, largest first
     std::vector<int> sizes(b->L);
     std::sort(sizes.begin(), sizes.end(), [](int p, int q) { return p > q; });
@@ -568,6 +885,9 @@ int sl_batch_create(int d, const int* L_per_sample, int nsamples, int ntemps, co
         class_list.insert(class_list.end(), ids.begin(), ids.end());
         b->class_ids.push_back(ids);
     }
+    b->class_k.assign(b->class_L.size(), 1);
+    b->class_cost.assign(b->class_L.size(), 0.0);
+    for (size_t ci = 0; ci < b->class_L.size(); ++ci) b->class_k[ci] = max_pack(b, (int)ci);
     // thresholds of every temperature (Ising classes of the +-1 spin glass)
     std::vector<uint32_t> thr(kMaxTemps * 4, 0xFFFFFFFFu);
     for (int k = 0; k < ntemps; ++k)
@@ -589,12 +909,7 @@ int sl_batch_create(int d, const int* L_per_sample, int nsamples, int ntemps, co
     std::vector<PairMeta> meta;
     std::vector<uint32_t> tab;
     build_pt(betas, ntemps, max_m, meta, tab);
-    cudaError_t e = cudaSuccess;
-    for (int k = 0; k < 8 && e == cudaSuccess; ++k) {
-        e = cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join[k], cudaEventDisableTiming);
-    }
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+    cudaError_t e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
     cudaStream_t s0 = b->stream;
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->Ls_dev, b->L.data(), sizeof(int) * nsamples, cudaMemcpyHostToDevice, s0);
@@ -633,34 +948,64 @@ int sl_batch_run(sl_batch* b, int64_t nsweeps, uint64_t seed, double* dev_E)
     if (nsweeps < 0 || nsweeps > (1 << 30)) return fail(SL_EINVAL, "nsweeps out of range");
     if (b->sweeps_done + nsweeps > 4294967296LL) return fail(SL_EINVAL, "sweep index would exceed 2^32");
     if (nsweeps == 0) return SL_OK;
-    BatchArgs a;
-    std::memset(&a, 0, sizeof a);
-    a.spins = b->spins;
-    a.bonds = b->bonds;
-    a.perm = b->perm;
-    a.word_off = b->word_off_dev;
-    a.d = b->d;
-    a.ntemps = b->ntemps;
+    if (!b->tuned) {
+        int st = SL_OK;
+        if (b->autotune && b->force_k <= 0) st = autotune(b);
+        if (st == SL_OK) st = build_queue(b);
+        if (st != SL_OK) return st;
+        b->tuned = 1;
+    }
+    BatchArgs a = base_args(b);
+    a.nitems = b->nitems;
     a.t0 = b->sweeps_done;
     a.nsweeps = (int)nsweeps;
     a.rk = make_round_keys(seed);
-    a.thr_temp = b->thr_temp;
-    a.pt_tab = b->pt_tab;
-    a.pt_meta = b->pt_meta;
     a.E_out = dev_E;
-    // fork one stream per sample size so the sizes run side by side
-    cudaError_t e = cudaEventRecord(b->ev_fork, b->stream);
-    const int nc = (int)b->class_L.size();
-    for (int ci = 0; ci < nc && e == cudaSuccess; ++ci) {
-        cudaStream_t st = b->side[ci % 8];
-        e = cudaStreamWaitEvent(st, b->ev_fork, 0);
-        if (e == cudaSuccess) e = b->d == 3 ? launch_class<3>(b, ci, a, st) : launch_class<2>(b, ci, a, st);
-        if (e == cudaSuccess) e = cudaEventRecord(b->ev_join[ci % 8], st);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_join[ci % 8], 0);
-    }
+    // one launch: replay the captured graph with this run's arguments
+    cudaKernelNodeParams kp;
+    std::memset(&kp, 0, sizeof kp);
+    void* args[1] = {&a};
+    kp.func = b->d == 3 ? (void*)ea_pt_persistent<3> : (void*)ea_pt_persistent<2>;
+    kp.gridDim = dim3((unsigned)b->grid);
+    kp.blockDim = dim3(1024);
+    kp.sharedMemBytes = (unsigned)b->smem_dyn;
+    kp.kernelParams = args;
+    kp.extra = nullptr;
+    cudaError_t e = cudaGraphExecKernelNodeSetParams(b->graph, b->kernel_node, &kp);
+    if (e == cudaSuccess) e = cudaGraphLaunch(b->graph, b->stream);
     if (e != cudaSuccess) return cuda_fail(e, "sl_batch_run");
     b->sweeps_done += nsweeps;
     return SL_OK;
+}
+
+int sl_batch_set_option(sl_batch* b, int option, int64_t value)
+{
+    if (!b) return fail(SL_EINVAL, "batch is NULL");
+    switch (option) {
+    case SL_BOPT_AUTOTUNE:
+        if (value != 0 && value != 1) return fail(SL_EINVAL, "autotune must be 0 or 1");
+        b->autotune = (int)value;
+        b->tuned = 0;
+        return SL_OK;
+    case SL_BOPT_PACK:
+        if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8)
+            return fail(SL_EINVAL, "pack must be 0 (tuned) or 1, 2, 4, 8");
+        b->force_k = (int)value;
+        b->tuned = 0;
+        return SL_OK;
+    default:
+        return fail(SL_EINVAL, "unknown batch option %d", option);
+    }
+}
+
+int sl_batch_tuning(sl_batch* b, int cls, int* L, int* pack, double* ms_per_sample_sweep)
+{
+    if (!b) return fail(SL_EINVAL, "batch is NULL");
+    if (cls < 0 || cls >= (int)b->class_L.size()) return fail(SL_EINVAL, "class out of range");
+    if (L) *L = b->class_L[cls];
+    if (pack) *pack = b->force_k > 0 ? std::min(b->force_k, max_pack(b, cls)) : b->class_k[cls];
+    if (ms_per_sample_sweep) *ms_per_sample_sweep = b->class_cost[cls];
+    return (int)b->class_L.size();
 }
 
 int sl_batch_get(sl_batch* b, int sample, int slot, int8_t* dst, int* temp_index)
@@ -715,11 +1060,9 @@ void sl_batch_destroy(sl_batch* b)
 {
     if (!b) return;
     cudaStreamSynchronize(b->stream);
-    for (int k = 0; k < 8; ++k) {
-        if (b->side[k]) cudaStreamDestroy(b->side[k]);
-        if (b->ev_join[k]) cudaEventDestroy(b->ev_join[k]);
-    }
-    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->graph_def) cudaGraphDestroy(b->graph_def);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     if (b->owned_buf) cudaFree(b->owned_buf);
     delete b;
 }

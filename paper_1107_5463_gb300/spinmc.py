@@ -24,6 +24,7 @@ SL_OPT_RENORM_EVERY, SL_OPT_FAST_MATH, SL_OPT_KERNEL, SL_OPT_ROWS, SL_OPT_GRAPH 
 SL_OPT_UPDATE, SL_OPT_MULTIHIT, SL_OPT_TILE = 6, 7, 8
 SL_UPDATE_METROPOLIS, SL_UPDATE_HEATBATH, SL_UPDATE_SW = 0, 1, 2
 SL_WOPT_SPINS_SMEM = 1
+SL_BOPT_AUTOTUNE, SL_BOPT_PACK = 1, 2
 
 if not os.path.exists(LIB_PATH):
     raise ImportError("libspinmc.so is not built at %s; run paper_1107_5463_gb300.build.build()"
@@ -64,6 +65,9 @@ _sig("sl_batch_get", _int, _vp, _int, _int, _vp, ctypes.POINTER(_int))
 _sig("sl_batch_get_bonds", _int, _vp, _int, _vp)
 _sig("sl_batch_sweeps_done", _int, _vp, ctypes.POINTER(_i64))
 _sig("sl_batch_destroy", None, _vp)
+_sig("sl_batch_set_option", _int, _vp, _int, _i64)
+_sig("sl_batch_tuning", _int, _vp, _int, ctypes.POINTER(_int), ctypes.POINTER(_int),
+     ctypes.POINTER(_dbl))
 _sig("sl_ising_measure_static", _int, _int, _int, _dbl, _vp, _vp, _vp)
 _sig("sl_walkers_required_bytes", _int, _int, _int, _vp, _vp, _int, ctypes.POINTER(_sz))
 _sig("sl_walkers_create", _int, _int, _int, _vp, _vp, _int, _u64, _vp, _sz, _vp,
@@ -228,6 +232,28 @@ def sl_batch_sweeps_done(h):
 
 def sl_batch_destroy(h):
     _lib.sl_batch_destroy(h)
+
+
+def sl_batch_set_option(h, option, value):
+    _check(_lib.sl_batch_set_option(h, option, value), "sl_batch_set_option")
+
+
+def sl_batch_tuning(h):
+    """[(L, pack, ms per sample-sweep)] for every size class, largest first."""
+    out = []
+    cls = 0
+    while True:
+        L, k, ms = _int(), _int(), _dbl()
+        n = _lib.sl_batch_tuning(h, cls, ctypes.byref(L), ctypes.byref(k), ctypes.byref(ms))
+        if n < 0:
+            if cls == 0:
+                _check(n, "sl_batch_tuning")
+            break
+        out.append((L.value, k.value, ms.value))
+        cls += 1
+        if cls >= n:
+            break
+    return out
 
 
 def sl_ising_measure_static(d, L, J, dev_spins, dev_out, stream):
@@ -478,6 +504,12 @@ class Batch:
                             device=self.buf.device)
         sl_batch_run(self.h, nsweeps, seed, E)
         return E
+
+    def set_option(self, option, value):
+        sl_batch_set_option(self.h, option, value)
+
+    def tuning(self):
+        return sl_batch_tuning(self.h)
 
     def get(self, sample, slot):
         """(spins of the slot in natural order, temperature index it holds)."""

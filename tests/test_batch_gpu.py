@@ -1,8 +1,9 @@
 """GPU parity of the batched Edwards-Anderson +-J spin glass with replica
-exchange (one CTA per disorder sample, replicas multispin-coded in shared
-memory) against the oracle's per-sample, per-replica loops: couplings, start
-states, every slot's spins, the slot-to-temperature assignment and the
-energy series at every temperature, bit for bit."""
+exchange (one persistent launch: CTAs take packs of same-size samples from a
+queue, every sample's replicas multispin-coded in shared memory) against the
+oracle's per-sample, per-replica loops: couplings, start states, every slot's
+spins, the slot-to-temperature assignment and the energy series at every
+temperature, bit for bit, whatever pack sizes the autotuner picks."""
 import numpy as np
 import pytest
 
@@ -40,8 +41,10 @@ def gpu_state(b, s):
     return np.stack(spins), perm
 
 
-def check_batch(sm, d, Ls, nt, betas, nsw, seed=5, run_seed=6, samples=None):
+def check_batch(sm, d, Ls, nt, betas, nsw, seed=5, run_seed=6, samples=None, pack=None):
     b = sm.Batch(d, Ls, nt, betas, seed=seed)
+    if pack is not None:
+        b.set_option(sm.SL_BOPT_PACK, pack)
     E = b.run(nsw, run_seed, series=True).cpu().numpy()
     for s in (range(len(Ls)) if samples is None else samples):
         jb, spins, perm, Er = oracle_sample(d, Ls[s], nt, betas, seed, run_seed, s, nsw)
@@ -106,3 +109,33 @@ def test_bad_arguments(sm):
                              (3, [8], 4, [0.1, -1.0, 0.2, 0.3])):
         with pytest.raises(sm.SpinMCError):
             sm.Batch(d, Ls, nt, betas)
+
+
+@pytest.mark.parametrize("pack", [1, 2, 4, 8])
+def test_parity_forced_pack_sizes(sm, pack):
+    """Every pack size (samples per CTA, each on its own named barrier) gives
+    the oracle's chains; uneven classes leave a partial last pack."""
+    Ls = [8, 12, 8, 16, 12, 8, 24, 8, 16, 12, 8]
+    check_batch(sm, 3, Ls, 12, inputs.geometric_betas(12), 8, pack=pack)
+
+
+def test_autotuner_reports_and_keeps_the_chain(sm):
+    """The tuner times every fitting pack size per class on a copy of the
+    state: afterwards the chain is the oracle's, each class has a pack size
+    that fits (side 32 alone in a CTA) and a positive measured cost."""
+    Ls = [8, 12, 16, 24, 32] * 3
+    nt = 32
+    betas = inputs.geometric_betas(nt)
+    b = sm.Batch(3, Ls, nt, betas, seed=3)
+    E = b.run(6, 4, series=True).cpu().numpy()
+    tune = b.tuning()
+    assert [t[0] for t in tune] == [32, 24, 16, 12, 8]
+    assert tune[0][1] == 1 and all(t[1] in (1, 2, 4, 8) for t in tune)
+    assert all(t[2] > 0 for t in tune)
+    for s in (0, 4, 9):
+        jb, spins, perm, Er = oracle_sample(3, Ls[s], nt, betas, 3, 4, s, 6)
+        gs, gp = gpu_state(b, s)
+        np.testing.assert_array_equal(gs, spins)
+        np.testing.assert_array_equal(gp, perm)
+        np.testing.assert_array_equal(E[s], Er)
+    b.close()
