@@ -31,15 +31,18 @@ UNIT = "flips/ns"
 
 # bytes: algorithmic HBM bytes per site update of one colour pass (read the
 # updated colour and the other colour, write the updated colour)
+# ops: algorithmic 32-bit integer operations per site update (Ising: a quarter
+# of a Philox4x32-10 call = 10 rounds x (2 mulhi + 2 mullo + 4 xor) / 4 = 20,
+# plus about 8 for the neighbour count, threshold compares and flip)
 WORKLOADS = {
-    "ising2d_L16384_i8": dict(d=2, L=16384, n=1, beta=0.440687, storage="i8", bytes=3.0,
+    "ising2d_L16384_i8": dict(d=2, L=16384, n=1, beta=0.440687, storage="i8", bytes=3.0, ops=28,
                               desc="2D Ising ferromagnet J=1, L=16384 periodic, int8 spins, "
                                    "beta_c=0.440687, random start"),
-    "ising3d_L512_i8": dict(d=3, L=512, n=1, beta=0.2216546, storage="i8", bytes=3.0,
+    "ising3d_L512_i8": dict(d=3, L=512, n=1, beta=0.2216546, storage="i8", bytes=3.0, ops=30,
                             desc="3D Ising ferromagnet J=1, L=512 simple cubic, int8 spins, "
                                  "beta=0.2216546, random start"),
     "ising2d_L16384_i8_heatbath": dict(d=2, L=16384, n=1, beta=0.440687, storage="i8",
-                                       bytes=3.0, update=1,
+                                       bytes=3.0, ops=28, update=1,
                                        desc="2D Ising, L=16384, int8 spins, heat-bath rule"),
     "ising2d_L16384_i8_k100": dict(d=2, L=16384, n=1, beta=0.440687, storage="i8", bytes=0.0,
                                    multihit=100, tile=16, paper_flips_per_ns=1 / 0.034,
@@ -87,6 +90,20 @@ def peaks():
             j = json.load(f)
         return j.get("hbm_gbs", 6800.0), "measured"
     return 6800.0, "fallback"
+
+
+def alu_peak_tops():
+    """Integer issue peak of the GPU from its unit counts and clock: every SM
+    issues one 32-bit integer operation per clock on each of its 128 lanes
+    (152 SMs x 128 x 2.07 GHz = 40.3 T ops/s on GB300)."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz = 2070.0
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            mhz = json.load(f).get("sm_max_mhz", mhz)
+    return sms * 128 * mhz * 1e6 / 1e12
 
 
 def kernel_source_hash(files):
@@ -235,6 +252,35 @@ def time_batch(spinmc, wl, steps, warmup, want_clocks, local, rank=0, world=1):
     tuning = b.tuning()
     b.close()
     return ms, cl, tuning
+
+
+def roofline_line(wl, N, hits, launch_ms, achieved_gbs, hbm, peak_kind, traffic, kernel_name,
+                  bytes_per_launch):
+    """The binding roofline of the dominant kernel: the slower of the HBM
+    bound (algorithmic bytes) and the integer-issue bound (algorithmic ops)
+    for the Ising byte paths, which are ALU-bound; the HBM roofline
+    otherwise.  Both figures are per launch (one colour pass)."""
+    hbm_obj = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
+               "frac": achieved_gbs / hbm, "peak_kind": peak_kind, "traffic": traffic,
+               "kernel": kernel_name, "bytes_per_launch": bytes_per_launch,
+               "launch_ms": launch_ms}
+    if not wl.get("ops"):
+        return hbm_obj
+    ops_per_launch = wl["ops"] * hits * (N // 2)
+    achieved = ops_per_launch / (launch_ms * 1e-3) / 1e12
+    peak = alu_peak_tops()
+    alu_bound = peak * 1e12 / wl["ops"] / 1e9          # flips/ns at the issue peak
+    hbm_bound = hbm * 1e9 / wl["bytes"] / 1e9 if wl["bytes"] else float("inf")
+    if hbm_bound < alu_bound:
+        return hbm_obj
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+            "frac": achieved / peak, "peak_kind": "unit counts x max SM clock",
+            "ops_per_site": wl["ops"], "ops_per_launch": ops_per_launch,
+            "traffic": traffic, "kernel": kernel_name, "launch_ms": launch_ms,
+            "bound_flips_per_ns": {"alu": alu_bound, "hbm": hbm_bound},
+            "hbm": {"achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
+                    "frac": achieved_gbs / hbm, "peak_kind": peak_kind,
+                    "bytes_per_launch": bytes_per_launch}}
 
 
 def launch_shape(wl):
@@ -597,10 +643,8 @@ def main():
                    "sites": N, "beta": wl["beta"], "step": "one full sweep + fused E,|m|",
                    "l2": "inputs larger than L2 (%d MB of spins)" % (N // 2**20),
                    "parallelism": "replica per GPU" if world > 1 else "single GPU"},
-        "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved_gbs / hbm, "peak_kind": peak_kind,
-                     "traffic": traffic, "kernel": kernel_name,
-                     "bytes_per_launch": bytes_per_launch, "launch_ms": launch_ms},
+        "roofline": roofline_line(wl, N, hits, launch_ms, achieved_gbs, hbm, peak_kind, traffic,
+                                  kernel_name, bytes_per_launch),
         "gpu_launches": args.steps * launches_per_step + 1,
         "clocks": clocks,
         "check": {"E_per_site_last": e_last / N},
@@ -628,6 +672,9 @@ def main():
                 gbs = w["bytes"] * (n // 2) / (vms / (2 * k) * 1e-3) / 1e9
                 var[name] = {"value": n * k * hits / (vms * 1e6), "unit": UNIT,
                              "ms_per_step": vms / k, "achieved_gbs": gbs, "hbm_frac": gbs / hbm}
+                if w.get("ops"):
+                    var[name]["alu_frac"] = (w["ops"] * var[name]["value"] * 1e9 /
+                                             (alu_peak_tops() * 1e12))
                 if w.get("paper_flips_per_ns"):
                     var[name]["paper_gtx480_flips_per_ns"] = w["paper_flips_per_ns"]
                     var[name]["over_paper_gtx480"] = var[name]["value"] / w["paper_flips_per_ns"]
