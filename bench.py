@@ -71,6 +71,18 @@ WORKLOADS = {
     "heis3d_L256_f32": dict(d=3, L=256, n=3, beta=0.693, storage="vec", bytes=36.0,
                             desc="3D Heisenberg J=1, L=256, FP32 unit vectors, beta=0.693, "
                                  "renormalised every 16 sweeps"),
+    "heis2d_L4096_f32": dict(d=2, L=4096, n=3, beta=0.693, storage="vec", bytes=24.0,
+                             paper_flips_per_ns=1 / 0.50,
+                             desc="2D Heisenberg J=1, L=4096, FP32 unit vectors, FP64 aggregates "
+                                  "(the paper's Table 1 single-precision row)"),
+    "heis2d_L4096_f32_fast": dict(d=2, L=4096, n=3, beta=0.693, storage="vec", bytes=24.0,
+                                  fast=1, paper_flips_per_ns=1 / 0.18,
+                                  desc="2D Heisenberg L=4096 with hardware sin/cos/exp "
+                                       "intrinsics (the paper's Table 1 fast-math row)"),
+    "ising2d_L32_i8_k100": dict(d=2, L=32, n=1, beta=0.440687, storage="i8", bytes=0.0,
+                                multihit=100, tile=16, paper_flips_per_ns=1 / 1.60,
+                                desc="2D Ising L=32, k=100 multi-hit in 16x16 tiles (the paper's "
+                                     "Table 1 small-lattice row)"),
     "xy2d_L4096_f32": dict(d=2, L=4096, n=2, beta=1.12, storage="angle", bytes=12.0,
                            desc="2D XY J=1, L=4096, FP32 angles, beta=1.12"),
     "ea3d_batch_1024x32": dict(d=3, L=32, n=1, beta=None, storage="batch", bytes=0.0,
@@ -300,7 +312,9 @@ def launch_shape(wl):
 
 
 def configure(spinmc, lat, wl):
-    """Apply a workload's update rule and multi-hit options to a lattice."""
+    """Apply a workload's update rule, multi-hit and fast-math options."""
+    if wl.get("fast"):
+        lat.set_option(spinmc.SL_OPT_FAST_MATH, 1)
     if wl.get("update"):
         lat.set_update(wl["update"])
     if wl.get("multihit"):
@@ -372,7 +386,8 @@ def walkers_run(spinmc, wl, sweeps=10):
             "over_paper_gtx480": flips / (ms * 1e6) / wl["paper_flips_per_ns"]}
 
 
-def batch_run(spinmc, nsamples=1024, ntemps=32, sweeps=100, plain_lattices=32, plain_sweeps=20):
+def batch_run(spinmc, nsamples=1024, ntemps=32, sweeps=100, plain_lattices=32, plain_sweeps=20,
+              d=3, sizes=None):
     """The batched Edwards-Anderson workload: nsamples 3D +-J samples of sides
     [8,12,16,24,32][s mod 5], ntemps temperatures geometric in [0.5, 3],
     exchange after every sweep, one run of `sweeps` sweeps timed with CUDA
@@ -381,9 +396,9 @@ def batch_run(spinmc, nsamples=1024, ntemps=32, sweeps=100, plain_lattices=32, p
     for the same number of sweeps per lattice."""
     import torch
     from paper_1107_5463_gb300 import inputs
-    Ls = inputs.ea_sample_sizes(nsamples)
+    Ls = inputs.ea_sample_sizes(nsamples) if sizes is None else list(sizes)
     betas = inputs.geometric_betas(ntemps)
-    b = spinmc.Batch(3, Ls, ntemps, betas, seed=inputs.DEFAULT_SEED)
+    b = spinmc.Batch(d, Ls, ntemps, betas, seed=inputs.DEFAULT_SEED)
     b.run(2, 1)
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -392,7 +407,11 @@ def batch_run(spinmc, nsamples=1024, ntemps=32, sweeps=100, plain_lattices=32, p
     ev1.record(b.stream)
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
-    flips = sum(L ** 3 for L in Ls) * ntemps * sweeps
+    flips = sum(L ** d for L in Ls) * ntemps * sweeps
+    if plain_lattices == 0:
+        b.close()
+        return {"value": flips / (ms * 1e6), "unit": UNIT, "ms": ms, "sweeps": sweeps,
+                "samples": nsamples, "temps": ntemps}
     # plain path: the samples of side 32, one lattice per (sample, temperature)
     lats = []
     s32 = [s for s, L in enumerate(Ls) if L == 32]
@@ -664,7 +683,11 @@ def main():
                 if w["storage"] == "walkers":
                     var[name] = walkers_run(spinmc, w)
                     continue
-                k = 10 if w.get("multihit") else (100 if w.get("update") == 2 else 300)
+                n_sites = w["L"] ** w["d"]
+                if w.get("multihit"):
+                    k = max(10, min(2000, 2 ** 28 // (n_sites * w["multihit"])))
+                else:
+                    k = 100 if w.get("update") == 2 else 300
                 vms, _, _ = time_sweeps(spinmc, w, k, 3 if w.get("multihit") else 5, rank,
                                         False, local)
                 n = w["L"] ** w["d"]
@@ -679,6 +702,12 @@ def main():
                     var[name]["paper_gtx480_flips_per_ns"] = w["paper_flips_per_ns"]
                     var[name]["over_paper_gtx480"] = var[name]["value"] / w["paper_flips_per_ns"]
             var["ea3d_batch_1024x32"] = batch_run(spinmc)
+            # the paper's 2D spin-glass rows (L = 32; 64-bit multi-spin coding:
+            # 0.0023 ns per flip on the GTX 480)
+            v2 = batch_run(spinmc, plain_lattices=0, d=2, sizes=[32] * 1024)
+            v2["paper_gtx480_flips_per_ns"] = 1 / 0.0023
+            v2["over_paper_gtx480"] = v2["value"] / v2["paper_gtx480_flips_per_ns"]
+            var["ea2d_batch_L32_1024x32"] = v2
             line["variants"] = var
         print(json.dumps(line), flush=True)
     barrier(world)

@@ -105,6 +105,7 @@ class Pair:
                 self.max_err = max(self.max_err, float(err.max()))
             dE = abs(float(E[0].item()) - float(Er[0])) / N
             self.max_dE = max(self.max_dE, dE)
+            self.max_dm = max(getattr(self, "max_dm", 0.0), abs(float(m[0].item()) - float(mr[0])))
             if self.ntie == 0:
                 self.max_dE_clean = max(self.max_dE_clean, dE)
                 self.max_dm_clean = max(self.max_dm_clean, abs(float(m[0].item()) - float(mr[0])))
@@ -231,3 +232,23 @@ def test_full_size_first_ten_sweeps(sm, n, d, L, beta):
     p.check(min_fraction=0.3)
     # after near-ties the energies differ by a few units per cone
     assert p.max_dE < 1e-4
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("n,d,L,beta", [(2, 2, 4096, 0.9), (2, 2, 4096, 1.12), (2, 2, 4096, 1.4),
+                                        (3, 3, 256, 0.693)])
+def test_precision_report(sm, n, d, L, beta, capsys):
+    """FP32 kernels against the FP64 oracle per observable on the paper-shaped
+    workloads (XY at the three temperatures of the workload, Heisenberg with
+    renormalisation every 16 sweeps), first 10 sweeps: the largest spin
+    component error outside near-tie cones, |dE|/N and |d|m|| after every
+    sweep, and the number of near-ties; printed as one line per workload."""
+    p = Pair(sm, n, d, L, beta, 10, seed=inputs.DEFAULT_SEED)
+    with capsys.disabled():
+        print("\nprecision n=%d d=%d L=%d beta=%g: component %.2e (%s), |dE|/N %.2e, |d|m|| %.2e, "
+              "near-ties %d, sites compared %.3f" % (n, d, L, beta, p.max_err,
+                                                     "rad" if n == 2 else "per component",
+                                                     p.max_dE, p.max_dm, p.ntie,
+                                                     p.compared / (p.N * p.nsw)))
+    p.check(min_fraction=0.3)
+    assert p.max_dE < 1e-4 and p.max_dm < 1e-4
