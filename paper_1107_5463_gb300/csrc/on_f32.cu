@@ -275,7 +275,7 @@ __device__ __forceinline__ V3 shfl3_down(V3 v)
 }
 
 template <int D, bool FAST>
-__global__ void __launch_bounds__(256, 3) heis_stream(const OnArgs a)
+__global__ void __launch_bounds__(256, D == 2 ? 4 : 3) heis_stream(const OnArgs a)
 {
     __shared__ double red[32];
     const unsigned long long t64 = a.ctrl->t;
