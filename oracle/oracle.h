@@ -156,6 +156,19 @@ int64_t orc_heis_sweeps(int d, int L, double J, const float* Jb, double beta,
                         int renorm_every, double* s, double* E_out, double* absm_out,
                         double tie_tol, int64_t* ties, int64_t ties_cap);
 
+/* Heat-bath sweeps (Section 2: each spin drawn from its conditional law given
+ * its neighbours), same arguments; near-ties are XY rejection-test margins
+ * below tie_tol and Heisenberg sites whose field has |h_z| / |h| < tie_tol
+ * (where the sampling basis changes sign). */
+int64_t orc_xy_heatbath_sweeps(int d, int L, double J, const float* Jb, double beta,
+                               uint64_t seed, uint32_t replica, int64_t t0, int64_t nsweeps,
+                               double* theta, double* E_out, double* absm_out,
+                               double tie_tol, int64_t* ties, int64_t ties_cap);
+int64_t orc_heis_heatbath_sweeps(int d, int L, double J, const float* Jb, double beta,
+                                 uint64_t seed, uint32_t replica, int64_t t0, int64_t nsweeps,
+                                 int renorm_every, double* s, double* E_out, double* absm_out,
+                                 double tie_tol, int64_t* ties, int64_t ties_cap);
+
 /* ---- Edwards-Anderson +-J spin glass with replica exchange --------------
  * One disorder sample of side L with ntemps replicas (slots).  spins holds
  * ntemps configurations [slot][N]; slot_of_temp[k] is the slot currently at

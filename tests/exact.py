@@ -65,6 +65,14 @@ def enumerate_ising(d, L, beta, J=1.0, Jb=None):
                 lnZ=math.log(Z) + wmax, energies=E, probs=p, states=S)
 
 
+def neighbour(d, L, i, k):
+    """Natural index of neighbour k = 2 mu + (0 for -e_mu, 1 for +e_mu) of site i."""
+    x = [i % L, (i // L) % L, i // (L * L)][:d]
+    mu = k >> 1
+    x[mu] = (x[mu] + (1 if k & 1 else -1)) % L
+    return sum(c * L ** a for a, c in enumerate(x))
+
+
 def colour_of_site(d, L):
     N = L ** d
     i = np.arange(N)

@@ -403,6 +403,117 @@ def test_heatbath_two_spin_bond_and_beta_zero():
         assert s[i] == (1 if int(out[j & 3]) < 2**31 else -1)
 
 
+# ------------------------------------------- continuous-spin heat-bath --
+
+def _perp_basis(n):
+    """Any orthonormal pair perpendicular to the unit vector n (numpy)."""
+    a = np.array([1.0, 0.0, 0.0]) if abs(n[0]) < 0.9 else np.array([0.0, 1.0, 0.0])
+    e1 = np.cross(n, a)
+    e1 /= np.linalg.norm(e1)
+    return e1, np.cross(n, e1)
+
+
+@pytest.mark.parametrize("kappa", [0.3, 2.5, 15.0])
+def test_xy_heatbath_draws_the_von_mises_conditional(kappa):
+    """One heat-bath sweep from a fixed state, repeated over 3000 seeds: the
+    new angle of a colour-0 site minus the angle of its (fixed) local field
+    follows the von Mises law with concentration beta |h| (scipy's CDF)."""
+    d, L = 2, 4
+    th0 = inputs.angles(d, L, 8)
+    N = L * L
+    nb = [exact.neighbour(d, L, 0, k) for k in range(4)]
+    hx, hy = sum(math.cos(th0[q]) for q in nb), sum(math.sin(th0[q]) for q in nb)
+    beta = kappa / math.hypot(hx, hy)
+    offs = np.empty(3000)
+    for sd in range(offs.size):
+        th = th0.copy()
+        oracle.xy_sweeps(d, L, th, beta, 1000 + sd, 0, 1, heatbath=True, series=False)
+        offs[sd] = (th[0] - math.atan2(hy, hx) + math.pi) % (2 * math.pi) - math.pi
+        assert 0.0 <= th[N - 1] < 2 * math.pi
+    assert stats.kstest(offs, stats.vonmises(kappa).cdf).pvalue > 1e-3
+    assert abs(np.mean(np.cos(offs)) - exact.two_spin_mean(2, kappa)) < 4 / math.sqrt(offs.size)
+
+
+@pytest.mark.parametrize("kappa", [0.3, 2.5, 15.0])
+def test_heisenberg_heatbath_draws_the_exponential_conditional(kappa):
+    """As above for a Heisenberg site: c = s'.h/|h| has the distribution
+    function (e^{kappa (c+1)} - 1) / (e^{2 kappa} - 1), the azimuth about h
+    is uniform, and the new spin has unit length."""
+    d, L = 3, 4
+    s0 = inputs.unit_vectors(d, L, 9)
+    nb = [exact.neighbour(d, L, 0, k) for k in range(6)]
+    h = s0[nb].sum(axis=0)
+    H = np.linalg.norm(h)
+    n = h / H
+    e1, e2 = _perp_basis(n)
+    beta = kappa / H
+    cs, phis = np.empty(3000), np.empty(3000)
+    for sd in range(cs.size):
+        s = s0.copy()
+        oracle.heis_sweeps(d, L, s, beta, 1000 + sd, 0, 1, renorm_every=0, heatbath=True,
+                           series=False)
+        v = s[0]
+        assert abs(np.linalg.norm(v) - 1.0) < 1e-12
+        cs[sd] = v @ n
+        phis[sd] = math.atan2(v @ e2, v @ e1)
+    cdf = lambda c: np.expm1(kappa * (np.asarray(c) + 1)) / math.expm1(2 * kappa)
+    assert stats.kstest(cs, cdf).pvalue > 1e-3
+    assert stats.kstest(phis, stats.uniform(-math.pi, 2 * math.pi).cdf).pvalue > 1e-3
+
+
+@pytest.mark.parametrize("n", [2, 3])
+def test_continuous_heatbath_two_spin_bond(n):
+    """The single-bond lattice under heat-bath sweeps: the bond variable
+    follows the exact two-spin law (mean and KS), as under Metropolis; every
+    other site has h = 0 and is redrawn uniformly."""
+    d, L, beta = 2, 4, 1.4
+    jb = inputs.two_spin_bonds(d, L, 0, 0).astype(np.float32)
+    nsw = 40_000
+    if n == 2:
+        th = oracle.xy_init(d, L, 5)
+        E, _, _, _ = oracle.xy_sweeps(d, L, th, beta, 6, 0, nsw, Jb=jb, heatbath=True)
+    else:
+        s = oracle.heis_init(d, L, 5)
+        E, _, _, _ = oracle.heis_sweeps(d, L, s, beta, 6, 0, nsw, Jb=jb, heatbath=True)
+    x = -E[10:]
+    mean, err = exact.binned_mean(x, 50)
+    assert abs(mean - exact.two_spin_mean(n, beta)) < 3 * err, (mean, err)
+    assert stats.kstest(x[::7][:3000], exact.two_spin_cdf(n, beta)).pvalue > 1e-3
+
+
+def test_continuous_heatbath_at_beta_zero_is_uniform():
+    """beta = 0: every new XY angle is uniform on the circle and every new
+    Heisenberg spin uniform on the sphere (z uniform on [-1, 1], azimuth
+    uniform), whatever the old state."""
+    th = np.zeros(64 * 64)
+    oracle.xy_sweeps(2, 64, th, 0.0, 3, 0, 1, heatbath=True, series=False)
+    assert stats.kstest(th, stats.uniform(0, 2 * math.pi).cdf).pvalue > 1e-3
+    s = np.tile([0.0, 0.0, 1.0], (16 ** 3, 1))
+    oracle.heis_sweeps(3, 16, s, 0.0, 3, 0, 1, heatbath=True, series=False)
+    assert stats.kstest(s[:, 2], stats.uniform(-1, 2).cdf).pvalue > 1e-3
+    assert stats.kstest(np.arctan2(s[:, 1], s[:, 0]),
+                        stats.uniform(-math.pi, 2 * math.pi).cdf).pvalue > 1e-3
+
+
+@pytest.mark.parametrize("n,d,L,beta", [(2, 2, 8, 1.12), (3, 3, 4, 0.693)])
+def test_continuous_heatbath_and_metropolis_agree_in_equilibrium(n, d, L, beta):
+    """Both rules leave the Boltzmann law invariant: their mean energies on
+    the same lattice agree within three combined standard errors."""
+    nsw = 30_000
+    res = []
+    for hb in (False, True):
+        if n == 2:
+            st = oracle.xy_init(d, L, 11)
+            E, _, _, _ = oracle.xy_sweeps(d, L, st, beta, 12, 0, nsw, heatbath=hb)
+        else:
+            st = oracle.heis_init(d, L, 11)
+            E, _, _, _ = oracle.heis_sweeps(d, L, st, beta, 12, 0, nsw, heatbath=hb)
+        res.append(exact.binned_mean(E[2000:] / L ** d, 40))
+    (m0, e0), (m1, e1) = res
+    assert abs(m0 - m1) < 3 * math.hypot(e0, e1), res
+    assert max(e0, e1) < 1e-2
+
+
 # ------------------------------------------------------------ multi-hit --
 
 @pytest.mark.parametrize("k,beta", [(1, 0.35), (2, 0.2)])
