@@ -85,6 +85,14 @@ WORKLOADS = {
                                      "Table 1 small-lattice row)"),
     "xy2d_L4096_f32": dict(d=2, L=4096, n=2, beta=1.12, storage="angle", bytes=12.0,
                            desc="2D XY J=1, L=4096, FP32 angles, beta=1.12"),
+    "heis3d_L256_f32_heatbath": dict(d=3, L=256, n=3, beta=0.693, storage="vec", bytes=36.0,
+                                     update=1,
+                                     desc="3D Heisenberg L=256, FP32 vectors, heat-bath rule "
+                                          "(exponential draws about the local field)"),
+    "xy2d_L4096_f32_heatbath": dict(d=2, L=4096, n=2, beta=1.12, storage="angle", bytes=12.0,
+                                    update=1,
+                                    desc="2D XY L=4096, FP32 angles, heat-bath rule (Best-Fisher "
+                                         "von Mises draws)"),
     "ea3d_batch_1024x32": dict(d=3, L=32, n=1, beta=None, storage="batch", bytes=0.0,
                                samples=1024, temps=32,
                                desc="3D Edwards-Anderson +-J, 1024 samples of sides "
@@ -304,10 +312,11 @@ def launch_shape(wl):
         return 3, "ising_tile_kernel<%d,%d>" % (d, wl["tile"])
     if wl["storage"] == "bits":
         return 2, "bits_stream<%d,0>" % d
+    hb = 1 if wl.get("update") == 1 else 0
     if wl["storage"] == "vec":
-        return 2, "heis_stream<%d,0>" % d
+        return 2, "heis_stream<%d,%d,%d>" % (d, wl.get("fast", 0), hb)
     if wl["storage"] == "angle":
-        return 2, "xy_stream<0>"
+        return 2, "xy_stream<0,%d>" % hb
     return 2, "i8_stream<%d,0,0,%d>" % (d, 1 if wl.get("update") == 1 else 0)
 
 
@@ -496,9 +505,9 @@ def oracle_sweep(wl, s, t, L=None):
     from paper_1107_5463_gb300 import inputs
     d, L, beta, seed = wl["d"], L or wl["L"], wl["beta"], inputs.DEFAULT_SEED
     if wl["n"] == 3:
-        oracle.heis_sweeps(d, L, s, beta, seed, t, 1)
+        oracle.heis_sweeps(d, L, s, beta, seed, t, 1, heatbath=wl.get("update") == 1)
     elif wl["n"] == 2:
-        oracle.xy_sweeps(d, L, s, beta, seed, t, 1)
+        oracle.xy_sweeps(d, L, s, beta, seed, t, 1, heatbath=wl.get("update") == 1)
     elif wl.get("update") == 2:
         oracle.ising_sw_sweeps(d, L, s, beta, seed, t, 1)
     elif wl.get("update") == 1:

@@ -84,7 +84,16 @@ extern "C" {
 
 /* update rules for SL_OPT_UPDATE */
 #define SL_UPDATE_METROPOLIS 0 /* Eq. 2 */
-#define SL_UPDATE_HEATBATH 1   /* Ising bytes: s_i = +1 iff u < 2^32 / (1 + exp(-2 beta J h_i)) */
+#define SL_UPDATE_HEATBATH 1   /* heat-bath (Section 2): each spin drawn from its conditional
+                                  law given its neighbours.  Ising bytes: s_i = +1 iff
+                                  u < 2^32 / (1 + exp(-2 beta J h_i)).  XY: the offset from the
+                                  angle of h by the von Mises rejection method of Best and
+                                  Fisher, attempt a of a site using Philox counter word 3 =
+                                  a << 16 | colour (at most 32 attempts, else the angle is
+                                  kept).  Heisenberg: c = s'.h/|h| by inverting its exponential
+                                  law at u24(output 0), azimuth 2 pi u24(output 1) in the
+                                  orthonormal basis of Duff et al. (2017) around h.  Not for
+                                  bit storage or multi-hit sweeps */
 #define SL_UPDATE_SW 2         /* Ising bytes, uniform J, N <= 2^30: Swendsen-Wang cluster
                                   updates (Section 3), one per sweep index; needs a workspace
                                   (sl_workspace_bytes / sl_attach_workspace) */

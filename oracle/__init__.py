@@ -67,9 +67,12 @@ def lib():
         L.orc_heis_sweeps.argtypes = [_int, _int, _dbl, _vp, _dbl, _u64, _u32, _i64, _i64,
                                       _int, _f64p, _vp, _vp, _dbl, _vp, _i64]
         L.orc_heis_sweeps.restype = _i64
-        L.orc_xy_heatbath_sweeps.argtypes = L.orc_xy_sweeps.argtypes
+        L.orc_xy_heatbath_sweeps.argtypes = [_int, _int, _dbl, _vp, _dbl, _u64, _u32, _i64,
+                                             _i64, _int, _f64p, _vp, _vp, _dbl, _vp, _i64]
         L.orc_xy_heatbath_sweeps.restype = _i64
-        L.orc_heis_heatbath_sweeps.argtypes = L.orc_heis_sweeps.argtypes
+        L.orc_heis_heatbath_sweeps.argtypes = [_int, _int, _dbl, _vp, _dbl, _u64, _u32, _i64,
+                                               _i64, _int, _int, _f64p, _vp, _vp, _dbl, _vp,
+                                               _i64]
         L.orc_heis_heatbath_sweeps.restype = _i64
         L.orc_ea_pt_sweeps.argtypes = [_int, _int, _i8p, _int, _f64p, _u64, _u32, _i64, _i64,
                                        _i8p, _i32p, _f64p]
@@ -278,32 +281,46 @@ def heis_measure(d, L, s, J=1.0, Jb=None):
 
 
 def xy_sweeps(d, L, theta, beta, seed, t0, nsweeps, J=1.0, Jb=None, replica=0,
-              tie_tol=0.0, ties_cap=0, series=True, heatbath=False):
+              tie_tol=0.0, ties_cap=0, series=True, heatbath=False, colours=3):
     """Sweeps (Metropolis, or heat-bath if heatbath) in place on theta; return
-    (E, |m|, near-ties (k,2) array, count)."""
+    (E, |m|, near-ties (k,2) array, count).  Heat-bath only: colours = 1 or 2
+    runs just the pass of colour 0 or 1."""
     assert theta.dtype == np.float64 and theta.flags.c_contiguous
+    assert colours == 3 or heatbath
     jb = _bonds_f32(Jb, d, L)
     E = np.empty(nsweeps) if series else None
     m = np.empty(nsweeps) if series else None
     ties = np.zeros((max(ties_cap, 1), 2), np.int64)
-    fn = lib().orc_xy_heatbath_sweeps if heatbath else lib().orc_xy_sweeps
-    n = fn(d, L, J, _ptr(jb), beta, seed, replica, t0, nsweeps, theta, _ptr(E), _ptr(m), tie_tol,
-           _ptr(ties), ties_cap)
+    if heatbath:
+        n = lib().orc_xy_heatbath_sweeps(d, L, J, _ptr(jb), beta, seed, replica, t0, nsweeps,
+                                         colours, theta, _ptr(E), _ptr(m), tie_tol, _ptr(ties),
+                                         ties_cap)
+    else:
+        n = lib().orc_xy_sweeps(d, L, J, _ptr(jb), beta, seed, replica, t0, nsweeps, theta,
+                                _ptr(E), _ptr(m), tie_tol, _ptr(ties), ties_cap)
     return E, m, ties[:min(n, ties_cap)], n
 
 
 def heis_sweeps(d, L, s, beta, seed, t0, nsweeps, J=1.0, Jb=None, replica=0,
-                renorm_every=16, tie_tol=0.0, ties_cap=0, series=True, heatbath=False):
+                renorm_every=16, tie_tol=0.0, ties_cap=0, series=True, heatbath=False,
+                colours=3):
     """Sweeps (Metropolis, or heat-bath if heatbath) in place on s (N,3);
-    return (E, |m|, near-ties (k,2) array, count)."""
+    return (E, |m|, near-ties (k,2) array, count).  Heat-bath only: colours =
+    1 or 2 runs just the pass of colour 0 or 1."""
     assert s.dtype == np.float64 and s.flags.c_contiguous
+    assert colours == 3 or heatbath
     jb = _bonds_f32(Jb, d, L)
     E = np.empty(nsweeps) if series else None
     m = np.empty(nsweeps) if series else None
     ties = np.zeros((max(ties_cap, 1), 2), np.int64)
-    fn = lib().orc_heis_heatbath_sweeps if heatbath else lib().orc_heis_sweeps
-    n = fn(d, L, J, _ptr(jb), beta, seed, replica, t0, nsweeps, renorm_every, s.reshape(-1),
-           _ptr(E), _ptr(m), tie_tol, _ptr(ties), ties_cap)
+    if heatbath:
+        n = lib().orc_heis_heatbath_sweeps(d, L, J, _ptr(jb), beta, seed, replica, t0, nsweeps,
+                                           colours, renorm_every, s.reshape(-1), _ptr(E),
+                                           _ptr(m), tie_tol, _ptr(ties), ties_cap)
+    else:
+        n = lib().orc_heis_sweeps(d, L, J, _ptr(jb), beta, seed, replica, t0, nsweeps,
+                                  renorm_every, s.reshape(-1), _ptr(E), _ptr(m), tie_tol,
+                                  _ptr(ties), ties_cap)
     return E, m, ties[:min(n, ties_cap)], n
 
 

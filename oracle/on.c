@@ -156,8 +156,8 @@ static int xy_heatbath_draw(double hx, double hy, double beta, const uint32_t ke
 
 static int64_t xy_sweeps(int d, int L, double J, const float* Jb, double beta, uint64_t seed,
                          uint32_t replica, int64_t t0, int64_t nsweeps, int heatbath,
-                         double* theta, double* E_out, double* absm_out, double tie_tol,
-                         int64_t* ties, int64_t ties_cap)
+                         int colours, double* theta, double* E_out, double* absm_out,
+                         double tie_tol, int64_t* ties, int64_t ties_cap)
 {
     orc_geom g = orc_make_geom(d, L);
     const uint32_t key[2] = {orc_key_lo(seed), orc_key_hi(seed)};
@@ -166,7 +166,7 @@ static int64_t xy_sweeps(int d, int L, double J, const float* Jb, double beta, u
     for (int64_t step = 0; step < nsweeps; ++step) {
         int64_t t = t0 + step;
         for (int c = 0; c < 2; ++c)
-            for (int z = 0; z < Lz; ++z)
+            for (int z = 0; z < Lz && ((colours >> c) & 1); ++z)
                 for (int y = 0; y < L; ++y)
                     for (int x0 = (c + y + z) & 1; x0 < L; x0 += 2) {
                         int x[3] = {x0, y, z};
@@ -217,17 +217,17 @@ int64_t orc_xy_sweeps(int d, int L, double J, const float* Jb, double beta,
                       double* theta, double* E_out, double* absm_out,
                       double tie_tol, int64_t* ties, int64_t ties_cap)
 {
-    return xy_sweeps(d, L, J, Jb, beta, seed, replica, t0, nsweeps, 0, theta, E_out, absm_out,
-                     tie_tol, ties, ties_cap);
+    return xy_sweeps(d, L, J, Jb, beta, seed, replica, t0, nsweeps, 0, 3, theta, E_out,
+                     absm_out, tie_tol, ties, ties_cap);
 }
 
 int64_t orc_xy_heatbath_sweeps(int d, int L, double J, const float* Jb, double beta,
                                uint64_t seed, uint32_t replica, int64_t t0, int64_t nsweeps,
-                               double* theta, double* E_out, double* absm_out,
+                               int colours, double* theta, double* E_out, double* absm_out,
                                double tie_tol, int64_t* ties, int64_t ties_cap)
 {
-    return xy_sweeps(d, L, J, Jb, beta, seed, replica, t0, nsweeps, 1, theta, E_out, absm_out,
-                     tie_tol, ties, ties_cap);
+    return xy_sweeps(d, L, J, Jb, beta, seed, replica, t0, nsweeps, 1, colours, theta, E_out,
+                     absm_out, tie_tol, ties, ties_cap);
 }
 
 /* -------------------------------------------------------- Heisenberg ---- */
@@ -294,7 +294,9 @@ static double heis_heatbath_draw(const double h[3], double beta, double u, doubl
         if (omc <= 1.0) {
             opc = 2.0 - omc;
         } else {
-            opc = log1p(u * expm1(2.0 * kappa)) / kappa;
+            /* where expm1 overflows, log1p(u e^{2 kappa}) = log(u) + 2 kappa */
+            opc = 2.0 * kappa < 700.0 ? log1p(u * expm1(2.0 * kappa)) / kappa
+                                      : fmax(0.0, 2.0 + log(u) / kappa);
             omc = 2.0 - opc;
         }
     } else {
@@ -319,8 +321,8 @@ static double heis_heatbath_draw(const double h[3], double beta, double u, doubl
 
 static int64_t heis_sweeps(int d, int L, double J, const float* Jb, double beta, uint64_t seed,
                            uint32_t replica, int64_t t0, int64_t nsweeps, int heatbath,
-                           int renorm_every, double* s, double* E_out, double* absm_out,
-                           double tie_tol, int64_t* ties, int64_t ties_cap)
+                           int colours, int renorm_every, double* s, double* E_out,
+                           double* absm_out, double tie_tol, int64_t* ties, int64_t ties_cap)
 {
     orc_geom g = orc_make_geom(d, L);
     const uint32_t key[2] = {orc_key_lo(seed), orc_key_hi(seed)};
@@ -330,7 +332,7 @@ static int64_t heis_sweeps(int d, int L, double J, const float* Jb, double beta,
         int64_t t = t0 + step;
         int renorm = renorm_every > 0 && (t + 1) % renorm_every == 0;
         for (int c = 0; c < 2; ++c)
-            for (int z = 0; z < Lz; ++z)
+            for (int z = 0; z < Lz && ((colours >> c) & 1); ++z)
                 for (int y = 0; y < L; ++y)
                     for (int x0 = (c + y + z) & 1; x0 < L; x0 += 2) {
                         int x[3] = {x0, y, z};
@@ -386,15 +388,16 @@ int64_t orc_heis_sweeps(int d, int L, double J, const float* Jb, double beta,
                         int renorm_every, double* s, double* E_out, double* absm_out,
                         double tie_tol, int64_t* ties, int64_t ties_cap)
 {
-    return heis_sweeps(d, L, J, Jb, beta, seed, replica, t0, nsweeps, 0, renorm_every, s, E_out,
-                       absm_out, tie_tol, ties, ties_cap);
+    return heis_sweeps(d, L, J, Jb, beta, seed, replica, t0, nsweeps, 0, 3, renorm_every, s,
+                       E_out, absm_out, tie_tol, ties, ties_cap);
 }
 
 int64_t orc_heis_heatbath_sweeps(int d, int L, double J, const float* Jb, double beta,
                                  uint64_t seed, uint32_t replica, int64_t t0, int64_t nsweeps,
-                                 int renorm_every, double* s, double* E_out, double* absm_out,
-                                 double tie_tol, int64_t* ties, int64_t ties_cap)
+                                 int colours, int renorm_every, double* s, double* E_out,
+                                 double* absm_out, double tie_tol, int64_t* ties,
+                                 int64_t ties_cap)
 {
-    return heis_sweeps(d, L, J, Jb, beta, seed, replica, t0, nsweeps, 1, renorm_every, s, E_out,
-                       absm_out, tie_tol, ties, ties_cap);
+    return heis_sweeps(d, L, J, Jb, beta, seed, replica, t0, nsweeps, 1, colours, renorm_every, s,
+                       E_out, absm_out, tie_tol, ties, ties_cap);
 }

@@ -157,17 +157,20 @@ int64_t orc_heis_sweeps(int d, int L, double J, const float* Jb, double beta,
                         double tie_tol, int64_t* ties, int64_t ties_cap);
 
 /* Heat-bath sweeps (Section 2: each spin drawn from its conditional law given
- * its neighbours), same arguments; near-ties are XY rejection-test margins
- * below tie_tol and Heisenberg sites whose field has |h_z| / |h| < tie_tol
- * (where the sampling basis changes sign). */
+ * its neighbours), same arguments plus `colours`: bit c set runs the pass of
+ * colour c (3 = whole sweeps; a single pass repeats one colour update from
+ * given inputs).  Near-ties are XY rejection-test margins below tie_tol and
+ * Heisenberg sites whose field has |h_z| / |h| < tie_tol (where the sampling
+ * basis changes sign). */
 int64_t orc_xy_heatbath_sweeps(int d, int L, double J, const float* Jb, double beta,
                                uint64_t seed, uint32_t replica, int64_t t0, int64_t nsweeps,
-                               double* theta, double* E_out, double* absm_out,
+                               int colours, double* theta, double* E_out, double* absm_out,
                                double tie_tol, int64_t* ties, int64_t ties_cap);
 int64_t orc_heis_heatbath_sweeps(int d, int L, double J, const float* Jb, double beta,
                                  uint64_t seed, uint32_t replica, int64_t t0, int64_t nsweeps,
-                                 int renorm_every, double* s, double* E_out, double* absm_out,
-                                 double tie_tol, int64_t* ties, int64_t ties_cap);
+                                 int colours, int renorm_every, double* s, double* E_out,
+                                 double* absm_out, double tie_tol, int64_t* ties,
+                                 int64_t ties_cap);
 
 /* ---- Edwards-Anderson +-J spin glass with replica exchange --------------
  * One disorder sample of side L with ntemps replicas (slots).  spins holds

@@ -517,8 +517,10 @@ int sl_set_option(sl_lattice* h, int option, int64_t value)
         if (value != SL_UPDATE_METROPOLIS && value != SL_UPDATE_HEATBATH && value != SL_UPDATE_SW)
             return fail(SL_EINVAL, "update must be 0 (Metropolis), 1 (heat-bath) or 2 "
                                    "(Swendsen-Wang)");
-        if (value != SL_UPDATE_METROPOLIS && h->storage != SL_STORE_I8)
-            return fail(SL_EINVAL, "heat-bath and Swendsen-Wang updates need Ising byte storage");
+        if (value == SL_UPDATE_HEATBATH && h->storage == SL_STORE_BITS)
+            return fail(SL_EINVAL, "the heat-bath rule needs byte (Ising) or FP32 storage");
+        if (value == SL_UPDATE_SW && h->storage != SL_STORE_I8)
+            return fail(SL_EINVAL, "Swendsen-Wang updates need Ising byte storage");
         if (value != SL_UPDATE_METROPOLIS && h->multihit > 0)
             return fail(SL_EINVAL, "multi-hit sweeps use the Metropolis rule");
         if (value == SL_UPDATE_SW) {

@@ -17,6 +17,16 @@
 // FAST selects the hardware sin/cos/exp intrinsics (the "fast math" row of
 // Table 1), with angles shifted into [-pi, pi) where the intrinsics are
 // accurate.
+//
+// HB selects the heat-bath rule (Section 2's other local update): the new
+// spin is drawn from its conditional law, density proportional to
+// exp(beta s' . h), independent of the old spin.  Heisenberg: c = s'.h/|h|
+// by inverting its exponential distribution function at u24(output 0), the
+// azimuth 2 pi u24(output 1) in the orthonormal basis of Duff et al.
+// (JCGT 2017) around h.  XY: the offset from the angle of h by the
+// von Mises rejection method of Best and Fisher (1979), attempt a of a site
+// drawing its two uniforms from Philox(group, t, replica, a << 16 | colour).
+// The draws use the accurate log1p / expm1 / atan2 / sincospi whatever FAST.
 #include "internal.h"
 
 namespace spinmc {
@@ -43,6 +53,10 @@ struct OnArgs {
 };
 
 __device__ __forceinline__ float u24(uint32_t x) { return (float)(x >> 8) * (1.0f / 16777216.0f); }
+
+struct V3 {
+    float x, y, z;
+};
 
 // sin and cos of an angle given in turns t in [0, 1)
 template <bool FAST>
@@ -81,6 +95,105 @@ __device__ __forceinline__ float3 sphere_point(uint32_t oz, uint32_t ophi)
     return make_float3(r * cp, r * sp, z);
 }
 
+// Heat-bath draw of a Heisenberg spin in the local field h, kappa = beta |h|.
+// 1 - c and 1 + c are both formed without
+// cancellation: 1 - c = -log1p((1 - u) expm1(-2 kappa)) / kappa when that is
+// <= 1, else 1 + c = log1p(u expm1(2 kappa)) / kappa (for 2 kappa > 80,
+// where expm1 overflows, 2 + log(u) / kappa, exact to FP32 precision).
+__device__ __forceinline__ V3 heis_heatbath(float hx, float hy, float hz, float beta,
+                                             uint32_t o0, uint32_t o1)
+{
+    const float H2 = hx * hx + hy * hy + hz * hz;
+    float nx = 0.f, ny = 0.f, nz = 1.f, kappa = 0.f;
+    if (H2 > 0.f) {
+        const float inv = rsqrtf(H2);
+        nx = hx * inv;
+        ny = hy * inv;
+        nz = hz * inv;
+        kappa = beta * (H2 * inv);
+    }
+    const float u = u24(o0);
+    float omc, opc;  // 1 - c, 1 + c
+    if (kappa > 0.f) {
+        omc = -log1pf((1.f - u) * expm1f(-2.f * kappa)) / kappa;
+        if (omc <= 1.f) {
+            opc = 2.f - omc;
+        } else {
+            opc = 2.f * kappa <= 80.f ? log1pf(u * expm1f(2.f * kappa)) / kappa
+                                      : fmaxf(0.f, 2.f + logf(u) / kappa);
+            omc = 2.f - opc;
+        }
+    } else {
+        omc = 2.f * (1.f - u);
+        opc = 2.f * u;
+    }
+    omc = fmaxf(omc, 0.f);
+    opc = fmaxf(opc, 0.f);
+    const float c = omc <= 1.f ? 1.f - omc : opc - 1.f;
+    const float r = sqrtf(omc * opc);
+    // basis (e1, e2, n) of Duff et al.: smooth except where n_z changes sign
+    const float sg = copysignf(1.f, nz);
+    const float ia = -1.f / (sg + nz);
+    const float b = nx * ny * ia;
+    float sp, cp;
+    sincospif(2.0f * u24(o1), &sp, &cp);
+    const float p1 = r * cp, p2 = r * sp;
+    V3 v;
+    v.x = c * nx + p1 * (1.f + sg * nx * nx * ia) + p2 * b;
+    v.y = c * ny + p1 * (sg * b) + p2 * (sg + ny * ny * ia);
+    v.z = c * nz - p1 * (sg * nx) - p2 * ny;
+    return v;
+}
+
+// Per-site constants of the Best-Fisher von Mises sampler for kappa = beta |h|:
+// the wrapped-Cauchy parameter rho = 2 kappa / (tau + sqrt(2 tau)),
+// tau = 1 + sqrt(1 + 4 kappa^2), the half-angle factor g = (1 - rho) / (1 + rho)
+// and the numerator of the test quantity, (tau + sqrt(2 tau)) (1 - rho^2)^2 / 4.
+struct VonMises {
+    float rho, g, cnum, base;  // base: angle of h in turns
+};
+
+__device__ __forceinline__ VonMises von_mises_setup(float hx, float hy, float beta)
+{
+    VonMises m;
+    const float kappa = beta * sqrtf(hx * hx + hy * hy);
+    const float tau = 1.f + sqrtf(1.f + 4.f * kappa * kappa);
+    const float s2 = sqrtf(2.f * tau);
+    m.rho = 2.f * kappa / (tau + s2);
+    m.g = (1.f - m.rho) / (1.f + m.rho);
+    const float q = 1.f - m.rho * m.rho;
+    m.cnum = 0.25f * (tau + s2) * q * q;
+    m.base = atan2f(hy, hx) * (1.0f / kTwoPiF);
+    return m;
+}
+
+// The acceptance test of one Best-Fisher attempt from the raw outputs o1
+// (U1, with w = pi U1 / 2) and o2 (U2).
+__device__ __forceinline__ bool von_mises_accept(const VonMises& m, uint32_t o1, uint32_t o2)
+{
+    const float cw = cospif(0.5f * u24(o1));
+    const float omr = 1.f - m.rho;
+    const float cc = m.cnum / (omr * omr + 4.f * m.rho * cw * cw);
+    const float U2 = u24(o2);
+    return cc * (2.f - cc) > U2 || logf(cc / U2) + 1.f - cc >= 0.f;
+}
+
+// The new angle, in turns in [0, 1), of the accepted attempt with output o1:
+// the angle of h plus or minus (bit 0 of o1) delta, tan(delta/2) = g tan w.
+// Kept out of the attempt loop so that a warp pays for it once.
+__device__ __forceinline__ float von_mises_angle(const VonMises& m, uint32_t o1)
+{
+    float sw, cw;
+    sincospif(0.5f * u24(o1), &sw, &cw);
+    float dt = atan2f(m.g * sw, cw) * (1.0f / kPiF);
+    if (o1 & 1u) dt = -dt;
+    float tn = m.base + dt;
+    tn -= floorf(tn);
+    return tn < 1.f ? tn : 0.f;
+}
+
+constexpr int kVonMisesAttempts = 32;
+
 __device__ __forceinline__ void on_finish(const OnArgs& a, const Partial& tot)
 {
     Ctrl* C = a.ctrl;
@@ -99,7 +212,7 @@ __device__ __forceinline__ void on_finish(const OnArgs& a, const Partial& tot)
 
 // One thread per site; a block walks whole rows (fixed y, z) so that the
 // loads of a warp are contiguous.  Any even L.
-template <int NC, int D, bool FAST>
+template <int NC, int D, bool FAST, bool HB>
 __global__ void __launch_bounds__(128) on_generic(const OnArgs a)
 {
     __shared__ double red[32];
@@ -169,7 +282,32 @@ __global__ void __launch_bounds__(128) on_generic(const OnArgs a)
                 sz = a.own[2 * H + j];
             }
             bool changed = false;
-            if (a.update) {
+            if (a.update && HB) {
+                if (NC == 2) {
+                    const VonMises vm = von_mises_setup(hx, hy, a.beta);
+                    for (int at = 0; at < kVonMisesAttempts; ++at) {
+                        const uint4 r = philox4x32_10(
+                            make_uint4((uint32_t)(j >> 1), t, a.replica,
+                                       ((uint32_t)at << 16) | (kSweep << 1) | (uint32_t)a.c),
+                            a.rk);
+                        const uint32_t o1 = (j & 1) ? r.z : r.x;
+                        if (von_mises_accept(vm, o1, (j & 1) ? r.w : r.y)) {
+                            th = von_mises_angle(vm, o1);
+                            sincos_angle<FAST>(th, &sy, &sx);
+                            changed = true;
+                            break;
+                        }
+                    }
+                } else {
+                    const uint4 r = philox4x32_10(
+                        make_uint4((uint32_t)j, t, a.replica, (kSweep << 1) | (uint32_t)a.c), a.rk);
+                    const V3 v = heis_heatbath(hx, hy, hz, a.beta, r.x, r.y);
+                    sx = v.x;
+                    sy = v.y;
+                    sz = v.z;
+                    changed = true;
+                }
+            } else if (a.update) {
                 float nx, ny, nz = 0.f, nth = 0.f, u;
                 if (NC == 2) {
                     const uint4 r = philox4x32_10(
@@ -198,6 +336,8 @@ __global__ void __launch_bounds__(128) on_generic(const OnArgs a)
                     th = nth;
                     changed = true;
                 }
+            }
+            if (a.update) {
                 if (renorm) {
                     const float inv = rsqrtf(sx * sx + sy * sy + sz * sz);
                     sx *= inv;
@@ -243,10 +383,6 @@ __global__ void __launch_bounds__(128) on_generic(const OnArgs a)
 // warp-edge lanes load theirs).  Loads for the next row are issued one row
 // ahead.
 
-struct V3 {
-    float x, y, z;
-};
-
 __device__ __forceinline__ V3 ld3(const float* p, long long H, long long i)
 {
     V3 v;
@@ -274,8 +410,8 @@ __device__ __forceinline__ V3 shfl3_down(V3 v)
     return r;
 }
 
-template <int D, bool FAST>
-__global__ void __launch_bounds__(256, D == 2 ? 4 : 3) heis_stream(const OnArgs a)
+template <int D, bool FAST, bool HB>
+__global__ void __launch_bounds__(256, D == 2 && !HB ? 4 : 3) heis_stream(const OnArgs a)
 {
     __shared__ double red[32];
     const unsigned long long t64 = a.ctrl->t;
@@ -382,15 +518,20 @@ __global__ void __launch_bounds__(256, D == 2 ? 4 : 3) heis_stream(const OnArgs 
             if (a.update) {
                 const uint4 rnd = philox4x32_10(
                     make_uint4((uint32_t)j, t, a.replica, (kSweep << 1) | (uint32_t)a.c), a.rk);
-                const float u = u24(rnd.x);
-                const float3 v = sphere_point<FAST>(rnd.y, rnd.z);
-                const float dE = -((v.x - s.x) * hx + (v.y - s.y) * hy + (v.z - s.z) * hz);
                 bool changed = false;
-                if (dE <= 0.f || u < boltzmann<FAST>(-a.beta * dE)) {
-                    s.x = v.x;
-                    s.y = v.y;
-                    s.z = v.z;
+                if (HB) {
+                    s = heis_heatbath(hx, hy, hz, a.beta, rnd.x, rnd.y);
                     changed = true;
+                } else {
+                    const float u = u24(rnd.x);
+                    const float3 v = sphere_point<FAST>(rnd.y, rnd.z);
+                    const float dE = -((v.x - s.x) * hx + (v.y - s.y) * hy + (v.z - s.z) * hz);
+                    if (dE <= 0.f || u < boltzmann<FAST>(-a.beta * dE)) {
+                        s.x = v.x;
+                        s.y = v.y;
+                        s.z = v.z;
+                        changed = true;
+                    }
                 }
                 if (renorm) {
                     const float inv = rsqrtf(s.x * s.x + s.y * s.y + s.z * s.z);
@@ -441,7 +582,7 @@ __device__ __forceinline__ CS2 cs_pair(const float* p, long long i)
 
 // XY, 2D: each thread owns the column pair (2q, 2q+1), whose sites share one
 // Philox block (group j >> 1).
-template <bool FAST>
+template <bool FAST, bool HB>
 __global__ void __launch_bounds__(256) xy_stream(const OnArgs a)
 {
     __shared__ double red[32];
@@ -520,7 +661,32 @@ __global__ void __launch_bounds__(256) xy_stream(const OnArgs a)
             float sx0, sy0, sx1, sy1;
             sincos_angle<FAST>(th.x, &sy0, &sx0);
             sincos_angle<FAST>(th.y, &sy1, &sx1);
-            if (a.update) {
+            if (a.update && HB) {
+                // both sites of the pair draw from the same Philox block per attempt
+                const VonMises m0 = von_mises_setup(hx0, hy0, a.beta);
+                const VonMises m1 = von_mises_setup(hx1, hy1, a.beta);
+                bool p0 = true, p1 = true;
+                uint32_t acc0 = 0u, acc1 = 0u;  // U1 outputs of the accepted attempts
+                for (int at = 0; at < kVonMisesAttempts && (p0 || p1); ++at) {
+                    const uint4 rnd = philox4x32_10(
+                        make_uint4((uint32_t)(j >> 1), t, a.replica,
+                                   ((uint32_t)at << 16) | (kSweep << 1) | (uint32_t)a.c),
+                        a.rk);
+                    if (p0 && von_mises_accept(m0, rnd.x, rnd.y)) {
+                        acc0 = rnd.x;
+                        p0 = false;
+                    }
+                    if (p1 && von_mises_accept(m1, rnd.z, rnd.w)) {
+                        acc1 = rnd.z;
+                        p1 = false;
+                    }
+                }
+                if (!p0) th.x = von_mises_angle(m0, acc0);
+                if (!p1) th.y = von_mises_angle(m1, acc1);
+                sincos_angle<FAST>(th.x, &sy0, &sx0);
+                sincos_angle<FAST>(th.y, &sy1, &sx1);
+                *reinterpret_cast<float2*>(a.own + j) = th;
+            } else if (a.update) {
                 const uint4 rnd = philox4x32_10(
                     make_uint4((uint32_t)(j >> 1), t, a.replica, (kSweep << 1) | (uint32_t)a.c),
                     a.rk);
@@ -685,10 +851,12 @@ int on_rows(const sl_lattice* h, long long cols)
     return R;
 }
 
+// kernel variant: 0 Metropolis, 1 Metropolis with intrinsics, 2 heat-bath
+// (whose draws and fields use the accurate functions only)
 template <int NC>
 cudaError_t launch_on(const sl_lattice* h, OnArgs a, cudaStream_t s)
 {
-    const bool fast = h->fast_math != 0;
+    const int var = a.update && h->update == SL_UPDATE_HEATBATH ? 2 : h->fast_math != 0;
     if (on_stream_ok(h)) {
         const long long cols = NC == 3 ? h->W : h->W / 2;
         a.R = on_rows(h, cols);
@@ -696,15 +864,18 @@ cudaError_t launch_on(const sl_lattice* h, OnArgs a, cudaStream_t s)
         const int grid = grid_for(items, 256);
         if (NC == 3) {
             if (h->d == 2) {
-                if (fast) heis_stream<2, true><<<grid, 256, 0, s>>>(a);
-                else heis_stream<2, false><<<grid, 256, 0, s>>>(a);
+                if (var == 2) heis_stream<2, false, true><<<grid, 256, 0, s>>>(a);
+                else if (var == 1) heis_stream<2, true, false><<<grid, 256, 0, s>>>(a);
+                else heis_stream<2, false, false><<<grid, 256, 0, s>>>(a);
             } else {
-                if (fast) heis_stream<3, true><<<grid, 256, 0, s>>>(a);
-                else heis_stream<3, false><<<grid, 256, 0, s>>>(a);
+                if (var == 2) heis_stream<3, false, true><<<grid, 256, 0, s>>>(a);
+                else if (var == 1) heis_stream<3, true, false><<<grid, 256, 0, s>>>(a);
+                else heis_stream<3, false, false><<<grid, 256, 0, s>>>(a);
             }
         } else {
-            if (fast) xy_stream<true><<<grid, 256, 0, s>>>(a);
-            else xy_stream<false><<<grid, 256, 0, s>>>(a);
+            if (var == 2) xy_stream<false, true><<<grid, 256, 0, s>>>(a);
+            else if (var == 1) xy_stream<true, false><<<grid, 256, 0, s>>>(a);
+            else xy_stream<false, false><<<grid, 256, 0, s>>>(a);
         }
         return cudaGetLastError();
     }
@@ -712,11 +883,13 @@ cudaError_t launch_on(const sl_lattice* h, OnArgs a, cudaStream_t s)
     int grid = (int)(rows < 152LL * 8 ? rows : 152LL * 8);
     if (grid > kMaxBlocks) grid = kMaxBlocks;
     if (h->d == 2) {
-        if (fast) on_generic<NC, 2, true><<<grid, 128, 0, s>>>(a);
-        else on_generic<NC, 2, false><<<grid, 128, 0, s>>>(a);
+        if (var == 2) on_generic<NC, 2, false, true><<<grid, 128, 0, s>>>(a);
+        else if (var == 1) on_generic<NC, 2, true, false><<<grid, 128, 0, s>>>(a);
+        else on_generic<NC, 2, false, false><<<grid, 128, 0, s>>>(a);
     } else {
-        if (fast) on_generic<NC, 3, true><<<grid, 128, 0, s>>>(a);
-        else on_generic<NC, 3, false><<<grid, 128, 0, s>>>(a);
+        if (var == 2) on_generic<NC, 3, false, true><<<grid, 128, 0, s>>>(a);
+        else if (var == 1) on_generic<NC, 3, true, false><<<grid, 128, 0, s>>>(a);
+        else on_generic<NC, 3, false, false><<<grid, 128, 0, s>>>(a);
     }
     return cudaGetLastError();
 }

@@ -1,0 +1,261 @@
+"""GPU parity of the continuous-spin heat-bath rule (Section 2: each spin drawn
+from its conditional law given its neighbours; XY by the Best-Fisher von
+Mises method, Heisenberg by inverting the exponential law of s'.h/|h|)
+against the FP64 oracle.
+
+A heat-bath spin is a smooth function of its local field, so FP32 rounding
+does not stay put as it does for Metropolis proposals: two runs from one
+start separate by about 15% per sweep (the chain's own sensitivity), and a
+trajectory comparison over many sweeps measures that growth, not the kernel.
+The gate is therefore one kernel launch at a time: after every sweep of the
+GPU run the oracle repeats its colour-0 pass from the GPU's state before the
+sweep, and its colour-1 pass from the GPU's colour-0 result, and every
+component must agree within 1e-5, except
+  - near-ties the oracle logs (XY rejection-test margins below 2e-5;
+    Heisenberg sites whose field has |h_z|/|h| < 2e-5, where the sampling
+    basis changes sign), and
+  - sites whose field is weak, |h| < 0.25, where the direction of h itself
+    is ill-conditioned: their tolerance is 1e-5 * 0.25 / |h|.
+Sampler laws are checked on the GPU directly as well (the exact two-spin law),
+and equilibrium energies against the oracle within three standard errors."""
+import math
+
+import numpy as np
+import pytest
+from scipy import stats
+
+import oracle
+from paper_1107_5463_gb300 import inputs
+from tests import exact
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+TIE_TOL = 2e-5
+H_WEAK = 0.25
+
+
+@pytest.fixture(scope="module")
+def sm():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1107_5463_gb300 import spinmc
+    return spinmc
+
+
+def angle_diff(a, b):
+    d = np.abs(np.asarray(a, np.float64) - np.asarray(b, np.float64)) % (2 * math.pi)
+    return np.minimum(d, 2 * math.pi - d)
+
+
+def vectors(n, s):
+    s = np.asarray(s, np.float64)
+    return np.stack([np.cos(s), np.sin(s)], axis=-1) if n == 2 else s
+
+
+def field_norms(n, d, L, before, after, J=1.0, Jb=None):
+    """|h_i| for every site as its update saw it: colour-0 sites from the
+    colour-1 spins before the sweep, colour-1 sites from the colour-0 spins
+    after it (numpy rolls, natural order, x fastest)."""
+    colour = exact.colour_of_site(d, L)
+    mix = np.where(colour[:, None] == 1, vectors(n, before), vectors(n, after))
+    shape = (L,) * d
+    a = mix.reshape(shape[::-1] + (2 if n == 2 else 3,))
+    h = np.zeros_like(a)
+    for mu in range(d):
+        ax = d - 1 - mu
+        jf = np.ones(shape[::-1]) if Jb is None else np.asarray(Jb[mu], np.float64).reshape(
+            shape[::-1])
+        h += jf[..., None] * np.roll(a, -1, axis=ax)                       # +e_mu
+        h += np.roll(jf, 1, axis=ax)[..., None] * np.roll(a, 1, axis=ax)    # -e_mu
+    return np.abs(J) * np.linalg.norm(h.reshape(-1, a.shape[-1]), axis=1)
+
+
+class Steps:
+    """nsw GPU heat-bath sweeps; each colour pass is repeated by the oracle
+    from the GPU's own inputs to that pass and compared site by site."""
+
+    def __init__(self, sm, n, d, L, beta, nsw, seed=3, sweep_seed=11, J=1.0, Jb=None, kernel=0,
+                 renorm=16, fast=0):
+        N = L ** d
+        lat = sm.Lattice(d, L, n=n, J=J, J_bonds=Jb, seed=seed)
+        lat.set_update(sm.SL_UPDATE_HEATBATH)
+        lat.set_option(sm.SL_OPT_FAST_MATH, fast)
+        if kernel:
+            lat.set_option(sm.SL_OPT_KERNEL, kernel)
+        if n == 3:
+            lat.set_option(sm.SL_OPT_RENORM_EVERY, renorm)
+        self.N, self.nsw = N, nsw
+        self.max_err = self.max_err_weak = self.max_dE = 0.0
+        self.ntie = self.nweak = self.compared = 0
+        colour = exact.colour_of_site(d, L)
+        kw = dict(J=J, Jb=Jb, tie_tol=TIE_TOL, ties_cap=1 << 20, heatbath=True)
+        if n == 3:
+            kw["renorm_every"] = renorm
+        run = oracle.xy_sweeps if n == 2 else oracle.heis_sweeps
+        before = lat.get_spins()
+        for t in range(nsw):
+            E, m = lat.sweep_series(beta, 1, sweep_seed)
+            got = lat.get_spins()
+            # colour 0 from the state before the sweep, colour 1 from the
+            # GPU's colour-0 result
+            ref = before.astype(np.float64)
+            _, _, tt0, nt0 = run(d, L, ref, beta, sweep_seed, t, 1, colours=1, series=False, **kw)
+            ref1 = np.where((colour == 0).reshape((-1,) + (1,) * (ref.ndim - 1)),
+                            got.astype(np.float64), before.astype(np.float64))
+            ref1 = np.ascontiguousarray(ref1)
+            Er, mr, tt1, nt1 = run(d, L, ref1, beta, sweep_seed, t, 1, colours=2, **kw)
+            ref = np.where((colour == 0).reshape((-1,) + (1,) * (ref.ndim - 1)), ref, ref1)
+            if n == 2:
+                err = angle_diff(got, ref)
+            else:
+                err = np.abs(got.astype(np.float64) - ref).max(axis=1)
+            nt = nt0 + nt1
+            assert nt <= 1 << 20
+            ok = np.ones(N, bool)
+            ok[tt0[:, 1]] = False
+            ok[tt1[:, 1]] = False
+            self.ntie += nt
+            hn = field_norms(n, d, L, before, got, J, Jb)
+            weak = hn < H_WEAK
+            tol = np.where(weak, TOL * H_WEAK / np.maximum(hn, 1e-30), TOL)
+            bad = ok & (err > tol)
+            assert not bad.any(), ("sweep", t, np.flatnonzero(bad)[:8], err[bad][:8], hn[bad][:8])
+            strong = ok & ~weak
+            self.compared += int(ok.sum())
+            self.nweak += int((ok & weak).sum())
+            if strong.any():
+                self.max_err = max(self.max_err, float(err[strong].max()))
+            if (ok & weak).any():
+                self.max_err_weak = max(self.max_err_weak, float(err[ok & weak].max()))
+            self.max_dE = max(self.max_dE, abs(float(E[0].item()) - float(Er[0])) / N)
+            before = got
+        lat.close()
+
+    def check(self, min_fraction=0.95):
+        assert self.max_err <= TOL
+        assert self.compared >= min_fraction * self.N * self.nsw, ("near-ties", self.ntie)
+        assert self.max_dE < 1e-5
+
+
+@pytest.mark.parametrize("n,d,L,beta", [(2, 2, 16, 1.12), (2, 2, 30, 0.9), (2, 3, 8, 0.5),
+                                        (2, 2, 16, 8.0), (3, 3, 16, 0.693), (3, 2, 32, 1.5),
+                                        (3, 3, 6, 0.3), (3, 3, 8, 5.0), (3, 2, 8, 40.0),
+                                        (2, 2, 2, 1.0), (3, 3, 2, 0.7)])
+def test_heatbath_step_parity(sm, n, d, L, beta):
+    """Every sweep of the first ten, small lattices (L = 2 multigraph, ragged
+    L = 30, 3D) and inverse temperatures from 0.3 to 40 (kappa up to 240,
+    where expm1(2 kappa) overflows FP32)."""
+    Steps(sm, n, d, L, beta, 10).check()
+
+
+@pytest.mark.parametrize("n,d,L,beta", [(3, 3, 64, 0.693), (3, 2, 64, 1.5), (2, 2, 128, 1.12),
+                                        (2, 2, 256, 0.9)])
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_heatbath_streaming_and_generic_kernels(sm, n, d, L, beta, kernel):
+    """Both kernels on sizes the streaming kernels accept; J = -0.8 on the
+    L = 64 lattices checks the coupling sign; fast math does not apply to
+    heat-bath draws."""
+    Steps(sm, n, d, L, beta, 4, kernel=kernel, J=-0.8 if L == 64 else 1.0,
+          fast=1 if L == 128 else 0).check()
+
+
+@pytest.mark.parametrize("n", [2, 3])
+def test_heatbath_float_bonds_and_negative_J(sm, n):
+    d, L = 3, 8
+    Steps(sm, n, d, L, 0.8, 6, J=-0.6, Jb=inputs.float_bonds(d, L, 5)).check()
+
+
+def test_heatbath_renormalising_sweep(sm):
+    """Sweep 15 renormalises at interval 16 after the draw, as the oracle does."""
+    d, L = 3, 8
+    lat = sm.Lattice(d, L, n=3, seed=4)
+    lat.set_update(sm.SL_UPDATE_HEATBATH)
+    lat.set_state(15)
+    before = lat.get_spins()
+    lat.sweep(0.693, 1, 7)
+    got = lat.get_spins().astype(np.float64)
+    lat.close()
+    ref = before.astype(np.float64)
+    oracle.heis_sweeps(d, L, ref, 0.693, 7, 15, 1, renorm_every=16, heatbath=True, series=False)
+    assert np.abs(np.linalg.norm(got, axis=1) - 1).max() < 1e-6
+    assert np.abs(got - ref).max() < 1e-4
+
+
+@pytest.mark.parametrize("n", [2, 3])
+def test_heatbath_two_spin_law_on_gpu(sm, n):
+    """The single-bond lattice on the GPU: the bond variable s_0 . s_1 = -E
+    follows the exact two-spin law (mean within 3 standard errors, KS test);
+    the other sites see h = 0 and are redrawn uniformly."""
+    d, L, beta = 2, 4, 1.4
+    jb = inputs.two_spin_bonds(d, L, 0, 0).astype(np.float32)
+    lat = sm.Lattice(d, L, n=n, J_bonds=jb, seed=5)
+    lat.set_update(sm.SL_UPDATE_HEATBATH)
+    E, _ = lat.sweep_series(beta, 40_000, 6)
+    lat.close()
+    x = -E.cpu().numpy()[10:]
+    mean, err = exact.binned_mean(x, 50)
+    assert abs(mean - exact.two_spin_mean(n, beta)) < 3 * err, (mean, err)
+    assert stats.kstest(x[::7][:3000], exact.two_spin_cdf(n, beta)).pvalue > 1e-3
+
+
+@pytest.mark.parametrize("n,d,L,beta", [(2, 2, 32, 1.12), (3, 3, 12, 0.693)])
+def test_heatbath_equilibrium_energy_agrees(sm, n, d, L, beta):
+    """<E>/N of a GPU heat-bath chain and an independent oracle heat-bath chain
+    agree within three combined standard errors."""
+    nsw, burn = 3000, 300
+    lat = sm.Lattice(d, L, n=n, seed=12)
+    lat.set_update(sm.SL_UPDATE_HEATBATH)
+    E, _ = lat.sweep_series(beta, nsw, 13)
+    Eg = E.cpu().numpy()[burn:] / L ** d
+    lat.close()
+    if n == 2:
+        s = oracle.xy_init(d, L, 99)
+        Er, _, _, _ = oracle.xy_sweeps(d, L, s, beta, 98, 0, nsw, heatbath=True)
+    else:
+        s = oracle.heis_init(d, L, 99)
+        Er, _, _, _ = oracle.heis_sweeps(d, L, s, beta, 98, 0, nsw, heatbath=True)
+    mg, eg = exact.binned_mean(Eg, 20)
+    mr, er = exact.binned_mean(Er[burn:] / L ** d, 20)
+    assert abs(mg - mr) < 3 * math.hypot(eg, er), (mg, mr, eg, er)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("n,d,L,beta", [(3, 3, 256, 0.693), (2, 2, 4096, 1.12)])
+def test_heatbath_full_size_steps(sm, n, d, L, beta):
+    """The paper-shaped workloads at full size, first three sweeps, each
+    repeated by the oracle from the GPU's state."""
+    p = Steps(sm, n, d, L, beta, 3, seed=inputs.DEFAULT_SEED)
+    p.check(min_fraction=0.99)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("n,d,L,beta", [(3, 3, 64, 0.693), (2, 2, 256, 1.12)])
+def test_heatbath_trajectory_drift_report(sm, n, d, L, beta, capsys):
+    """Two chains from one FP32 start, the GPU's and the oracle's, compared
+    after each of 10 sweeps: the median and largest component differences
+    (printed) grow with the chain's sensitivity; the energies per site stay
+    within 1e-4."""
+    s32 = (oracle.xy_init(d, L, 3) if n == 2 else oracle.heis_init(d, L, 3)).astype(np.float32)
+    lat = sm.Lattice(d, L, n=n, seed=3)
+    lat.set_update(sm.SL_UPDATE_HEATBATH)
+    lat.set_spins(s32)
+    ref = s32.astype(np.float64)
+    med, mx = [], []
+    for t in range(10):
+        E, _ = lat.sweep_series(beta, 1, 11)
+        got = lat.get_spins()
+        if n == 2:
+            Er, _, _, _ = oracle.xy_sweeps(d, L, ref, beta, 11, t, 1, heatbath=True)
+            err = angle_diff(got, ref)
+        else:
+            Er, _, _, _ = oracle.heis_sweeps(d, L, ref, beta, 11, t, 1, heatbath=True)
+            err = np.abs(got.astype(np.float64) - ref).max(axis=1)
+        med.append(float(np.median(err)))
+        mx.append(float(err.max()))
+        assert abs(float(E[0].item()) - float(Er[0])) / L ** d < 1e-4
+    lat.close()
+    with capsys.disabled():
+        print("\nheat-bath drift n=%d d=%d L=%d beta=%g: median %s, max %s" % (
+            n, d, L, beta, " ".join("%.1e" % v for v in med), " ".join("%.1e" % v for v in mx)))
+    assert med[-1] < 1e-5

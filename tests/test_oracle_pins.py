@@ -495,6 +495,24 @@ def test_continuous_heatbath_at_beta_zero_is_uniform():
                         stats.uniform(-math.pi, 2 * math.pi).cdf).pvalue > 1e-3
 
 
+@pytest.mark.parametrize("n", [2, 3])
+def test_continuous_heatbath_colour_passes_compose_to_sweeps(n):
+    """The pass of colour 0 followed by the pass of colour 1 (same sweep
+    index) is exactly one whole sweep, and a pass touches only its colour."""
+    d, L, beta = 3, 4, 0.9
+    init = oracle.xy_init if n == 2 else oracle.heis_init
+    run = oracle.xy_sweeps if n == 2 else oracle.heis_sweeps
+    a, b = init(d, L, 3), init(d, L, 3)
+    run(d, L, a, beta, 5, 7, 1, heatbath=True, series=False)
+    start = b.copy()
+    run(d, L, b, beta, 5, 7, 1, heatbath=True, series=False, colours=1)
+    colour = exact.colour_of_site(d, L)
+    np.testing.assert_array_equal(b[colour == 1], start[colour == 1])
+    assert (b[colour == 0] != start[colour == 0]).any()
+    run(d, L, b, beta, 5, 7, 1, heatbath=True, series=False, colours=2)
+    np.testing.assert_array_equal(a, b)
+
+
 @pytest.mark.parametrize("n,d,L,beta", [(2, 2, 8, 1.12), (3, 3, 4, 0.693)])
 def test_continuous_heatbath_and_metropolis_agree_in_equilibrium(n, d, L, beta):
     """Both rules leave the Boltzmann law invariant: their mean energies on
