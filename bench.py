@@ -317,7 +317,8 @@ def launch_shape(wl):
         return 2, "heis_stream<%d,%d,%d>" % (d, wl.get("fast", 0), hb)
     if wl["storage"] == "angle":
         return 2, "xy_stream<0,%d>" % hb
-    return 2, "i8_stream<%d,0,0,%d>" % (d, 1 if wl.get("update") == 1 else 0)
+    # two colour passes and the one-block kernel that closes the measuring pass
+    return 3, "i8_stream<%d,0,0,%d,0/1>" % (d, 1 if wl.get("update") == 1 else 0)
 
 
 def configure(spinmc, lat, wl):

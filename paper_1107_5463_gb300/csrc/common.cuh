@@ -134,4 +134,45 @@ __device__ __forceinline__ void finish_pass(Ctrl* ctrl, Partial* partials, const
     }
 }
 
+// Deferred finishing.  A measuring pass of thousands of short blocks loses
+// several percent of its time if every block ends with the fence and the
+// arrival atomic above while its SM slot waits.  Instead each block stores
+// its partial (no fence, no atomic) and a one-block kernel launched right
+// after the pass on the same stream adds them; the kernel boundary orders the
+// stores before the loads.  Thread k adds blocks k, k + kFinishThreads, ...
+// in order and the block tree-sums the threads: a fixed order for a given
+// grid, so FP64 totals stay reproducible.
+constexpr int kFinishThreads = 512;
+
+__device__ __forceinline__ void store_partial(Partial* partials, const Partial& mine)
+{
+    if (threadIdx.x == 0) partials[blockIdx.x] = mine;
+}
+
+// Total of the first nblocks partials (FP: also the four double members),
+// valid in thread 0.
+template <bool FP>
+__device__ __forceinline__ Partial sum_partials(const Partial* partials, unsigned nblocks)
+{
+    __shared__ long long red_i[32];
+    __shared__ double red_f[32];
+    long long i0 = 0, i1 = 0;
+    double f[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll 4
+    for (unsigned b = threadIdx.x; b < nblocks; b += blockDim.x) {
+        i0 += partials[b].i0;
+        i1 += partials[b].i1;
+        if (FP) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) f[k] += partials[b].f[k];
+        }
+    }
+    Partial tot;
+    tot.i0 = block_sum(i0, red_i);
+    tot.i1 = block_sum(i1, red_i);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) tot.f[k] = FP ? block_sum(f[k], red_f) : 0.0;
+    return tot;
+}
+
 }  // namespace spinmc

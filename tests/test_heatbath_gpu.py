@@ -57,9 +57,19 @@ def test_heatbath_long_run_2d_L64(sm):
     run_both(sm, 2, 64, BETA_C, 2000, seed=inputs.DEFAULT_SEED, sweep_seed=inputs.DEFAULT_SEED)
 
 
-def test_heatbath_only_for_ising_bytes(sm):
-    for d, L, n, storage in ((2, 64, 1, sm.SL_STORE_BITS), (2, 16, 2, None), (2, 16, 3, None)):
-        lat = sm.Lattice(d, L, n=n, storage=storage)
-        with pytest.raises(sm.SpinMCError):
-            lat.set_option(sm.SL_OPT_UPDATE, 1)
+def test_heatbath_storage_rules(sm):
+    """Bit storage and multi-hit sweeps have no heat-bath rule; byte, angle and
+    vector storage accept it."""
+    lat = sm.Lattice(2, 64, n=1, storage=sm.SL_STORE_BITS)
+    with pytest.raises(sm.SpinMCError):
+        lat.set_option(sm.SL_OPT_UPDATE, sm.SL_UPDATE_HEATBATH)
+    lat.close()
+    lat = sm.Lattice(2, 64, n=1)
+    lat.set_option(sm.SL_OPT_MULTIHIT, 4)
+    with pytest.raises(sm.SpinMCError):
+        lat.set_option(sm.SL_OPT_UPDATE, sm.SL_UPDATE_HEATBATH)
+    lat.close()
+    for n in (1, 2, 3):
+        lat = sm.Lattice(2, 16, n=n)
+        lat.set_option(sm.SL_OPT_UPDATE, sm.SL_UPDATE_HEATBATH)
         lat.close()
