@@ -310,15 +310,16 @@ def launch_shape(wl):
         return 5, "sw_local<%d> .. sw_flip (Swendsen-Wang)" % d
     if wl.get("multihit"):
         return 3, "ising_tile_kernel<%d,%d>" % (d, wl["tile"])
+    # the streaming paths: two colour passes and the one-block kernel that
+    # adds the measuring pass's partials
     if wl["storage"] == "bits":
-        return 2, "bits_stream<%d,0>" % d
+        return 3, "bits_stream<%d,0,0/1>" % d
     hb = 1 if wl.get("update") == 1 else 0
     if wl["storage"] == "vec":
-        return 2, "heis_stream<%d,%d,%d>" % (d, wl.get("fast", 0), hb)
+        return 3, "heis_stream<%d,%d,%d,0/1>" % (d, wl.get("fast", 0), hb)
     if wl["storage"] == "angle":
-        return 2, "xy_stream<0,%d>" % hb
-    # two colour passes and the one-block kernel that closes the measuring pass
-    return 3, "i8_stream<%d,0,0,%d,0/1>" % (d, 1 if wl.get("update") == 1 else 0)
+        return 3, "xy_stream<0,%d,0/1>" % hb
+    return 3, "i8_stream<%d,0,0,%d,0/1>" % (d, hb)
 
 
 def configure(spinmc, lat, wl):

@@ -56,7 +56,9 @@ __device__ __forceinline__ void fadd(uint32_t a, uint32_t b, uint32_t c, uint32_
     k = (a & b) | (c & (a ^ b));
 }
 
-template <int D, int JNEG>
+// MEAS: the measuring (colour-1) pass, which stores its block partials for
+// bits_finish_kernel; the other pass is compiled without the counters.
+template <int D, int JNEG, bool MEAS>
 __global__ void __launch_bounds__(128) bits_stream(const BitArgs a)
 {
     __shared__ long long red[32];
@@ -155,7 +157,7 @@ __global__ void __launch_bounds__(128) bits_stream(const BitArgs a)
             }
             const uint32_t An = A ^ flip;
             if (a.update) a.own[rr * WW + w] = An;
-            if (a.measure) {
+            if (MEAS) {
                 i_na += __popc(b0) + 2 * __popc(b1) + 4 * __popc(b2);
                 i_flip += __popc(flip);
                 i_flipna += __popc(flip & b0) + 2 * __popc(flip & b1) + 4 * __popc(flip & b2);
@@ -164,7 +166,7 @@ __global__ void __launch_bounds__(128) bits_stream(const BitArgs a)
             prev = cur;
             cur = next;
         }
-        if (a.measure) {
+        if (MEAS) {
             s_na += i_na;
             s_flip += i_flip;
             s_flipna += i_flipna;
@@ -172,7 +174,7 @@ __global__ void __launch_bounds__(128) bits_stream(const BitArgs a)
             nsite += 32 * R;
         }
     }
-    if (!a.measure) return;
+    if (!MEAS) return;
     const long long na_after = (long long)s_na + 2 * D * (long long)s_flip - 2 * (long long)s_flipna;
     long long bond = (long long)(2 * D) * (long long)nsite - 2 * na_after;
     if (JNEG) bond = -bond;
@@ -180,7 +182,16 @@ __global__ void __launch_bounds__(128) bits_stream(const BitArgs a)
     mine.i0 = block_sum(bond, red);
     mine.i1 = block_sum((long long)down, red);
     mine.f[0] = mine.f[1] = mine.f[2] = mine.f[3] = 0.0;
-    finish_pass(a.ctrl, a.partials, mine, [&](const Partial& tot) { bits_finish(a, tot); });
+    store_partial(a.partials, mine);
+}
+
+// Adds the partials a measuring pass of nblocks blocks stored and closes the
+// pass (one block of kFinishThreads).
+__global__ void __launch_bounds__(kFinishThreads) bits_finish_kernel(const BitArgs a,
+                                                                     unsigned nblocks)
+{
+    const Partial tot = sum_partials<false>(a.partials, nblocks);
+    if (threadIdx.x == 0) bits_finish(a, tot);
 }
 
 __global__ void bits_init_kernel(uint32_t* s0, uint32_t* s1, long long nwords, uint32_t replica,
@@ -285,12 +296,23 @@ cudaError_t launch(const sl_lattice* h, const BitArgs& a, cudaStream_t s)
     const long long items = (long long)(h->W / 32) * (h->d == 3 ? h->L : 1) * (h->L / a.R);
     const int grid = grid_for(items, 128);
     const bool jneg = a.tab.sigma_neg != 0;
+#define SPINMC_BITS(D, N)                                                     \
+    do {                                                                      \
+        if (a.measure) bits_stream<D, N, true><<<grid, 128, 0, s>>>(a);        \
+        else bits_stream<D, N, false><<<grid, 128, 0, s>>>(a);                 \
+    } while (0)
     if (h->d == 2) {
-        if (jneg) bits_stream<2, 1><<<grid, 128, 0, s>>>(a);
-        else bits_stream<2, 0><<<grid, 128, 0, s>>>(a);
+        if (jneg) SPINMC_BITS(2, 1);
+        else SPINMC_BITS(2, 0);
     } else {
-        if (jneg) bits_stream<3, 1><<<grid, 128, 0, s>>>(a);
-        else bits_stream<3, 0><<<grid, 128, 0, s>>>(a);
+        if (jneg) SPINMC_BITS(3, 1);
+        else SPINMC_BITS(3, 0);
+    }
+#undef SPINMC_BITS
+    if (a.measure) {
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        bits_finish_kernel<<<1, kFinishThreads, 0, s>>>(a, (unsigned)grid);
     }
     return cudaGetLastError();
 }

@@ -410,7 +410,9 @@ __device__ __forceinline__ V3 shfl3_down(V3 v)
     return r;
 }
 
-template <int D, bool FAST, bool HB>
+// MEAS: the measuring (colour-1) pass, which stores its block partials for
+// on_finish_kernel; the other pass is compiled without the sums.
+template <int D, bool FAST, bool HB, bool MEAS>
 __global__ void __launch_bounds__(256, D == 2 && !HB ? 4 : 3) heis_stream(const OnArgs a)
 {
     __shared__ double red[32];
@@ -546,7 +548,7 @@ __global__ void __launch_bounds__(256, D == 2 && !HB ? 4 : 3) heis_stream(const 
                     sz_[j] = s.z;
                 }
             }
-            if (a.measure) {
+            if (MEAS) {
                 pe -= s.x * hx + s.y * hy + s.z * hz;
                 pmx += s.x + cur.x;
                 pmy += s.y + cur.y;
@@ -556,14 +558,14 @@ __global__ void __launch_bounds__(256, D == 2 && !HB ? 4 : 3) heis_stream(const 
             cur = nxt;
         }
     }
-    if (!a.measure) return;
+    if (!MEAS) return;
     Partial mine;
     mine.i0 = mine.i1 = 0;
     mine.f[0] = block_sum((double)pe, red);
     mine.f[1] = block_sum((double)pmx, red);
     mine.f[2] = block_sum((double)pmy, red);
     mine.f[3] = block_sum((double)pmz, red);
-    finish_pass(a.ctrl, a.partials, mine, [&](const Partial& tot) { on_finish(a, tot); });
+    store_partial(a.partials, mine);
 }
 
 struct CS2 {
@@ -582,7 +584,7 @@ __device__ __forceinline__ CS2 cs_pair(const float* p, long long i)
 
 // XY, 2D: each thread owns the column pair (2q, 2q+1), whose sites share one
 // Philox block (group j >> 1).
-template <bool FAST, bool HB>
+template <bool FAST, bool HB, bool MEAS>
 __global__ void __launch_bounds__(256) xy_stream(const OnArgs a)
 {
     __shared__ double red[32];
@@ -711,7 +713,7 @@ __global__ void __launch_bounds__(256) xy_stream(const OnArgs a)
                 }
                 if (ch) *reinterpret_cast<float2*>(a.own + j) = th;
             }
-            if (a.measure) {
+            if (MEAS) {
                 pe -= sx0 * hx0 + sy0 * hy0 + sx1 * hx1 + sy1 * hy1;
                 pmx += sx0 + sx1 + cur.c0 + cur.c1;
                 pmy += sy0 + sy1 + cur.s0 + cur.s1;
@@ -720,14 +722,23 @@ __global__ void __launch_bounds__(256) xy_stream(const OnArgs a)
             cur = nxt;
         }
     }
-    if (!a.measure) return;
+    if (!MEAS) return;
     Partial mine;
     mine.i0 = mine.i1 = 0;
     mine.f[0] = block_sum((double)pe, red);
     mine.f[1] = block_sum((double)pmx, red);
     mine.f[2] = block_sum((double)pmy, red);
     mine.f[3] = 0.0;
-    finish_pass(a.ctrl, a.partials, mine, [&](const Partial& tot) { on_finish(a, tot); });
+    store_partial(a.partials, mine);
+}
+
+// Adds the partials a streaming measuring pass of nblocks blocks stored and
+// closes the pass (one block of kFinishThreads; FP64 in a fixed order).
+__global__ void __launch_bounds__(kFinishThreads) on_finish_kernel(const OnArgs a,
+                                                                   unsigned nblocks)
+{
+    const Partial tot = sum_partials<true>(a.partials, nblocks);
+    if (threadIdx.x == 0) on_finish(a, tot);
 }
 
 template <int NC>
@@ -862,20 +873,31 @@ cudaError_t launch_on(const sl_lattice* h, OnArgs a, cudaStream_t s)
         a.R = on_rows(h, cols);
         const long long items = cols * (h->d == 3 ? h->L : 1) * (h->L / a.R);
         const int grid = grid_for(items, 256);
+#define SPINMC_ON(K, ...)                                                      \
+    do {                                                                       \
+        if (a.measure) K<__VA_ARGS__, true><<<grid, 256, 0, s>>>(a);          \
+        else K<__VA_ARGS__, false><<<grid, 256, 0, s>>>(a);                   \
+    } while (0)
         if (NC == 3) {
             if (h->d == 2) {
-                if (var == 2) heis_stream<2, false, true><<<grid, 256, 0, s>>>(a);
-                else if (var == 1) heis_stream<2, true, false><<<grid, 256, 0, s>>>(a);
-                else heis_stream<2, false, false><<<grid, 256, 0, s>>>(a);
+                if (var == 2) SPINMC_ON(heis_stream, 2, false, true);
+                else if (var == 1) SPINMC_ON(heis_stream, 2, true, false);
+                else SPINMC_ON(heis_stream, 2, false, false);
             } else {
-                if (var == 2) heis_stream<3, false, true><<<grid, 256, 0, s>>>(a);
-                else if (var == 1) heis_stream<3, true, false><<<grid, 256, 0, s>>>(a);
-                else heis_stream<3, false, false><<<grid, 256, 0, s>>>(a);
+                if (var == 2) SPINMC_ON(heis_stream, 3, false, true);
+                else if (var == 1) SPINMC_ON(heis_stream, 3, true, false);
+                else SPINMC_ON(heis_stream, 3, false, false);
             }
         } else {
-            if (var == 2) xy_stream<false, true><<<grid, 256, 0, s>>>(a);
-            else if (var == 1) xy_stream<true, false><<<grid, 256, 0, s>>>(a);
-            else xy_stream<false, false><<<grid, 256, 0, s>>>(a);
+            if (var == 2) SPINMC_ON(xy_stream, false, true);
+            else if (var == 1) SPINMC_ON(xy_stream, true, false);
+            else SPINMC_ON(xy_stream, false, false);
+        }
+#undef SPINMC_ON
+        if (a.measure) {
+            const cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+            on_finish_kernel<<<1, kFinishThreads, 0, s>>>(a, (unsigned)grid);
         }
         return cudaGetLastError();
     }
