@@ -549,12 +549,13 @@ bool stream_ok(const sl_lattice* h)
 int pick_rows(const sl_lattice* h)
 {
     if (h->rows > 0) return h->rows;
-    // measured on GB300: 16 rows per thread for 2D, 32 for 3D (the 3D pass
-    // keeps two more row windows per thread); fewer rows only when the grid
-    // would not fill the GPU
+    // measured on GB300: 16 rows per thread for 2D (1040 flips/ns at L =
+    // 16384, against 1027 for 8 and 999 for 32), 8 for 3D (807 at L = 512,
+    // against 803 for 16 and 795 for 32: more, shorter items balance the SMs
+    // better); fewer rows only when the grid would not fill the GPU
     const long long W16 = h->W / 16;
     const long long cross = h->d == 3 ? h->L : 1;
-    int R = h->d == 3 ? 32 : 16;
+    int R = h->d == 3 ? 8 : 16;
     while (R > 1 && (h->L % R != 0 || W16 * cross * (h->L / R) < 152LL * 512)) R >>= 1;
     return R;
 }
