@@ -40,6 +40,9 @@ def lib():
         L.orc_ising_sweeps.argtypes = [_int, _int, _dbl, _vp, _dbl, _u64, _u32, _i64, _i64,
                                        _i8p, _vp, _vp]
         L.orc_ising_heatbath_sweeps.argtypes = L.orc_ising_sweeps.argtypes
+        L.orc_ising_site_update.argtypes = [_int, _int, _dbl, _vp, _dbl, _u64, _u32, _i64, _int,
+                                            _i8p, _i64]
+        L.orc_ising_site_update.restype = _int
         L.orc_ising_multihit_sweeps.argtypes = [_int, _int, _int, _int, _dbl, _vp, _dbl, _u64,
                                                 _u32, _i64, _i64, _i8p, _vp, _vp]
         L.orc_ising_sw_sweeps.argtypes = [_int, _int, _dbl, _dbl, _u64, _u32, _i64, _i64, _i8p,
@@ -157,6 +160,17 @@ def ising_heatbath_sweeps(d, L, s, beta, seed, t0, nsweeps, J=1.0, Jb=None, repl
     lib().orc_ising_heatbath_sweeps(d, L, J, _ptr(jb), beta, seed, replica, t0, nsweeps, s,
                                     _ptr(E), _ptr(m))
     return E, m
+
+
+def ising_site_updates(d, L, s, sites, beta, seed, t, J=1.0, Jb=None, replica=0,
+                       heatbath=False):
+    """New spins of the given sites in sweep t, each from the configuration s
+    (natural order, the neighbour values its colour's update sees)."""
+    jb = _bonds_i8(Jb, d, L)
+    assert s.dtype == np.int8 and s.flags.c_contiguous
+    f = lib().orc_ising_site_update
+    return np.array([f(d, L, J, _ptr(jb), beta, seed, replica, t, int(heatbath), s, int(i))
+                     for i in sites], np.int8)
 
 
 def ising_multihit_sweeps(d, L, T, k, s, beta, seed, t0, nsweeps, J=1.0, Jb=None, replica=0,

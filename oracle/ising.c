@@ -154,6 +154,25 @@ static void ising_sweeps_rule(int d, int L, double J, const int8_t* Jb, double b
     }
 }
 
+int orc_ising_site_update(int d, int L, double J, const int8_t* Jb, double beta, uint64_t seed,
+                          uint32_t replica, int64_t t, int heatbath, const int8_t* s, int64_t i)
+{
+    orc_geom g = orc_make_geom(d, L);
+    const uint32_t key[2] = {orc_key_lo(seed), orc_key_hi(seed)};
+    int xyz[3];
+    orc_coords(&g, i, xyz);
+    const int c = orc_colour(&g, i);
+    const int64_t j = i >> 1;
+    uint32_t ctr[4] = {(uint32_t)(j >> 2), (uint32_t)t, replica, (uint32_t)(ORC_SWEEP << 1 | c)};
+    uint32_t out[4];
+    orc_philox4x32_10(ctr, key, out);
+    if (heatbath) {
+        double a = 2.0 * J * (double)ising_field(&g, Jb, s, xyz, i);
+        return (double)out[j & 3] < 4294967296.0 / (1.0 + exp(-beta * a)) ? 1 : -1;
+    }
+    return ising_accept(&g, J, Jb, beta, s, xyz, i, out[j & 3]) ? -s[i] : s[i];
+}
+
 void orc_ising_multihit_sweeps(int d, int L, int T, int k, double J, const int8_t* Jb,
                                double beta, uint64_t seed, uint32_t replica, int64_t t0,
                                int64_t nsweeps, int8_t* s, double* E_out, double* absm_out)

@@ -72,6 +72,15 @@ void orc_ising_heatbath_sweeps(int d, int L, double J, const int8_t* Jb, double 
                                uint64_t seed, uint32_t replica, int64_t t0, int64_t nsweeps,
                                int8_t* s, double* E_out, double* absm_out);
 
+/* The update of the single site i in sweep t (Metropolis, or heat-bath if
+ * heatbath): its new spin from the configuration s, which holds the values the
+ * site's neighbours have when its colour is updated (the other colour before
+ * the sweep for colour 0, after the colour-0 pass for colour 1; sites of one
+ * colour do not interact).  Checks sampled sites of lattices too large to
+ * sweep on the CPU. */
+int orc_ising_site_update(int d, int L, double J, const int8_t* Jb, double beta, uint64_t seed,
+                          uint32_t replica, int64_t t, int heatbath, const int8_t* s, int64_t i);
+
 /* k-fold multi-hit sweeps in big tiles (Section 2: the lattice is cut into
  * big tiles of side T forming a checkerboard; for tile colour 0 and then 1,
  * every tile of that colour receives k updates of all its spins, each an

@@ -43,6 +43,22 @@ def roll_energy(s, d, L, J=1.0, Jb=None):
     return -J * e
 
 
+def chunked_energy(s, d, L, rows=512):
+    """roll_energy for uniform J = 1 on lattices too large for whole-array
+    temporaries: slabs of `rows` rows (2D) or planes (3D) with their wrapped
+    successor, int64 sums."""
+    a = s.reshape((L,) * d)
+    e = 0
+    for y0 in range(0, L, rows):
+        y1 = min(y0 + rows, L)
+        blk = a[y0:y1]
+        nxt = np.concatenate([a[y0 + 1:y1], a[(y1) % L][None]], axis=0)
+        e += int((blk * nxt).sum(dtype=np.int64))                          # +e along the slow axis
+        for ax in range(1, d):
+            e += int((blk * np.roll(blk, -1, axis=ax)).sum(dtype=np.int64))
+    return -e
+
+
 def all_states(N):
     """All 2^N Ising configurations, shape (2^N, N), int8."""
     idx = np.arange(2 ** N, dtype=np.int64)[:, None]

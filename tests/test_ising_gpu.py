@@ -114,6 +114,58 @@ def test_full_size_first_sweeps_bit_exact(sm, d, L, beta):
     assert_same(gpu_run(sm, d, L, beta, seed, seed + 1, 5, bits=True), ref)
 
 
+def sample_sites(d, L, colour, c, n, rng):
+    """n random sites of colour c plus every site of colour c on the lattice's
+    first and last two columns of the first and last rows (and planes)."""
+    N = L ** d
+    pick = rng.integers(0, N, 4 * n, dtype=np.int64)
+    pick = pick[colour(pick) == c][:n]
+    edge = [0, 1, L - 2, L - 1]
+    cand = np.array([x + L * y + (L * L * z if d == 3 else 0)
+                     for x in edge for y in edge for z in (edge if d == 3 else [0])],
+                    np.int64)
+    return np.unique(np.concatenate([pick, cand[colour(cand) == c]]))
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("d,L,bits", [(2, 63232, False), (2, 63230, False), (3, 1568, False),
+                                      (2, 63232, True)])
+def test_maximum_size_sampled_sites(sm, d, L, bits):
+    """Lattices at the library's limit of 4e9 sites (63232^2, the ragged
+    63230^2 on the per-site kernel, 1568^3; bytes and bits): one sweep in the
+    bench's launch configuration from the Philox start; 8192 sampled sites of
+    each colour, every lattice corner among them, against the oracle's
+    single-site update from the configuration that colour's pass sees; the
+    swept |m| against the final state, and in 2D bytes the energy too."""
+    seed, sweep_seed, t = inputs.DEFAULT_SEED, 77, 0
+    lat = sm.Lattice(d, L, n=1, seed=seed, storage=sm.SL_STORE_BITS if bits else None)
+    before = lat.get_spins()
+    E, m = lat.sweep_series(BETA_C if d == 2 else inputs.BETA_3D_ISING, 1, sweep_seed)
+    beta = BETA_C if d == 2 else inputs.BETA_3D_ISING
+    after = lat.get_spins()
+    lat.close()
+    N = L ** d
+
+    def colour(i):
+        x, y, z = i % L, (i // L) % L, i // (L * L)
+        return (x + y + (z if d == 3 else 0)) & 1
+
+    rng = np.random.default_rng(5)
+    s0 = sample_sites(d, L, colour, 0, 8192, rng)
+    s1 = sample_sites(d, L, colour, 1, 8192, rng)
+    ref0 = oracle.ising_site_updates(d, L, before, s0, beta, sweep_seed, t)
+    np.testing.assert_array_equal(after[s0], ref0)
+    # colour 1 sees the colour-0 result and its own value before the sweep
+    got1 = after[s1].copy()
+    assert abs(int(after.sum(dtype=np.int64))) / N == pytest.approx(float(m[0].item()), abs=0)
+    if d == 2 and not bits:
+        from tests.exact import chunked_energy
+        assert chunked_energy(after, d, L) == float(E[0].item())
+    after[s1] = before[s1]
+    ref1 = oracle.ising_site_updates(d, L, after, s1, beta, sweep_seed, t)
+    np.testing.assert_array_equal(got1, ref1)
+
+
 @pytest.mark.parametrize("d,L", [(2, 64), (2, 192), (2, 1024), (3, 64), (3, 128)])
 @pytest.mark.parametrize("beta,J", [(BETA_C, 1.0), (0.3, -0.7)])
 def test_bit_storage_parity(sm, d, L, beta, J):

@@ -95,6 +95,14 @@ def test_ising_measure_matches_roll_energy(d, L):
         assert M == s.sum()
 
 
+@pytest.mark.parametrize("d,L,rows", [(2, 10, 3), (2, 8, 512), (3, 6, 4), (3, 4, 1)])
+def test_chunked_energy_matches_roll_energy(d, L, rows):
+    """The slab-wise energy used at the largest sizes equals the whole-array
+    roll energy."""
+    s = inputs.ising_spins(d, L, 7)
+    assert exact.chunked_energy(s, d, L, rows) == exact.roll_energy(s, d, L)
+
+
 @pytest.mark.parametrize("d", [2, 3])
 def test_ising_measure_special_states(d):
     L = 4
@@ -530,6 +538,27 @@ def test_continuous_heatbath_and_metropolis_agree_in_equilibrium(n, d, L, beta):
     (m0, e0), (m1, e1) = res
     assert abs(m0 - m1) < 3 * math.hypot(e0, e1), res
     assert max(e0, e1) < 1e-2
+
+
+@pytest.mark.parametrize("d,L,heatbath,J", [(2, 6, False, 1.0), (3, 4, False, -0.7),
+                                             (2, 8, True, 1.0), (3, 4, True, 1.3)])
+def test_site_updates_reproduce_a_sweep(d, L, heatbath, J):
+    """The single-site update, fed the configuration each colour's pass sees
+    (colour 0: the state before the sweep; colour 1: after the colour-0
+    pass), gives every site of one oracle sweep, on random +-1 couplings."""
+    beta, seed, t = 0.4, 21, 5
+    jb = inputs.ising_bonds(d, L, 3)
+    before = inputs.ising_spins(d, L, 4)
+    after = before.copy()
+    sweep = oracle.ising_heatbath_sweeps if heatbath else oracle.ising_sweeps
+    sweep(d, L, after, beta, seed, t, 1, J=J, Jb=jb, series=False)
+    colour = exact.colour_of_site(d, L)
+    mid = np.where(colour == 0, after, before).astype(np.int8)
+    for c, state in ((0, before), (1, mid)):
+        sites = np.flatnonzero(colour == c)
+        got = oracle.ising_site_updates(d, L, np.ascontiguousarray(state), sites, beta, seed, t,
+                                        J=J, Jb=jb, heatbath=heatbath)
+        np.testing.assert_array_equal(got, after[sites])
 
 
 # ------------------------------------------------------------ multi-hit --
