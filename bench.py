@@ -316,7 +316,8 @@ def launch_shape(wl):
         return 3, "bits_stream<%d,0,0/1>" % d
     hb = 1 if wl.get("update") == 1 else 0
     if wl["storage"] == "vec":
-        return 3, "heis_stream<%d,%d,%d,0/1>" % (d, wl.get("fast", 0), hb)
+        kern = "heis_pair" if (wl["L"] // 2) % 64 == 0 else "heis_stream"
+        return 3, "%s<%d,%d,%d,0/1>" % (kern, d, wl.get("fast", 0), hb)
     if wl["storage"] == "angle":
         return 3, "xy_stream<0,%d,0/1>" % hb
     return 3, "i8_stream<%d,0,0,%d,0/1>" % (d, hb)

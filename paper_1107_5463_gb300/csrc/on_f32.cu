@@ -376,12 +376,13 @@ __global__ void __launch_bounds__(128) on_generic(const OnArgs a)
 // ------------------------------------------------------------ streaming ----
 //
 // Uniform coupling, W % 32 == 0 (Heisenberg) or W % 64 == 0 (XY): a warp owns
-// 32 consecutive columns of one row and marches along the last axis (y in 2D,
-// z in 3D) through R rows, keeping the other colour's rows behind, at and
-// ahead of the current one in registers (for XY as cos/sin, computed once per
-// value).  The x neighbours come from the adjacent lane by a shuffle (the two
-// warp-edge lanes load theirs).  Loads for the next row are issued one row
-// ahead.
+// 32 consecutive columns (heis_stream) or column pairs (heis_pair when
+// W % 64 == 0, xy_stream) of one row and marches along the last axis (y in
+// 2D, z in 3D) through R rows, keeping the other colour's rows behind, at
+// and ahead of the current one in registers (for XY as cos/sin, computed once
+// per value).  The x neighbours come from the adjacent lane by a shuffle (the
+// two warp-edge lanes load theirs).  Loads for the next row are issued one
+// row ahead.
 
 __device__ __forceinline__ V3 ld3(const float* p, long long H, long long i)
 {
@@ -553,6 +554,209 @@ __global__ void __launch_bounds__(256, D == 2 && !HB ? 4 : 3) heis_stream(const 
                 pmx += s.x + cur.x;
                 pmy += s.y + cur.y;
                 pmz += s.z + cur.z;
+            }
+            prev = cur;
+            cur = nxt;
+        }
+    }
+    if (!MEAS) return;
+    Partial mine;
+    mine.i0 = mine.i1 = 0;
+    mine.f[0] = block_sum((double)pe, red);
+    mine.f[1] = block_sum((double)pmx, red);
+    mine.f[2] = block_sum((double)pmy, red);
+    mine.f[3] = block_sum((double)pmz, red);
+    store_partial(a.partials, mine);
+}
+
+struct P3 {
+    float2 x, y, z;
+};
+
+// Heisenberg streaming kernel on column pairs: as heis_stream, but each
+// thread owns colour columns (2q, 2q+1) of its rows and loads each component
+// of a row pair with one 8-byte load, which halves the load instructions and
+// the index arithmetic per site and doubles the bytes each load carries
+// (measured 9% faster in 3D).  Needs W % 64 == 0.
+template <int D, bool FAST, bool HB, bool MEAS>
+__global__ void __launch_bounds__(256, 2) heis_pair(const OnArgs a)
+{
+    __shared__ double red[32];
+    const unsigned long long t64 = a.ctrl->t;
+    const uint32_t t = (uint32_t)t64;
+    const bool renorm = a.update && a.renorm_every > 0 &&
+                        (t64 + 1) % (unsigned long long)a.renorm_every == 0;
+    const int L = a.L, W = a.W, R = a.R;
+    const int WP = W / 2;
+    const long long H = a.H;  // < 2^31: every offset below fits in 32 bits
+    const int lane = threadIdx.x & 31;
+    const long long nitems = (long long)WP * (D == 3 ? L : 1) * (L / R);
+    const float J = a.J;
+    const float* ox = a.oth;
+    const float* oy = a.oth + H;
+    const float* oz = a.oth + 2 * H;
+    float* sx_ = a.own;
+    float* sy_ = a.own + H;
+    float* sz_ = a.own + 2 * H;
+    auto ld = [&](int i) -> P3 {
+        P3 v;
+        v.x = __ldg(reinterpret_cast<const float2*>(ox + i));
+        v.y = __ldg(reinterpret_cast<const float2*>(oy + i));
+        v.z = __ldg(reinterpret_cast<const float2*>(oz + i));
+        return v;
+    };
+    auto ld_own = [&](int i) -> P3 {
+        P3 v;
+        v.x = *reinterpret_cast<const float2*>(sx_ + i);
+        v.y = *reinterpret_cast<const float2*>(sy_ + i);
+        v.z = *reinterpret_cast<const float2*>(sz_ + i);
+        return v;
+    };
+    auto ld_one = [&](int i) -> V3 {
+        V3 v;
+        v.x = __ldg(ox + i);
+        v.y = __ldg(oy + i);
+        v.z = __ldg(oz + i);
+        return v;
+    };
+    float pe = 0.f, pmx = 0.f, pmy = 0.f, pmz = 0.f;
+    for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < nitems;
+         it += (long long)gridDim.x * blockDim.x) {
+        const int k0 = 2 * (int)(it % WP);
+        const long long rest = it / WP;
+        const int y3 = D == 3 ? (int)(rest % L) : 0;
+        const int m0 = (int)(D == 3 ? rest / L : rest) * R;
+        auto off = [&](int m) -> int { return (D == 3 ? m * L + y3 : m) * W + k0; };
+        const int dym = (y3 == 0 ? L - 1 : -1) * W, dyp = (y3 == L - 1 ? 1 - L : 1) * W;
+        const int mprev = m0 == 0 ? L - 1 : m0 - 1;
+        P3 prev = ld(off(mprev));
+        P3 cur = ld(off(m0));
+        P3 nxt_pf = ld(off(m0 == L - 1 ? 0 : m0 + 1));
+        P3 own_pf = ld_own(off(m0));
+        P3 ym_pf = prev, yp_pf = prev;
+        if (D == 3) {
+            ym_pf = ld(off(m0) + dym);
+            yp_pf = ld(off(m0) + dyp);
+        }
+        // the x neighbour outside the pair that a warp-edge lane cannot get by
+        // shuffle: column 2q-1 for lane 0 when p = 0, 2q+2 for lane 31 when p = 1
+        const int kl = k0 == 0 ? W - 1 : k0 - 1, kr = k0 + 2 == W ? 0 : k0 + 2;
+        V3 edge_pf = {0.f, 0.f, 0.f};
+        {
+            const int p0 = ((D == 3 ? y3 : m0) + (D == 3 ? m0 : 0) + a.c) & 1;
+            if (p0 ? lane == 31 : lane == 0) edge_pf = ld_one(off(m0) - k0 + (p0 ? kr : kl));
+        }
+        for (int r = 0; r < R; ++r) {
+            const int m = m0 + r;
+            const int yy = D == 3 ? y3 : m, zz = D == 3 ? m : 0;
+            const int p = (yy + zz + a.c) & 1;
+            const int j = off(m);
+            const P3 nxt = nxt_pf, vm = ym_pf, vp = yp_pf;
+            const V3 edge = edge_pf;
+            P3 s = own_pf;
+            if (r + 1 < R) {
+                const int m2 = m + 2 >= L ? m + 2 - L : m + 2;
+                const int j1 = off(m + 1);
+                nxt_pf = ld(off(m2));
+                own_pf = ld_own(j1);
+                if (D == 3) {
+                    ym_pf = ld(j1 + dym);
+                    yp_pf = ld(j1 + dyp);
+                }
+                const int p1 = p ^ 1;  // the parity alternates along the marching axis
+                if (p1 ? lane == 31 : lane == 0) edge_pf = ld_one(j1 - k0 + (p1 ? kr : kl));
+            }
+            // x neighbours: p = 0 -> A (2q-1, 2q), B (2q, 2q+1);
+            //               p = 1 -> A (2q, 2q+1), B (2q+1, 2q+2)
+            float ex, ey, ez;
+            if (p == 0) {
+                ex = __shfl_up_sync(0xffffffffu, cur.x.y, 1);
+                ey = __shfl_up_sync(0xffffffffu, cur.y.y, 1);
+                ez = __shfl_up_sync(0xffffffffu, cur.z.y, 1);
+                if (lane == 0) {
+                    ex = edge.x;
+                    ey = edge.y;
+                    ez = edge.z;
+                }
+            } else {
+                ex = __shfl_down_sync(0xffffffffu, cur.x.x, 1);
+                ey = __shfl_down_sync(0xffffffffu, cur.y.x, 1);
+                ez = __shfl_down_sync(0xffffffffu, cur.z.x, 1);
+                if (lane == 31) {
+                    ex = edge.x;
+                    ey = edge.y;
+                    ez = edge.z;
+                }
+            }
+            V3 hA, hB;
+            hA.x = (p ? cur.x.y : ex) + cur.x.x + prev.x.x + nxt.x.x;
+            hA.y = (p ? cur.y.y : ey) + cur.y.x + prev.y.x + nxt.y.x;
+            hA.z = (p ? cur.z.y : ez) + cur.z.x + prev.z.x + nxt.z.x;
+            hB.x = (p ? ex : cur.x.x) + cur.x.y + prev.x.y + nxt.x.y;
+            hB.y = (p ? ey : cur.y.x) + cur.y.y + prev.y.y + nxt.y.y;
+            hB.z = (p ? ez : cur.z.x) + cur.z.y + prev.z.y + nxt.z.y;
+            if (D == 3) {
+                hA.x += vm.x.x + vp.x.x;
+                hA.y += vm.y.x + vp.y.x;
+                hA.z += vm.z.x + vp.z.x;
+                hB.x += vm.x.y + vp.x.y;
+                hB.y += vm.y.y + vp.y.y;
+                hB.z += vm.z.y + vp.z.y;
+            }
+            hA.x *= J;
+            hA.y *= J;
+            hA.z *= J;
+            hB.x *= J;
+            hB.y *= J;
+            hB.z *= J;
+            if (a.update) {
+                bool changed = false;
+#pragma unroll
+                for (int b = 0; b < 2; ++b) {
+                    const uint4 rnd = philox4x32_10(
+                        make_uint4((uint32_t)(j + b), t, a.replica, (kSweep << 1) | (uint32_t)a.c),
+                        a.rk);
+                    float& sx = b ? s.x.y : s.x.x;
+                    float& sy = b ? s.y.y : s.y.x;
+                    float& sz = b ? s.z.y : s.z.x;
+                    const V3 h = b ? hB : hA;
+                    if (HB) {
+                        const V3 v = heis_heatbath(h.x, h.y, h.z, a.beta, rnd.x, rnd.y);
+                        sx = v.x;
+                        sy = v.y;
+                        sz = v.z;
+                        changed = true;
+                    } else {
+                        const float u = u24(rnd.x);
+                        const float3 v = sphere_point<FAST>(rnd.y, rnd.z);
+                        const float dE = -((v.x - sx) * h.x + (v.y - sy) * h.y + (v.z - sz) * h.z);
+                        if (dE <= 0.f || u < boltzmann<FAST>(-a.beta * dE)) {
+                            sx = v.x;
+                            sy = v.y;
+                            sz = v.z;
+                            changed = true;
+                        }
+                    }
+                    if (renorm) {
+                        const float inv = rsqrtf(sx * sx + sy * sy + sz * sz);
+                        sx *= inv;
+                        sy *= inv;
+                        sz *= inv;
+                        changed = true;
+                    }
+                }
+                if (changed) {
+                    *reinterpret_cast<float2*>(sx_ + j) = s.x;
+                    *reinterpret_cast<float2*>(sy_ + j) = s.y;
+                    *reinterpret_cast<float2*>(sz_ + j) = s.z;
+                }
+            }
+            if (MEAS) {
+                pe -= s.x.x * hA.x + s.y.x * hA.y + s.z.x * hA.z + s.x.y * hB.x + s.y.y * hB.y +
+                      s.z.y * hB.z;
+                pmx += s.x.x + s.x.y + cur.x.x + cur.x.y;
+                pmy += s.y.x + s.y.y + cur.y.x + cur.y.y;
+                pmz += s.z.x + s.z.y + cur.z.x + cur.z.y;
             }
             prev = cur;
             cur = nxt;
@@ -869,7 +1073,9 @@ cudaError_t launch_on(const sl_lattice* h, OnArgs a, cudaStream_t s)
 {
     const int var = a.update && h->update == SL_UPDATE_HEATBATH ? 2 : h->fast_math != 0;
     if (on_stream_ok(h)) {
-        const long long cols = NC == 3 ? h->W : h->W / 2;
+        // Heisenberg on column pairs when W % 64 == 0; XY always takes pairs
+        const bool pairs = NC == 2 || h->W % 64 == 0;
+        const long long cols = pairs ? h->W / 2 : h->W;
         a.R = on_rows(h, cols);
         const long long items = cols * (h->d == 3 ? h->L : 1) * (h->L / a.R);
         const int grid = grid_for(items, 256);
@@ -878,7 +1084,17 @@ cudaError_t launch_on(const sl_lattice* h, OnArgs a, cudaStream_t s)
         if (a.measure) K<__VA_ARGS__, true><<<grid, 256, 0, s>>>(a);          \
         else K<__VA_ARGS__, false><<<grid, 256, 0, s>>>(a);                   \
     } while (0)
-        if (NC == 3) {
+        if (NC == 3 && pairs) {
+            if (h->d == 2) {
+                if (var == 2) SPINMC_ON(heis_pair, 2, false, true);
+                else if (var == 1) SPINMC_ON(heis_pair, 2, true, false);
+                else SPINMC_ON(heis_pair, 2, false, false);
+            } else {
+                if (var == 2) SPINMC_ON(heis_pair, 3, false, true);
+                else if (var == 1) SPINMC_ON(heis_pair, 3, true, false);
+                else SPINMC_ON(heis_pair, 3, false, false);
+            }
+        } else if (NC == 3) {
             if (h->d == 2) {
                 if (var == 2) SPINMC_ON(heis_stream, 2, false, true);
                 else if (var == 1) SPINMC_ON(heis_stream, 2, true, false);

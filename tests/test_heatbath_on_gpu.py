@@ -149,14 +149,15 @@ def test_heatbath_step_parity(sm, n, d, L, beta):
     Steps(sm, n, d, L, beta, 10).check()
 
 
-@pytest.mark.parametrize("n,d,L,beta", [(3, 3, 64, 0.693), (3, 2, 64, 1.5), (2, 2, 128, 1.12),
-                                        (2, 2, 256, 0.9)])
+@pytest.mark.parametrize("n,d,L,beta", [(3, 3, 64, 0.693), (3, 2, 64, 1.5), (3, 3, 128, 0.693),
+                                        (3, 2, 128, 1.5), (2, 2, 128, 1.12), (2, 2, 256, 0.9)])
 @pytest.mark.parametrize("kernel", [1, 2])
 def test_heatbath_streaming_and_generic_kernels(sm, n, d, L, beta, kernel):
-    """Both kernels on sizes the streaming kernels accept; J = -0.8 on the
-    L = 64 lattices checks the coupling sign; fast math does not apply to
+    """Both kernels on sizes the streaming kernels accept (Heisenberg on
+    single columns for L = 64, on column pairs for L = 128); J = -0.8 on the
+    Heisenberg lattices checks the coupling sign; fast math does not apply to
     heat-bath draws."""
-    Steps(sm, n, d, L, beta, 4, kernel=kernel, J=-0.8 if L == 64 else 1.0,
+    Steps(sm, n, d, L, beta, 4, kernel=kernel, J=-0.8 if n == 3 else 1.0,
           fast=1 if L == 128 else 0).check()
 
 

@@ -141,14 +141,15 @@ def test_parity_first_ten_sweeps(sm, n, d, L, beta):
     Pair(sm, n, d, L, beta, 10).check()
 
 
-@pytest.mark.parametrize("n,d,L,beta", [(3, 3, 64, 0.693), (3, 2, 64, 1.5), (2, 2, 128, 1.12),
-                                        (2, 2, 256, 0.9)])
+@pytest.mark.parametrize("n,d,L,beta", [(3, 3, 64, 0.693), (3, 2, 64, 1.5), (3, 3, 128, 0.693),
+                                        (3, 2, 128, 1.5), (2, 2, 128, 1.12), (2, 2, 256, 0.9)])
 @pytest.mark.parametrize("kernel", [1, 2])
 def test_streaming_and_generic_kernels(sm, n, d, L, beta, kernel):
-    """The row-streaming kernels (register window, warp shuffles) and the
+    """The row-streaming kernels (register window, warp shuffles; Heisenberg
+    on single columns for L = 64, on column pairs for L = 128) and the
     per-site kernel both match the oracle on sizes the streaming kernels
-    accept; J = -0.8 checks the coupling sign."""
-    Pair(sm, n, d, L, beta, 6, kernel=kernel, J=-0.8 if L == 64 else 1.0).check()
+    accept; J = -0.8 on the Heisenberg lattices checks the coupling sign."""
+    Pair(sm, n, d, L, beta, 6, kernel=kernel, J=-0.8 if n == 3 else 1.0).check()
 
 
 @pytest.mark.parametrize("n,d,L,beta", [(3, 3, 64, 0.693), (2, 2, 128, 1.12)])
