@@ -5,8 +5,8 @@
 //
 //   XY (n = 2):          one FP32 angle per site, colour arrays t[c][j] holding
 //                        the angle in turns (theta / 2 pi, in [0, 1)), so a
-//                        proposal u24 is stored exactly and cos / sin are
-//                        sincospi(2 t) without a large range reduction;
+//                        proposal u24 is stored exactly and cos / sin of an
+//                        angle need no large range reduction (sincos_turns);
 //   Heisenberg (n = 3):  FP32 unit vectors, colour arrays of components
 //                        s[c][a*H + j] (structure of arrays).
 //
@@ -26,7 +26,8 @@
 // (JCGT 2017) around h.  XY: the offset from the angle of h by the
 // von Mises rejection method of Best and Fisher (1979), attempt a of a site
 // drawing its two uniforms from Philox(group, t, replica, a << 16 | colour).
-// The draws use the accurate log1p / expm1 / atan2 / sincospi whatever FAST.
+// The draws use the accurate log1p / expm1 / atan2 and sincos_turns whatever
+// FAST.
 #include "internal.h"
 
 namespace spinmc {
@@ -58,6 +59,32 @@ struct V3 {
     float x, y, z;
 };
 
+// sin and cos of 2 pi t for t in [0, 1]: the nearest quarter turn q / 4 is
+// taken off exactly (r = t - q / 4 lies in [-1/8, 1/8], Sterbenz), and sin
+// and cos of 2 pi r come from their Taylor series to degrees 9 and 10
+// (truncation below 2e-9 for |2 pi r| <= pi / 4; FP32 evaluation within
+// 1e-7 of the exact values); the quadrant q mod 4 swaps and negates them.
+__device__ __forceinline__ void sincos_turns(float t, float* s, float* c)
+{
+    const float q = rintf(4.0f * t);
+    const float r = fmaf(-0.25f, q, t);
+    const float y = r * r;
+    const float sp =
+        r * fmaf(fmaf(fmaf(fmaf(42.0586929f, y, -76.7058563f), y, 81.6052475f), y, -41.3417015f),
+                 y, 6.28318548f);
+    const float cp = fmaf(
+        fmaf(fmaf(fmaf(fmaf(-26.4262562f, y, 60.2446404f), y, -85.4568176f), y, 64.9393921f), y,
+             -19.7392082f),
+        y, 1.0f);
+    const int k = (int)q & 3;
+    float ss = (k & 1) ? cp : sp;
+    float cc = (k & 1) ? sp : cp;
+    if (k == 1 || k == 2) cc = -cc;
+    if (k >= 2) ss = -ss;
+    *s = ss;
+    *c = cc;
+}
+
 // sin and cos of an angle given in turns t in [0, 1)
 template <bool FAST>
 __device__ __forceinline__ void sincos_angle(float t, float* s, float* c)
@@ -68,7 +95,7 @@ __device__ __forceinline__ void sincos_angle(float t, float* s, float* c)
         *s = -*s;
         *c = -*c;
     } else {
-        sincospif(2.0f * t, s, c);
+        sincos_turns(t, s, c);
     }
 }
 
@@ -90,7 +117,7 @@ __device__ __forceinline__ float3 sphere_point(uint32_t oz, uint32_t ophi)
         sp = -sp;
         cp = -cp;
     } else {
-        sincospif(2.0f * u24(ophi), &sp, &cp);
+        sincos_turns(u24(ophi), &sp, &cp);
     }
     return make_float3(r * cp, r * sp, z);
 }
@@ -136,7 +163,7 @@ __device__ __forceinline__ V3 heis_heatbath(float hx, float hy, float hz, float 
     const float ia = -1.f / (sg + nz);
     const float b = nx * ny * ia;
     float sp, cp;
-    sincospif(2.0f * u24(o1), &sp, &cp);
+    sincos_turns(u24(o1), &sp, &cp);
     const float p1 = r * cp, p2 = r * sp;
     V3 v;
     v.x = c * nx + p1 * (1.f + sg * nx * nx * ia) + p2 * b;
@@ -171,7 +198,8 @@ __device__ __forceinline__ VonMises von_mises_setup(float hx, float hy, float be
 // (U1, with w = pi U1 / 2) and o2 (U2).
 __device__ __forceinline__ bool von_mises_accept(const VonMises& m, uint32_t o1, uint32_t o2)
 {
-    const float cw = cospif(0.5f * u24(o1));
+    float sw, cw;
+    sincos_turns(0.25f * u24(o1), &sw, &cw);
     const float omr = 1.f - m.rho;
     const float cc = m.cnum / (omr * omr + 4.f * m.rho * cw * cw);
     const float U2 = u24(o2);
@@ -184,7 +212,7 @@ __device__ __forceinline__ bool von_mises_accept(const VonMises& m, uint32_t o1,
 __device__ __forceinline__ float von_mises_angle(const VonMises& m, uint32_t o1)
 {
     float sw, cw;
-    sincospif(0.5f * u24(o1), &sw, &cw);
+    sincos_turns(0.25f * u24(o1), &sw, &cw);
     float dt = atan2f(m.g * sw, cw) * (1.0f / kPiF);
     if (o1 & 1u) dt = -dt;
     float tn = m.base + dt;

@@ -169,6 +169,31 @@ def test_fast_math_parity(sm, n, d, L, beta):
     Pair(sm, n, d, L, beta, 10, fast=1, tie_tol=TIE_TOL_FAST).check()
 
 
+def test_sin_cos_of_angles_in_turns(sm):
+    """The kernels' sin and cos of an angle stored in turns (exact reduction
+    to the nearest quarter turn, Taylor series to degrees 9 and 10) against
+    FP64: on the 2 x 2 XY lattice with every spin at one angle, M / 4 is
+    exactly the kernel's (cos, sin) of the stored turn; 4001 angles cover
+    every quadrant, the octant boundaries and the wrap at one turn."""
+    lat = sm.Lattice(2, 2, n=2, seed=1)
+    two_pi = np.float32(6.28318530717958647692)
+    inv = np.float32(1) / two_pi
+    ks = np.arange(4001)
+    turns = np.concatenate([ks / 4000.0, [1 / 8, 3 / 8, 5 / 8, 7 / 8, 1 - 2 ** -24]])
+    worst = 0.0
+    for tt in turns:
+        theta = np.float32(tt * 2 * math.pi)
+        lat.set_spins(np.full(4, theta, np.float32))
+        # the stored turn, as the layout kernel forms it in FP32
+        tr = np.float32(theta * inv)
+        t = float(tr - np.floor(tr))
+        _, M = lat.measure()
+        err = max(abs(M[0] / 4 - math.cos(2 * math.pi * t)), abs(M[1] / 4 - math.sin(2 * math.pi * t)))
+        worst = max(worst, err)
+    lat.close()
+    assert worst < 2e-7, worst
+
+
 def test_heisenberg_renormalisation(sm):
     """Sweep 15 is a renormalising sweep at interval 16: every spin ends at
     unit length even when the start had norm 1.5."""
