@@ -412,15 +412,6 @@ __global__ void __launch_bounds__(128) on_generic(const OnArgs a)
 // two warp-edge lanes load theirs).  Loads for the next row are issued one
 // row ahead.
 
-__device__ __forceinline__ V3 ld3(const float* p, long long H, long long i)
-{
-    V3 v;
-    v.x = __ldg(p + i);
-    v.y = __ldg(p + H + i);
-    v.z = __ldg(p + 2 * H + i);
-    return v;
-}
-
 __device__ __forceinline__ V3 shfl3_up(V3 v)
 {
     V3 r;
