@@ -541,31 +541,86 @@ def cpu_baseline(wl, target_s=15.0):
                        "single-threaded C oracle, %.1f s" % (nsw, L, d, dt))
 
 
-def reference_arm(args, world, rank):
-    """--impl reference: the CPU oracle as it stands, each step one sweep of a
-    2D L=1024 sample of the headline workload, on the host cores."""
-    if rank != 0:
-        return
+def reference_sample(wl):
+    """A bounded sample of a workload for the oracle: (step(t), sites updated
+    per step, description).  Lattice workloads keep their dimension, model and
+    rule on a smaller side; walkers run 8 windows spread over the energy
+    range; the spin-glass batch runs one sample of each side with all its
+    temperatures and replica exchange."""
+    import numpy as np
     import oracle
     from paper_1107_5463_gb300 import inputs
-    wl = WORKLOADS[HEADLINE]
-    L = 1024
-    s = oracle.ising_init(2, L, inputs.DEFAULT_SEED)
+    seed = inputs.DEFAULT_SEED
+    st = wl["storage"]
+    if st == "walkers":
+        L, width = wl["L"], wl["width"]
+        N = L * L
+        klo = list(range(0, N - width + 1, width))
+        pick = klo[::len(klo) // 8][:8]
+        walkers = [oracle.Walker(L, k, k + width, seed, i) for i, k in enumerate(pick)]
+        flat = np.zeros(width + 1)
+
+        def step(t):
+            for w in walkers:
+                if wl["kind"] == "wl":
+                    w.wl(1, 20)
+                else:
+                    w.muca(flat, 1)
+        return step, len(walkers) * N, ("one sweep of 8 walkers of a %d^2 lattice in windows "
+                                        "of %d levels per step" % (L, width + 1))
+    if st == "batch":
+        d, nt = wl["d"], wl["temps"]
+        betas = inputs.geometric_betas(nt)
+        samples = []
+        for q, Ls in enumerate(inputs.EA_SIZES):
+            jb = oracle.ea_couplings(d, Ls, seed, q)
+            spins = np.stack([oracle.ising_init(d, Ls, seed, q * nt + r) for r in range(nt)])
+            samples.append((Ls, q, jb, spins, np.arange(nt, dtype=np.int32)))
+
+        def step(t):
+            for Ls, q, jb, spins, perm in samples:
+                oracle.ea_pt_sweeps(d, Ls, jb, betas, seed, q, t, 1, spins, perm)
+        n = nt * sum(Ls ** d for Ls in inputs.EA_SIZES)
+        return step, n, ("one sweep with exchange of one sample of each side %s x %d "
+                         "temperatures per step" % (list(inputs.EA_SIZES), nt))
+    d = wl["d"]
+    if wl.get("multihit"):
+        Ls = 64 if d == 2 else 32
+    elif wl["n"] > 1:
+        Ls = 512 if d == 2 else 64
+    else:
+        Ls = 1024 if d == 2 else 96
+    Ls = min(Ls, wl["L"])
+    s = oracle_state(wl, Ls)
+    hits = wl.get("multihit") or 1
+    return (lambda t: oracle_sweep(wl, s, t, Ls)), Ls ** d * hits, (
+        "one sweep of a %d^%d sample lattice incl. E/|m| per step" % (Ls, d))
+
+
+def reference_arm(args, world, rank):
+    """--impl reference: the CPU oracle as it stands, on a bounded sample of the
+    workload (reference_sample), on the host cores; rank 0 alone runs."""
+    if rank != 0:
+        return
+    wl = WORKLOADS[args.workload]
+    step, n, sample = reference_sample(wl)
     for k in range(args.warmup):
-        oracle.ising_sweeps(2, L, s, wl["beta"], 7, k, 1)
+        step(k)
     t0 = time.perf_counter()
     for k in range(args.steps):
-        oracle.ising_sweeps(2, L, s, wl["beta"], 7, args.warmup + k, 1)
+        step(args.warmup + k)
     dt = time.perf_counter() - t0
-    v = L * L * args.steps / (dt * 1e9)
+    v = n * args.steps / (dt * 1e9)
+    dtype = {"i8": "int8", "bits": "int8", "vec": "f64", "angle": "f64", "walkers": "int8",
+             "batch": "int8"}[wl["storage"]]
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "int8", "data": "synthetic",
-            "config": {"workload": HEADLINE, "sample": "one sweep of a 2D L=1024 lattice per step",
+            "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+            "config": {"workload": args.workload, "desc": wl["desc"], "sample": sample,
                        "parallelism": "host, 1 thread"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "2D Ising L=1024 at beta_c, one sweep incl. E/|m| per step"},
+                             "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
