@@ -323,6 +323,42 @@ def launch_shape(wl):
     return 3, "i8_stream<%d,0,0,%d,0/1>" % (d, hb)
 
 
+def compute_ceilings(spinmc, target_ms=2.0):
+    """Measured throughput of the units the sweeps lean on (sl_microbench):
+    Philox4x32-10 calls, 32-bit integer multiplies, FP32 FMAs and hardware
+    exp2, each timed with CUDA events over one launch of at least target_ms
+    after a warm-up launch."""
+    import torch
+    n = spinmc.sl_microbench_threads()
+    out = torch.empty(n, dtype=torch.int32, device="cuda")
+    st = torch.cuda.current_stream()
+    res = {}
+    for name, kind, it in (("philox_calls_per_ns", spinmc.SL_MB_PHILOX, 256),
+                           ("imad_per_ns", spinmc.SL_MB_IMAD, 1024),
+                           ("ffma_per_ns", spinmc.SL_MB_FFMA, 4096),
+                           ("mufu_ex2_per_ns", spinmc.SL_MB_MUFU, 1024)):
+        while True:
+            spinmc.sl_microbench(kind, it, out, out.numel() * 4, st.cuda_stream)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            ops = spinmc.sl_microbench(kind, it, out, out.numel() * 4, st.cuda_stream)
+            e1.record(st)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            limit = (2 ** 32 - 1) // n if kind == spinmc.SL_MB_PHILOX else 1 << 22
+            if ms >= target_ms or 2 * it > limit:
+                break
+            it *= 2
+        res[name] = ops / (ms * 1e6)
+    return res
+
+
+# sites one Philox4x32-10 call serves in a sweep (Metropolis and heat-bath
+# Ising: a quarter call per site; XY Metropolis: half; Heisenberg: one)
+RNG_SITES_PER_CALL = {"i8": 4, "bits": 4, "angle": 2, "vec": 1}
+
+
 def configure(spinmc, lat, wl):
     """Apply a workload's update rule, multi-hit and fast-math options."""
     if wl.get("fast"):
@@ -735,6 +771,14 @@ def main():
         "clocks": clocks,
         "check": {"E_per_site_last": e_last / N},
     }
+    if rank == 0:
+        ceil = compute_ceilings(spinmc)
+        per_call = RNG_SITES_PER_CALL.get(wl["storage"])
+        if per_call and wl.get("update") != 2:
+            # no sweep can outrun its random numbers
+            ceil["rng_bound_flips_per_ns"] = per_call * ceil["philox_calls_per_ns"]
+            ceil["frac_of_rng_bound"] = value / ceil["rng_bound_flips_per_ns"]
+        line["compute_ceilings"] = ceil
     if rank == 0:
         if args.e2e_jobs > 0:
             if wl["n"] == 1:

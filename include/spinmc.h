@@ -400,7 +400,35 @@ const char* sl_strerror(int status);
  * msg (cap bytes, NUL-terminated); returns its full length. */
 int sl_last_error(char* msg, size_t cap);
 
+/*
+ * Microbenchmarks — throughput of the units the sweeps lean on, so that a
+ * measured compute ceiling can stand beside the one from unit counts and the
+ * clock (the paper's speed-ups are bounded by the same units).  One call
+ * launches, asynchronously on `stream`, a full-occupancy grid of
+ * sl_microbench_threads() threads, each running independent chains:
+ *   SL_MB_PHILOX  Philox4x32-10 with key 1: thread g makes `iterations` calls
+ *                 with counters (g * iterations + i, 7, 0, 0) and writes the
+ *                 xor of all their outputs to dev_out[g] (uint32; checkable
+ *                 against any Philox implementation);
+ *   SL_MB_IMAD    32-bit integer multiplies (mulhi and mullo chains);
+ *   SL_MB_FFMA    FP32 fused multiply-adds;
+ *   SL_MB_MUFU    hardware exp2 of the special-function unit.
+ * dev_out holds 4 bytes per thread (device memory, caller-owned); *ops
+ * receives the operations the launch performs (calls for SL_MB_PHILOX,
+ * lane operations otherwise).  The caller times the launch (CUDA events on
+ * the same stream).  SL_EINVAL for an unknown kind, iterations < 1, a short
+ * buffer, or Philox counters beyond 32 bits; SL_ECUDA if the launch fails.
+ */
+#define SL_MB_PHILOX 0
+#define SL_MB_IMAD 1
+#define SL_MB_FFMA 2
+#define SL_MB_MUFU 3
+int sl_microbench_threads(int* threads);
+int sl_microbench(int kind, int iterations, void* dev_out, size_t out_bytes, void* stream,
+                  double* ops);
+
 #ifdef __cplusplus
 }
 #endif
+
 #endif /* SPINMC_H */

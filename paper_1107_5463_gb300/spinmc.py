@@ -25,6 +25,7 @@ SL_OPT_UPDATE, SL_OPT_MULTIHIT, SL_OPT_TILE = 6, 7, 8
 SL_UPDATE_METROPOLIS, SL_UPDATE_HEATBATH, SL_UPDATE_SW = 0, 1, 2
 SL_WOPT_SPINS_SMEM = 1
 SL_BOPT_AUTOTUNE, SL_BOPT_PACK = 1, 2
+SL_MB_PHILOX, SL_MB_IMAD, SL_MB_FFMA, SL_MB_MUFU = 0, 1, 2, 3
 
 if not os.path.exists(LIB_PATH):
     raise ImportError("libspinmc.so is not built at %s; run paper_1107_5463_gb300.build.build()"
@@ -69,6 +70,8 @@ _sig("sl_batch_set_option", _int, _vp, _int, _i64)
 _sig("sl_batch_tuning", _int, _vp, _int, ctypes.POINTER(_int), ctypes.POINTER(_int),
      ctypes.POINTER(_dbl))
 _sig("sl_ising_measure_static", _int, _int, _int, _dbl, _vp, _vp, _vp)
+_sig("sl_microbench_threads", _int, ctypes.POINTER(_int))
+_sig("sl_microbench", _int, _int, _int, _vp, _sz, _vp, ctypes.POINTER(_dbl))
 _sig("sl_walkers_required_bytes", _int, _int, _int, _vp, _vp, _int, ctypes.POINTER(_sz))
 _sig("sl_walkers_create", _int, _int, _int, _vp, _vp, _int, _u64, _vp, _sz, _vp,
      ctypes.POINTER(_vp))
@@ -254,6 +257,21 @@ def sl_batch_tuning(h):
         if cls >= n:
             break
     return out
+
+
+def sl_microbench_threads():
+    n = _int()
+    _check(_lib.sl_microbench_threads(ctypes.byref(n)), "sl_microbench_threads")
+    return n.value
+
+
+def sl_microbench(kind, iterations, dev_out, nbytes, stream):
+    """Launch one microbenchmark (SL_MB_*) on `stream`; return the operations
+    it performs (the caller times it)."""
+    ops = _dbl()
+    _check(_lib.sl_microbench(kind, iterations, _addr(dev_out), nbytes, stream,
+                              ctypes.byref(ops)), "sl_microbench")
+    return ops.value
 
 
 def sl_ising_measure_static(d, L, J, dev_spins, dev_out, stream):
