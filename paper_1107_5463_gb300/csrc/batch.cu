@@ -962,8 +962,7 @@ int sl_batch_run(sl_batch* b, int64_t nsweeps, uint64_t seed, double* dev_E)
     a.rk = make_round_keys(seed);
     a.E_out = dev_E;
     // one launch: replay the captured graph with this run's arguments
-    cudaKernelNodeParams kp;
-    std::memset(&kp, 0, sizeof kp);
+    cudaKernelNodeParams kp = {};
     void* args[1] = {&a};
     kp.func = b->d == 3 ? (void*)ea_pt_persistent<3> : (void*)ea_pt_persistent<2>;
     kp.gridDim = dim3((unsigned)b->grid);

@@ -435,7 +435,7 @@ int sl_walkers_required_bytes(int L, int nwin, const int* klo, const int* khi, i
                               size_t* bytes)
 {
     if (!bytes) return fail(SL_EINVAL, "bytes is NULL");
-    int kmax;
+    int kmax = 0;
     const int st = check_walk_config(L, nwin, klo, khi, wpw, &kmax);
     if (st != SL_OK) return st;
     if (!klo || !khi) return fail(SL_EINVAL, "window bounds are NULL");
@@ -449,7 +449,7 @@ int sl_walkers_create(int L, int nwin, const int* klo, const int* khi, int wpw, 
     if (!out) return fail(SL_EINVAL, "out is NULL");
     *out = nullptr;
     if (!klo || !khi) return fail(SL_EINVAL, "window bounds are NULL");
-    int kmax;
+    int kmax = 0;
     int st = check_walk_config(L, nwin, klo, khi, wpw, &kmax);
     if (st != SL_OK) return st;
     const WalkLayout y = walk_layout(L, nwin, wpw, kmax);
