@@ -138,8 +138,8 @@ static void ising_sweeps_rule(int d, int L, double J, const int8_t* Jb, double b
                         if (heatbath) {
                             /* P(s_i = +1) = 1 / (1 + exp(-2 beta J h)) */
                             double a = 2.0 * J * (double)ising_field(&g, Jb, s, xyz, i);
-                            double x = 4294967296.0 / (1.0 + exp(-beta * a));
-                            s[i] = (double)out[j & 3] < x ? 1 : -1;
+                            double thr = 4294967296.0 / (1.0 + exp(-beta * a));
+                            s[i] = (double)out[j & 3] < thr ? 1 : -1;
                         } else if (ising_accept(&g, J, Jb, beta, s, xyz, i, out[j & 3])) {
                             s[i] = (int8_t)-s[i];
                         }
