@@ -57,8 +57,10 @@ extern "C" {
 #define SL_EINVAL (-1)    /* invalid argument (message in sl_last_error) */
 #define SL_ENOMEM (-2)    /* buffer too small or allocation failed */
 #define SL_ECUDA (-3)     /* a CUDA runtime call failed */
-#define SL_ETIMEOUT (-4)  /* a bounded device-side wait gave up */
-#define SL_EDEVICE (-5)   /* a kernel raised the sticky device error word */
+#define SL_ETIMEOUT (-4)  /* reserved for bounded device-side waits (no kernel of this
+                             library waits on another thread, block or device) */
+#define SL_EDEVICE (-5)   /* a kernel reported a failure it detected (a walker that did
+                             not reach its window) */
 
 /* coupling layouts */
 #define SL_J_UNIFORM 0    /* every bond has J_ij = J */
@@ -148,8 +150,7 @@ int sl_sweep_series(sl_lattice* lat, double beta, int64_t nsweeps, uint64_t seed
 /*
  * sl_measure — energy (Eq. 1) and magnetisation of the current state.
  * magnetisation receives n components of M = sum_i s_i followed by |M|/N
- * (n + 1 doubles).  Synchronises the handle's stream; returns SL_EDEVICE if
- * a kernel has raised the device error word since the last check.
+ * (n + 1 doubles).  Synchronises the handle's stream.
  */
 int sl_measure(sl_lattice* lat, double* energy, double* magnetisation);
 

@@ -51,11 +51,8 @@ struct Ctrl {
     double* series_E;          // per-sweep energy, or null
     double* series_absm;       // per-sweep |m|, or null
     unsigned int done;         // blocks finished in the measuring pass
-    unsigned int error;        // sticky error bits (kErr*)
     double obs[4];             // E, Mx, My, Mz after the last measured pass
 };
-
-enum : unsigned int { kErrGrid = 1u, kErrBounds = 2u };
 
 // Partial sums one block contributes to a measured pass.  Ising passes use
 // the integer members (exact), continuous spins the double members.

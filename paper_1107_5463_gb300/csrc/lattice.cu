@@ -218,13 +218,8 @@ int ensure_graph(sl_lattice* h, const SweepParams& p)
 
 int sync_and_check(sl_lattice* h)
 {
-    cudaError_t e = cudaStreamSynchronize(h->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
-    unsigned err = 0;
-    e = cudaMemcpy(&err, &h->ctrl->error, sizeof err, cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return cuda_fail(e, "read device error word");
-    if (err) return fail(SL_EDEVICE, "device error word 0x%x", err);
-    return SL_OK;
+    const cudaError_t e = cudaStreamSynchronize(h->stream);
+    return e == cudaSuccess ? SL_OK : cuda_fail(e, "cudaStreamSynchronize");
 }
 
 size_t nat_bytes(const sl_lattice* h)
@@ -617,7 +612,7 @@ const char* sl_strerror(int status)
     case SL_ENOMEM: return "out of memory or buffer too small";
     case SL_ECUDA: return "CUDA runtime error";
     case SL_ETIMEOUT: return "device wait timed out";
-    case SL_EDEVICE: return "device error word raised";
+    case SL_EDEVICE: return "a kernel reported a failure";
     default: return "unknown status";
     }
 }
