@@ -577,6 +577,62 @@ def cpu_baseline(wl, target_s=15.0):
                        "single-threaded C oracle, %.1f s" % (nsw, L, d, dt))
 
 
+def sample_side(wl):
+    """Side of the oracle's sample lattice for a lattice workload: one sweep
+    takes a few tens of milliseconds on one core."""
+    d = wl["d"]
+    if wl.get("multihit"):
+        Ls = 64 if d == 2 else 32
+    elif wl["n"] > 1:
+        Ls = 512 if d == 2 else 64
+    else:
+        Ls = 1024 if d == 2 else 96
+    return min(Ls, wl["L"])
+
+
+def _oracle_worker(task):
+    """One process of the all-cores oracle baseline: sweeps of its own sample
+    lattice of the workload until the time budget is spent; returns (site
+    updates, seconds)."""
+    name, budget_s = task
+    wl = WORKLOADS[name]
+    Ls = sample_side(wl)
+    s = oracle_state(wl, Ls)
+    hits = wl.get("multihit") or 1
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        oracle_sweep(wl, s, n, Ls)
+        n += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    return n * Ls ** wl["d"] * hits, time.perf_counter() - t0
+
+
+def cpu_baseline_all_cores(name, budget_s=8.0):
+    """The oracle as it stands on every host core at once: one spawned process
+    per core, each sweeping its own sample lattice (the oracle is
+    single-threaded; the processes share nothing), aggregate throughput."""
+    import multiprocessing as mp
+    wl = WORKLOADS[name]
+    cores = os.cpu_count() or 1
+    try:
+        # spawned (the parent has touched the GPU), bounded in time; leaving
+        # the block terminates the workers
+        with mp.get_context("spawn").Pool(cores) as pool:
+            res = pool.map_async(_oracle_worker, [(name, budget_s)] * cores).get(
+                timeout=10 * budget_s + 120)
+    except Exception as e:  # the bench line is still printed
+        return dict(value=None, unit=UNIT, cores=cores, kind="oracle",
+                    error="all-cores run failed: %s" % type(e).__name__)
+    sites = sum(r[0] for r in res)
+    secs = max(r[1] for r in res)
+    Ls = sample_side(wl)
+    return dict(value=sites / (secs * 1e9), unit=UNIT, cores=cores, kind="oracle",
+                sample="%d processes, each sweeping its own %d^%d sample lattice for %.0f s"
+                       % (cores, Ls, wl["d"], budget_s))
+
+
 def reference_sample(wl):
     """A bounded sample of a workload for the oracle: (step(t), sites updated
     per step, description).  Lattice workloads keep their dimension, model and
@@ -620,13 +676,7 @@ def reference_sample(wl):
         return step, n, ("one sweep with exchange of one sample of each side %s x %d "
                          "temperatures per step" % (list(inputs.EA_SIZES), nt))
     d = wl["d"]
-    if wl.get("multihit"):
-        Ls = 64 if d == 2 else 32
-    elif wl["n"] > 1:
-        Ls = 512 if d == 2 else 64
-    else:
-        Ls = 1024 if d == 2 else 96
-    Ls = min(Ls, wl["L"])
+    Ls = sample_side(wl)
     s = oracle_state(wl, Ls)
     hits = wl.get("multihit") or 1
     return (lambda t: oracle_sweep(wl, s, t, Ls)), Ls ** d * hits, (
@@ -786,6 +836,7 @@ def main():
                 line["e2e"] = e2e_run(spinmc, wl, args.e2e_jobs, per_job, rank)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(wl)
+            line["cpu_baseline"]["all_cores"] = cpu_baseline_all_cores(args.workload)
         if not args.no_variants:
             var = {}
             for name, w in WORKLOADS.items():
