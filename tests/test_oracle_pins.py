@@ -194,6 +194,18 @@ def test_one_sweep_transition_matrix_on_L2(d, beta):
 
 
 @pytest.mark.slow
+def test_kaufman_energy_tends_to_onsager():
+    """Kaufman's exact finite-torus energy per site at beta_c approaches
+    Onsager's critical energy -sqrt(2) with a 1/L correction: (E + sqrt 2) L
+    is the same for L = 64, 256 and 1024, and E(1024) is within 7e-4 of
+    -sqrt(2).  With the L = 64 chain below this ties the oracle to Onsager's
+    value."""
+    prods = [(exact.kaufman_energy_per_site(BETA_C, L) + math.sqrt(2)) * L
+             for L in (64, 256, 1024)]
+    assert max(prods) - min(prods) < 1e-3, prods
+    assert abs(exact.kaufman_energy_per_site(BETA_C, 1024) + math.sqrt(2)) < 7e-4
+
+
 def test_ising_L64_energy_matches_kaufman():
     """The 2D Ising workload of side 64 at beta_c = ln(1+sqrt2)/2, 4 x 10^4
     sweeps from a random start: mean energy per site against Kaufman's exact
