@@ -248,14 +248,22 @@ def batch_sites(wl):
     return sum(L ** wl["d"] for L in inputs.ea_sample_sizes(wl["samples"])) * wl["temps"]
 
 
+def sample_range(nsamples, rank, world):
+    """The contiguous block of global sample indices rank `rank` of `world`
+    runs: [lo, hi), sizes differing by at most one."""
+    return nsamples * rank // world, nsamples * (rank + 1) // world
+
+
 def time_batch(spinmc, wl, steps, warmup, want_clocks, local, rank=0, world=1):
     """Device-timed K sweeps (with exchange) of the batched spin-glass
-    workload; under N ranks each rank takes every N-th sample."""
+    workload; under N ranks each rank takes a contiguous block of the global
+    samples, keyed by their global indices (the union is the 1-GPU batch)."""
     import torch
     from paper_1107_5463_gb300 import inputs
-    Ls = inputs.ea_sample_sizes(wl["samples"])[rank::world]
+    lo, hi = sample_range(wl["samples"], rank, world)
+    Ls = inputs.ea_sample_sizes(wl["samples"])[lo:hi]
     b = spinmc.Batch(wl["d"], Ls, wl["temps"], inputs.geometric_betas(wl["temps"]),
-                     seed=inputs.DEFAULT_SEED)
+                     seed=inputs.DEFAULT_SEED, first_sample=lo)
     b.run(warmup, inputs.DEFAULT_SEED)
     torch.cuda.synchronize()
     clocks = Clocks(local) if want_clocks else None

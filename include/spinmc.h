@@ -211,16 +211,21 @@ void sl_destroy(sl_lattice* lat);
  *
  * Section 2 of the paper: for quenched disorder, independent disorder samples
  * are a trivially parallel layer on top of the lattice decomposition.  A batch
- * holds nsamples Edwards-Anderson samples (couplings J_ij = +-1 with p = 1/2,
- * J_ij = +1 iff the top bit of output 0 of Philox(i, mu, sample, 2 << 1) under
- * the create seed is set), each with ntemps <= 32 replicas ("slots") at the
- * inverse temperatures betas[0..ntemps-1].  Slot r of sample s starts from
+ * holds nsamples Edwards-Anderson samples with the global indices
+ * s = first_sample .. first_sample + nsamples - 1 (couplings J_ij = +-1 with
+ * p = 1/2, J_ij = +1 iff the top bit of output 0 of Philox(i, mu, s, 2 << 1)
+ * under the create seed is set), each with ntemps <= 32 replicas ("slots") at
+ * the inverse temperatures betas[0..ntemps-1].  Slot r of sample s starts from
  * the Ising start state of replica id s * ntemps + r and always draws its
- * moves with that replica id.  After every sweep the energies of all slots
+ * moves with that replica id.  Every random number is keyed by the global
+ * index, so batches that split a sample range (one per GPU, say) together
+ * hold exactly the samples of one batch over the whole range.  Calls that
+ * take a `sample` argument count it from the batch's first sample (0 ..
+ * nsamples - 1).  After every sweep the energies of all slots
  * are measured and temperature pairs (k, k+1), k = t mod 2, t mod 2 + 2, ...
  * attempt an exchange accepted iff Delta >= 0 or U < exp(Delta) 2^32,
  * Delta = (b_k - b_{k+1}) (E_{r(k)} - E_{r(k+1)}), U = output 0 of
- * Philox(k, t, s, 3 << 1) under the sweep seed; accepted pairs swap which
+ * Philox(k, t, s, 3 << 1) under the sweep seed (s the global index); accepted pairs swap which
  * slot holds which temperature.  The replica exchange is not in the paper:
  * it is the standard Metropolis swap between neighbouring temperatures. */
 
@@ -233,11 +238,13 @@ int sl_batch_required_bytes(int d, const int* L_per_sample, int nsamples, int nt
                             const double* betas, size_t* bytes);
 
 /* Create the batch on `stream` and draw its couplings and start states from
- * `seed`.  betas: ntemps finite values >= 0 (host).  dev_buf as for
- * sl_create (caller-owned, 256-byte aligned, NULL = library-owned). */
+ * `seed`.  L_per_sample[q] is the side of global sample first_sample + q.
+ * betas: ntemps finite values >= 0 (host).  (first_sample + nsamples) *
+ * ntemps must not exceed 2^32.  dev_buf as for sl_create (caller-owned,
+ * 256-byte aligned, NULL = library-owned). */
 int sl_batch_create(int d, const int* L_per_sample, int nsamples, int ntemps,
-                    const double* betas, uint64_t seed, void* dev_buf, size_t dev_buf_bytes,
-                    void* stream, sl_batch** out);
+                    const double* betas, uint64_t seed, uint32_t first_sample, void* dev_buf,
+                    size_t dev_buf_bytes, void* stream, sl_batch** out);
 
 /* nsweeps sweeps of every slot of every sample, each followed by the energy
  * measurement and the exchange step, in one graph-captured launch per sample
@@ -278,13 +285,26 @@ int sl_batch_get_bonds(sl_batch* b, int sample, int8_t* dst);
 /* Sweeps done by the batch (the next sweep index). */
 int sl_batch_sweeps_done(sl_batch* b, int64_t* sweeps_done);
 
+/* Checkpoint load: the spins of every slot of a sample (ntemps x N int8 +-1,
+ * slot after slot, each in natural order; host or device memory) and the
+ * slot holding each temperature (ntemps int32 on the host, a permutation of
+ * 0 .. ntemps-1, as sl_batch_get reports it).  With sl_batch_set_sweeps_done
+ * and the create seed, a batch saved by sl_batch_get after n sweeps resumes
+ * exactly: its next sweeps equal those of an uninterrupted run.  SL_EINVAL
+ * if slot_of_temp is not a permutation.  Synchronises. */
+int sl_batch_set(sl_batch* b, int sample, const int8_t* spins, const int32_t* slot_of_temp);
+
+/* Set the sweeps done (the next sweep index) for resuming a checkpoint. */
+int sl_batch_set_sweeps_done(sl_batch* b, int64_t sweeps_done);
+
 /* Release host metadata (and the buffer if library-owned); synchronises. */
 void sl_batch_destroy(sl_batch* b);
 
 /*
- * sl_ising_measure_static — energy (Eq. 1 with J_ij = J) and magnetisation of
- * an Ising configuration, without allocating any device memory.  The paper
- * has no counterpart: this entry point exists for callers that cannot call
+ * sl_ising_measure_static — energy E = -J sum over nearest-neighbour pairs of
+ * s_i s_j (each pair once, periodic lattice) and magnetisation of an Ising
+ * configuration, without allocating any device memory.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
  * cudaMalloc, such as code running under another framework's device-memory
  * pool (a raw allocation would bypass its accounting or budget) or a
  * latency-critical loop that must not pay for an allocation.
@@ -294,10 +314,12 @@ void sl_batch_destroy(sl_batch* b);
  *   stream     cudaStream_t (NULL = legacy default stream); asynchronous.
  * Its reduction scratch is one static device array of about 192 KiB, held by
  * every GPU that loads the library until the process exits; it serves at
- * most 2^28 sites (larger lattices return SL_EINVAL).  The first call on a
- * device looks up that array's device address with the device current, so
- * make the first call before any stream capture.  All calls share the array:
- * calls that overlap on the GPU race, calls in order on one stream do not.
+ * most 2^28 sites (2D L <= 16384, 3D L <= 644; larger lattices return
+ * SL_EINVAL).  The first call on a device (and the first after the device's
+ * context was replaced, as by cudaDeviceReset) looks up that array's device
+ * address with the device current, so make the first call before any stream
+ * capture.  All calls share the array: calls that overlap on the GPU race,
+ * calls in order on one stream do not.
  */
 int sl_ising_measure_static(int d, int L, double J, const int8_t* dev_spins, double* dev_out,
                             void* stream);
@@ -368,6 +390,20 @@ int sl_walkers_read(sl_walkers* w, int64_t* S, uint32_t* H, int32_t* level, int3
 /* sl_walkers_get_spins — one walker's spins in natural order as int8 +-1
  * (host or device pointer, N entries).  Synchronises. */
 int sl_walkers_get_spins(sl_walkers* w, int walker, int8_t* dst);
+
+/* Checkpoint load.  sl_walkers_set_spins writes one walker's configuration
+ * (natural order int8 +-1, host or device, N entries) and sets the walker's
+ * level to that of the configuration (k = (E + 2N) / 4); SL_EINVAL if the
+ * level lies outside the walker's window.  sl_walkers_write sets S, H (host,
+ * [walker][kmax], as sl_walkers_read returns them), stages and visited-level
+ * masks; any pointer may be NULL to keep that array.
+ * sl_walkers_set_sweeps_done sets the next sweep index.  Restoring all of
+ * them from what sl_walkers_read, sl_walkers_get_spins and sl_walkers_info
+ * returned after n sweeps resumes the run exactly.  Each synchronises. */
+int sl_walkers_set_spins(sl_walkers* w, int walker, const int8_t* src);
+int sl_walkers_write(sl_walkers* w, const int64_t* S, const uint32_t* H, const int32_t* stage,
+                     const uint64_t* visited);
+int sl_walkers_set_sweeps_done(sl_walkers* w, int64_t sweeps_done);
 
 /* sl_walkers_set_option — SL_WOPT_SPINS_SMEM: 1 keeps each warp's 32
  * lattices in shared memory for the length of a run, 0 (default) reads and

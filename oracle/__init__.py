@@ -65,10 +65,10 @@ def lib():
         L.orc_xy_measure.argtypes = [_int, _int, _dbl, _vp, _f64p, ctypes.POINTER(_dbl), _f64p]
         L.orc_heis_measure.argtypes = [_int, _int, _dbl, _vp, _f64p, ctypes.POINTER(_dbl), _f64p]
         L.orc_xy_sweeps.argtypes = [_int, _int, _dbl, _vp, _dbl, _u64, _u32, _i64, _i64,
-                                    _f64p, _vp, _vp, _dbl, _vp, _i64]
+                                    _f64p, _vp, _vp, _dbl, _vp, _vp, _i64]
         L.orc_xy_sweeps.restype = _i64
         L.orc_heis_sweeps.argtypes = [_int, _int, _dbl, _vp, _dbl, _u64, _u32, _i64, _i64,
-                                      _int, _f64p, _vp, _vp, _dbl, _vp, _i64]
+                                      _int, _f64p, _vp, _vp, _dbl, _vp, _vp, _i64]
         L.orc_heis_sweeps.restype = _i64
         L.orc_xy_heatbath_sweeps.argtypes = [_int, _int, _dbl, _vp, _dbl, _u64, _u32, _i64,
                                              _i64, _int, _f64p, _vp, _vp, _dbl, _vp, _i64]
@@ -295,38 +295,48 @@ def heis_measure(d, L, s, J=1.0, Jb=None):
 
 
 def xy_sweeps(d, L, theta, beta, seed, t0, nsweeps, J=1.0, Jb=None, replica=0,
-              tie_tol=0.0, ties_cap=0, series=True, heatbath=False, colours=3):
+              tie_tol=0.0, ties_cap=0, series=True, heatbath=False, colours=3, tie_info=False):
     """Sweeps (Metropolis, or heat-bath if heatbath) in place on theta; return
-    (E, |m|, near-ties (k,2) array, count).  Heat-bath only: colours = 1 or 2
-    runs just the pass of colour 0 or 1."""
+    (E, |m|, near-ties (k,2) array, count), and with tie_info=True (Metropolis)
+    also the (k,2) array of (margin, condition factor K) of each near-tie.
+    Heat-bath only: colours = 1 or 2 runs just the pass of colour 0 or 1."""
     assert theta.dtype == np.float64 and theta.flags.c_contiguous
     assert colours == 3 or heatbath
+    assert not (tie_info and heatbath)
     jb = _bonds_f32(Jb, d, L)
     E = np.empty(nsweeps) if series else None
     m = np.empty(nsweeps) if series else None
     ties = np.zeros((max(ties_cap, 1), 2), np.int64)
+    info = np.zeros((max(ties_cap, 1), 2)) if tie_info else None
     if heatbath:
         n = lib().orc_xy_heatbath_sweeps(d, L, J, _ptr(jb), beta, seed, replica, t0, nsweeps,
                                          colours, theta, _ptr(E), _ptr(m), tie_tol, _ptr(ties),
                                          ties_cap)
     else:
         n = lib().orc_xy_sweeps(d, L, J, _ptr(jb), beta, seed, replica, t0, nsweeps, theta,
-                                _ptr(E), _ptr(m), tie_tol, _ptr(ties), ties_cap)
-    return E, m, ties[:min(n, ties_cap)], n
+                                _ptr(E), _ptr(m), tie_tol, _ptr(ties), _ptr(info), ties_cap)
+    k = min(n, ties_cap)
+    if tie_info:
+        return E, m, ties[:k], n, info[:k]
+    return E, m, ties[:k], n
 
 
 def heis_sweeps(d, L, s, beta, seed, t0, nsweeps, J=1.0, Jb=None, replica=0,
                 renorm_every=16, tie_tol=0.0, ties_cap=0, series=True, heatbath=False,
-                colours=3):
+                colours=3, tie_info=False):
     """Sweeps (Metropolis, or heat-bath if heatbath) in place on s (N,3);
-    return (E, |m|, near-ties (k,2) array, count).  Heat-bath only: colours =
-    1 or 2 runs just the pass of colour 0 or 1."""
+    return (E, |m|, near-ties (k,2) array, count), and with tie_info=True
+    (Metropolis) also the (k,2) array of (margin, condition factor K) of each
+    near-tie.  Heat-bath only: colours = 1 or 2 runs just the pass of colour 0
+    or 1."""
     assert s.dtype == np.float64 and s.flags.c_contiguous
     assert colours == 3 or heatbath
+    assert not (tie_info and heatbath)
     jb = _bonds_f32(Jb, d, L)
     E = np.empty(nsweeps) if series else None
     m = np.empty(nsweeps) if series else None
     ties = np.zeros((max(ties_cap, 1), 2), np.int64)
+    info = np.zeros((max(ties_cap, 1), 2)) if tie_info else None
     if heatbath:
         n = lib().orc_heis_heatbath_sweeps(d, L, J, _ptr(jb), beta, seed, replica, t0, nsweeps,
                                            colours, renorm_every, s.reshape(-1), _ptr(E),
@@ -334,8 +344,11 @@ def heis_sweeps(d, L, s, beta, seed, t0, nsweeps, J=1.0, Jb=None, replica=0,
     else:
         n = lib().orc_heis_sweeps(d, L, J, _ptr(jb), beta, seed, replica, t0, nsweeps,
                                   renorm_every, s.reshape(-1), _ptr(E), _ptr(m), tie_tol,
-                                  _ptr(ties), ties_cap)
-    return E, m, ties[:min(n, ties_cap)], n
+                                  _ptr(ties), _ptr(info), ties_cap)
+    k = min(n, ties_cap)
+    if tie_info:
+        return E, m, ties[:k], n, info[:k]
+    return E, m, ties[:k], n
 
 
 # ------------------------------------------------------------ EA + PT -----

@@ -75,6 +75,24 @@ static void log_tie(int64_t* count, int64_t* ties, int64_t cap, int64_t t, int64
     ++*count;
 }
 
+/* A Metropolis near-tie with its margin |u - p| and the condition factor
+ * K = p (beta (A + |dE|) + 1), A = 2 sum_a |h_a| + sum_a |s'_a - s_a| sum_k |J_ik|
+ * (components a of the spin vectors; cos and sin of the angles for XY).  If
+ * every spin component, the field's inputs and the evaluation carry relative
+ * or absolute errors up to eps, then dE is off by at most eps (A + |dE|) and
+ * p by at most eps K, so a decision can only differ where the margin is below
+ * eps K: this is instrumentation for the caller's tolerance, not part of the
+ * method. */
+static void log_tie_info(int64_t* count, int64_t* ties, double* info, int64_t cap, int64_t t,
+                         int64_t i, double margin, double K)
+{
+    if (info && *count < cap) {
+        info[2 * *count] = margin;
+        info[2 * *count + 1] = K;
+    }
+    log_tie(count, ties, cap, t, i);
+}
+
 /* ---------------------------------------------------------------- XY ---- */
 
 void orc_xy_init(int d, int L, uint64_t seed, uint32_t replica, double* theta)
@@ -157,7 +175,7 @@ static int xy_heatbath_draw(double hx, double hy, double beta, const uint32_t ke
 static int64_t xy_sweeps(int d, int L, double J, const float* Jb, double beta, uint64_t seed,
                          uint32_t replica, int64_t t0, int64_t nsweeps, int heatbath,
                          int colours, double* theta, double* E_out, double* absm_out,
-                         double tie_tol, int64_t* ties, int64_t ties_cap)
+                         double tie_tol, int64_t* ties, double* tie_info, int64_t ties_cap)
 {
     orc_geom g = orc_make_geom(d, L);
     const uint32_t key[2] = {orc_key_lo(seed), orc_key_hi(seed)};
@@ -172,12 +190,13 @@ static int64_t xy_sweeps(int d, int L, double J, const float* Jb, double beta, u
                         int x[3] = {x0, y, z};
                         int64_t i = orc_index(&g, x);
                         int64_t j = i >> 1;
-                        double hx = 0.0, hy = 0.0;
+                        double hx = 0.0, hy = 0.0, jsum = 0.0;
                         for (int k = 0; k < 2 * d; ++k) {
                             int64_t nb = orc_neighbour_at(&g, x, k);
                             double jij = bond_j(&g, J, Jb, x, i, k);
                             hx += jij * cos(theta[nb]);
                             hy += jij * sin(theta[nb]);
+                            jsum += fabs(jij);
                         }
                         if (heatbath) {
                             int tie = 0;
@@ -198,7 +217,13 @@ static int64_t xy_sweeps(int d, int L, double J, const float* Jb, double beta, u
                         if (dE > 0.0) {
                             double p = exp(-beta * dE);
                             accept = u < p;
-                            if (fabs(u - p) < tie_tol) log_tie(&nties, ties, ties_cap, t, i);
+                            if (fabs(u - p) < tie_tol) {
+                                double A = 2.0 * (fabs(hx) + fabs(hy)) +
+                                           (fabs(cos(th_new) - cos(theta[i])) +
+                                            fabs(sin(th_new) - sin(theta[i]))) * jsum;
+                                log_tie_info(&nties, ties, tie_info, ties_cap, t, i, fabs(u - p),
+                                             p * (beta * (A + fabs(dE)) + 1.0));
+                            }
                         }
                         if (accept) theta[i] = th_new;
                     }
@@ -215,10 +240,10 @@ static int64_t xy_sweeps(int d, int L, double J, const float* Jb, double beta, u
 int64_t orc_xy_sweeps(int d, int L, double J, const float* Jb, double beta,
                       uint64_t seed, uint32_t replica, int64_t t0, int64_t nsweeps,
                       double* theta, double* E_out, double* absm_out,
-                      double tie_tol, int64_t* ties, int64_t ties_cap)
+                      double tie_tol, int64_t* ties, double* tie_info, int64_t ties_cap)
 {
     return xy_sweeps(d, L, J, Jb, beta, seed, replica, t0, nsweeps, 0, 3, theta, E_out,
-                     absm_out, tie_tol, ties, ties_cap);
+                     absm_out, tie_tol, ties, tie_info, ties_cap);
 }
 
 int64_t orc_xy_heatbath_sweeps(int d, int L, double J, const float* Jb, double beta,
@@ -227,7 +252,7 @@ int64_t orc_xy_heatbath_sweeps(int d, int L, double J, const float* Jb, double b
                                double tie_tol, int64_t* ties, int64_t ties_cap)
 {
     return xy_sweeps(d, L, J, Jb, beta, seed, replica, t0, nsweeps, 1, colours, theta, E_out,
-                     absm_out, tie_tol, ties, ties_cap);
+                     absm_out, tie_tol, ties, NULL, ties_cap);
 }
 
 /* -------------------------------------------------------- Heisenberg ---- */
@@ -322,7 +347,8 @@ static double heis_heatbath_draw(const double h[3], double beta, double u, doubl
 static int64_t heis_sweeps(int d, int L, double J, const float* Jb, double beta, uint64_t seed,
                            uint32_t replica, int64_t t0, int64_t nsweeps, int heatbath,
                            int colours, int renorm_every, double* s, double* E_out,
-                           double* absm_out, double tie_tol, int64_t* ties, int64_t ties_cap)
+                           double* absm_out, double tie_tol, int64_t* ties, double* tie_info,
+                           int64_t ties_cap)
 {
     orc_geom g = orc_make_geom(d, L);
     const uint32_t key[2] = {orc_key_lo(seed), orc_key_hi(seed)};
@@ -345,10 +371,12 @@ static int64_t heis_sweeps(int d, int L, double J, const float* Jb, double beta,
                         double u = orc_u24(out[0]);
                         double sn[3];
                         double h[3] = {0.0, 0.0, 0.0};
+                        double jsum = 0.0;
                         for (int k = 0; k < 2 * d; ++k) {
                             int64_t nb = orc_neighbour_at(&g, x, k);
                             double jij = bond_j(&g, J, Jb, x, i, k);
                             for (int a = 0; a < 3; ++a) h[a] += jij * s[3 * nb + a];
+                            jsum += fabs(jij);
                         }
                         int accept = 1;
                         if (heatbath) {
@@ -362,7 +390,13 @@ static int64_t heis_sweeps(int d, int L, double J, const float* Jb, double beta,
                         if (!heatbath && dE > 0.0) {
                             double p = exp(-beta * dE);
                             accept = u < p;
-                            if (fabs(u - p) < tie_tol) log_tie(&nties, ties, ties_cap, t, i);
+                            if (fabs(u - p) < tie_tol) {
+                                double A = 0.0;
+                                for (int a = 0; a < 3; ++a)
+                                    A += 2.0 * fabs(h[a]) + fabs(sn[a] - s[3 * i + a]) * jsum;
+                                log_tie_info(&nties, ties, tie_info, ties_cap, t, i, fabs(u - p),
+                                             p * (beta * (A + fabs(dE)) + 1.0));
+                            }
                         }
                         if (accept)
                             for (int a = 0; a < 3; ++a) s[3 * i + a] = sn[a];
@@ -386,10 +420,10 @@ static int64_t heis_sweeps(int d, int L, double J, const float* Jb, double beta,
 int64_t orc_heis_sweeps(int d, int L, double J, const float* Jb, double beta,
                         uint64_t seed, uint32_t replica, int64_t t0, int64_t nsweeps,
                         int renorm_every, double* s, double* E_out, double* absm_out,
-                        double tie_tol, int64_t* ties, int64_t ties_cap)
+                        double tie_tol, int64_t* ties, double* tie_info, int64_t ties_cap)
 {
     return heis_sweeps(d, L, J, Jb, beta, seed, replica, t0, nsweeps, 0, 3, renorm_every, s,
-                       E_out, absm_out, tie_tol, ties, ties_cap);
+                       E_out, absm_out, tie_tol, ties, tie_info, ties_cap);
 }
 
 int64_t orc_heis_heatbath_sweeps(int d, int L, double J, const float* Jb, double beta,
@@ -399,5 +433,5 @@ int64_t orc_heis_heatbath_sweeps(int d, int L, double J, const float* Jb, double
                                  int64_t ties_cap)
 {
     return heis_sweeps(d, L, J, Jb, beta, seed, replica, t0, nsweeps, 1, colours, renorm_every, s,
-                       E_out, absm_out, tie_tol, ties, ties_cap);
+                       E_out, absm_out, tie_tol, ties, NULL, ties_cap);
 }

@@ -152,18 +152,22 @@ void orc_heis_measure(int d, int L, double J, const float* Jb, const double* s,
                       double* E, double* M);
 
 /* Decisions whose margin |u - exp(-beta dE)| is below tie_tol are recorded as
- * (t, site) pairs in ties[2*k], ties[2*k+1] for k < ties_cap; the return value
+ * (t, site) pairs in ties[2*k], ties[2*k+1] for k < ties_cap, and, if tie_info
+ * is not NULL, as (margin, K) in tie_info[2*k], tie_info[2*k+1] with the
+ * condition factor K = p (beta (A + |dE|) + 1), A = 2 sum_a |h_a| +
+ * sum_a |s'_a - s_a| sum_k |J_ik| (an evaluation whose spin components and
+ * operations err by at most eps moves p by at most eps K); the return value
  * is the total number of such near-ties.  E_out / absm_out as for Ising.
  * renorm_every > 0 renormalises each spin of the colour being updated right
  * after its decision in every sweep t with (t+1) % renorm_every == 0. */
 int64_t orc_xy_sweeps(int d, int L, double J, const float* Jb, double beta,
                       uint64_t seed, uint32_t replica, int64_t t0, int64_t nsweeps,
                       double* theta, double* E_out, double* absm_out,
-                      double tie_tol, int64_t* ties, int64_t ties_cap);
+                      double tie_tol, int64_t* ties, double* tie_info, int64_t ties_cap);
 int64_t orc_heis_sweeps(int d, int L, double J, const float* Jb, double beta,
                         uint64_t seed, uint32_t replica, int64_t t0, int64_t nsweeps,
                         int renorm_every, double* s, double* E_out, double* absm_out,
-                        double tie_tol, int64_t* ties, int64_t ties_cap);
+                        double tie_tol, int64_t* ties, double* tie_info, int64_t ties_cap);
 
 /* Heat-bath sweeps (Section 2: each spin drawn from its conditional law given
  * its neighbours), same arguments plus `colours`: bit c set runs the pass of

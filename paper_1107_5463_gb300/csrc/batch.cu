@@ -51,6 +51,7 @@ struct BatchArgs {
     unsigned* counter;          // next queue entry
     const long long* word_off;  // per sample: first spin word (colour 0), colour 1 at + H
     int d, ntemps;
+    uint32_t sample0;  // global index of sample 0 (Philox counters use global indices)
     long long t0;
     int nsweeps;
     RoundKeys rk;
@@ -134,6 +135,7 @@ __device__ void run_sample(const BatchArgs& a, int s, int L, unsigned char* base
     int* sot = unsat + kMaxTemps;  // slot of temperature
     const int lane = tid & 31, warp = tid >> 5;
     const uint32_t active = nt == 32 ? 0xFFFFFFFFu : ((1u << nt) - 1u);
+    const uint32_t gs = a.sample0 + (uint32_t)s;  // the sample's global index
 
     // load the sample
     const long long w0 = a.word_off[s];
@@ -171,7 +173,7 @@ __device__ void run_sample(const BatchArgs& a, int s, int L, unsigned char* base
                 for (int r = 0; r < kMaxTemps; ++r) {
                     if (r < nt) {
                         const uint4 rnd = philox4x32_10(
-                            make_uint4((uint32_t)g, (uint32_t)t, (uint32_t)(s * nt + r), ctr_w), a.rk);
+                            make_uint4((uint32_t)g, (uint32_t)t, gs * (uint32_t)nt + (uint32_t)r, ctr_w), a.rk);
                         const uint4 th = thr_slot[r];
                         const uint32_t u[4] = {rnd.x, rnd.y, rnd.z, rnd.w};
 #pragma unroll
@@ -261,7 +263,7 @@ __device__ void run_sample(const BatchArgs& a, int s, int L, unsigned char* base
                 if (!accept) {
                     const long long m = (dE < 0 ? -dE : dE) >> 1;
                     const uint4 rnd = philox4x32_10(
-                        make_uint4((uint32_t)k, (uint32_t)t, (uint32_t)s, kExchange << 1), a.rk);
+                        make_uint4((uint32_t)k, (uint32_t)t, gs, kExchange << 1), a.rk);
                     if (m < pm.m1) accept = rnd.x <= a.pt_tab[pm.off + m];
                     else if (m < pm.m0) accept = rnd.x == 0u;
                 }
@@ -307,9 +309,10 @@ __global__ void __launch_bounds__(1024) ea_pt_persistent(const BatchArgs a)
 
 __global__ void batch_init_kernel(uint32_t* spins, uint8_t* bonds, int32_t* perm,
                                   const int* Ls, const long long* word_off, int d, int ntemps,
-                                  RoundKeys rk)
+                                  uint32_t sample0, RoundKeys rk)
 {
     const int s = blockIdx.x;
+    const uint32_t gs = sample0 + (uint32_t)s;
     const int L = Ls[s];
     const int N = d == 3 ? L * L * L : L * L;
     const int H = N / 2;
@@ -321,7 +324,7 @@ __global__ void batch_init_kernel(uint32_t* spins, uint8_t* bonds, int32_t* perm
         uint8_t bits = 0;
         for (int mu = 0; mu < d; ++mu) {
             const uint4 r = philox4x32_10(
-                make_uint4((uint32_t)i, (uint32_t)mu, (uint32_t)s, kCoupling << 1), rk);
+                make_uint4((uint32_t)i, (uint32_t)mu, gs, kCoupling << 1), rk);
             if (!(r.x >> 31)) bits |= (uint8_t)(1u << mu);
         }
         B[c * H + (i >> 1)] = bits;
@@ -331,7 +334,8 @@ __global__ void batch_init_kernel(uint32_t* spins, uint8_t* bonds, int32_t* perm
         uint32_t w[4] = {0, 0, 0, 0};
         for (int r = 0; r < ntemps; ++r) {
             const uint4 o = philox4x32_10(
-                make_uint4((uint32_t)g, 0u, (uint32_t)(s * ntemps + r), (kInit << 1) | (uint32_t)c),
+                make_uint4((uint32_t)g, 0u, gs * (uint32_t)ntemps + (uint32_t)r,
+                           (kInit << 1) | (uint32_t)c),
                 rk);
             const uint32_t u[4] = {o.x, o.y, o.z, o.w};
             for (int b = 0; b < 4; ++b)
@@ -361,6 +365,21 @@ __global__ void batch_gather_kernel(const uint32_t* spins, const uint8_t* bonds,
     }
 }
 
+// Sets bit `slot` of every site word of one sample from a natural-order
+// +-1 configuration (1 = down); the other slots' bits are kept.
+__global__ void batch_scatter_kernel(uint32_t* spins, const int8_t* nat, long long w0, int L,
+                                     int d, int slot)
+{
+    const int N = d == 3 ? L * L * L : L * L;
+    const int H = N / 2;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        const int x = i % L, y = (i / L) % L, z = i / (L * L);
+        const int c = (x + y + z) & 1;
+        uint32_t* w = spins + w0 + c * H + (i >> 1);
+        *w = (*w & ~(1u << slot)) | ((nat[i] < 0 ? 1u : 0u) << slot);
+    }
+}
+
 size_t smem_bytes(int d, int L)
 {
     const int N = d == 3 ? L * L * L : L * L;
@@ -377,6 +396,7 @@ using namespace spinmc;
 
 struct sl_batch {
     int d, nsamples, ntemps;
+    uint32_t sample0;  // global index of the batch's first sample
     std::vector<int> L;
     std::vector<long long> word_off;
     std::vector<int> class_L;                 // distinct sizes, largest first
@@ -582,6 +602,7 @@ BatchArgs base_args(const sl_batch* b)
     a.counter = b->counter;
     a.d = b->d;
     a.ntemps = b->ntemps;
+    a.sample0 = b->sample0;
     a.thr_temp = b->thr_temp;
     a.pt_tab = b->pt_tab;
     a.pt_meta = b->pt_meta;
@@ -804,14 +825,16 @@ int sl_batch_required_bytes(int d, const int* L_per_sample, int nsamples, int nt
 }
 
 int sl_batch_create(int d, const int* L_per_sample, int nsamples, int ntemps, const double* betas,
-                    uint64_t seed, void* dev_buf, size_t dev_buf_bytes, void* stream,
-                    sl_batch** out)
+                    uint64_t seed, uint32_t first_sample, void* dev_buf, size_t dev_buf_bytes,
+                    void* stream, sl_batch** out)
 {
     if (!out) return fail(SL_EINVAL, "out is NULL");
     *out = nullptr;
     if (!betas) return fail(SL_EINVAL, "betas is NULL");
     int st = batch_check(d, L_per_sample, nsamples, ntemps, betas);
     if (st != SL_OK) return st;
+    if (((uint64_t)first_sample + (uint64_t)nsamples) * (uint64_t)ntemps > 4294967296ULL)
+        return fail(SL_EINVAL, "global replica ids (first_sample + nsamples) * ntemps exceed 2^32");
     const BatchLayout y = batch_layout(d, L_per_sample, nsamples, ntemps, betas);
     void* owned = nullptr;
     if (!dev_buf) {
@@ -834,6 +857,7 @@ int sl_batch_create(int d, const int* L_per_sample, int nsamples, int ntemps, co
     b->d = d;
     b->nsamples = nsamples;
     b->ntemps = ntemps;
+    b->sample0 = first_sample;
     b->L.assign(L_per_sample, L_per_sample + nsamples);
     b->word_off.resize(nsamples);
     long long w = 0;
@@ -928,7 +952,7 @@ int sl_batch_create(int d, const int* L_per_sample, int nsamples, int ntemps, co
         e = cudaMemcpyAsync(b->pt_tab, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice, s0);
     if (e == cudaSuccess) {
         batch_init_kernel<<<nsamples, 256, 0, s0>>>(b->spins, b->bonds, b->perm, b->Ls_dev,
-                                                   b->word_off_dev, d, ntemps,
+                                                   b->word_off_dev, d, ntemps, first_sample,
                                                    make_round_keys(seed));
         e = cudaGetLastError();
     }
@@ -1052,6 +1076,49 @@ int sl_batch_sweeps_done(sl_batch* b, int64_t* sweeps_done)
 {
     if (!b || !sweeps_done) return fail(SL_EINVAL, "NULL argument");
     *sweeps_done = b->sweeps_done;
+    return SL_OK;
+}
+
+int sl_batch_set(sl_batch* b, int sample, const int8_t* spins, const int32_t* slot_of_temp)
+{
+    if (!b || !spins || !slot_of_temp) return fail(SL_EINVAL, "NULL argument");
+    if (sample < 0 || sample >= b->nsamples) return fail(SL_EINVAL, "sample out of range");
+    const int nt = b->ntemps;
+    unsigned seen = 0;
+    for (int k = 0; k < nt; ++k) {
+        const int r = slot_of_temp[k];
+        if (r < 0 || r >= nt || (seen >> r) & 1u)
+            return fail(SL_EINVAL, "slot_of_temp is not a permutation of 0..%d", nt - 1);
+        seen |= 1u << r;
+    }
+    int32_t perm[kMaxTemps];
+    for (int k = 0; k < kMaxTemps; ++k) perm[k] = k < nt ? slot_of_temp[k] : k;
+    const int L = b->L[sample];
+    const long long N = (long long)L * L * (b->d == 3 ? L : 1);
+    cudaError_t e = cudaSuccess;
+    for (int r = 0; r < nt && e == cudaSuccess; ++r) {
+        e = cudaMemcpyAsync(b->staging, spins + (size_t)r * N, (size_t)N, cudaMemcpyDefault,
+                            b->stream);
+        if (e == cudaSuccess) {
+            batch_scatter_kernel<<<(int)((N + 255) / 256), 256, 0, b->stream>>>(
+                b->spins, b->staging, b->word_off[sample], L, b->d, r);
+            e = cudaGetLastError();
+        }
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->perm + sample * kMaxTemps, perm, sizeof perm,
+                            cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "sl_batch_set");
+    return SL_OK;
+}
+
+int sl_batch_set_sweeps_done(sl_batch* b, int64_t sweeps_done)
+{
+    if (!b) return fail(SL_EINVAL, "batch is NULL");
+    if (sweeps_done < 0 || sweeps_done > 4294967296LL)
+        return fail(SL_EINVAL, "sweeps_done out of range");
+    b->sweeps_done = sweeps_done;
     return SL_OK;
 }
 

@@ -44,6 +44,7 @@ struct sl_lattice {
     int d, L, n, j_layout, storage;
     int64_t N, H;            // sites, sites per colour
     int W;                   // sites of one colour in one row (L / 2)
+    int sms;                 // multiprocessors of the device the handle was created on
     double J;
     uint64_t init_seed;
     uint32_t replica;
@@ -62,8 +63,8 @@ struct sl_lattice {
     int renorm_every, fast_math, kernel, rows, use_graph;
     int update;              // SL_UPDATE_METROPOLIS, _HEATBATH or _SW
     int multihit, tile;      // k-fold multi-hit sweeps in tiles of side `tile` (0 = off)
-    // cached graph of kGraphSweeps sweeps
-    cudaGraphExec_t graph;
+    // cached graphs of kGraphSweeps sweeps and of one sweep
+    cudaGraphExec_t graph, graph1;
     int graph_sweeps;
     uint64_t graph_key[4];
     void* owned_buf;

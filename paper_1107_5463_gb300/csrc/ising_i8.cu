@@ -556,7 +556,7 @@ int pick_rows(const sl_lattice* h)
     const long long W16 = h->W / 16;
     const long long cross = h->d == 3 ? h->L : 1;
     int R = h->d == 3 ? 8 : 16;
-    while (R > 1 && (h->L % R != 0 || W16 * cross * (h->L / R) < 152LL * 512)) R >>= 1;
+    while (R > 1 && (h->L % R != 0 || W16 * cross * (h->L / R) < (long long)h->sms * 512)) R >>= 1;
     return R;
 }
 

@@ -31,7 +31,7 @@ int cuda_fail(cudaError_t e, const char* what)
 
 namespace {
 
-constexpr int kGraphSweeps = 32;
+constexpr int kGraphSweeps = 32;  // sweeps in the long graph; a one-sweep graph takes the rest
 
 struct Layout {
     size_t spin_colour;   // bytes of one colour's spins
@@ -181,6 +181,40 @@ int model_sweeps(const sl_lattice* h, const SweepParams& p, int64_t count, cudaS
     return e == cudaSuccess ? SL_OK : cuda_fail(e, "sweep launch");
 }
 
+// Capture `count` sweeps into an executable graph on the private capture stream.
+int capture_sweeps(sl_lattice* h, const SweepParams& p, int count, cudaGraphExec_t* out)
+{
+    *out = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+    const int st = model_sweeps(h, p, count, h->cap_stream);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(h->cap_stream, &g);
+    if (st != SL_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        *out = nullptr;
+        return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    return SL_OK;
+}
+
+void drop_graphs(sl_lattice* h)
+{
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    if (h->graph1) cudaGraphExecDestroy(h->graph1);
+    h->graph = h->graph1 = nullptr;
+}
+
+// The two graphs of the sweep parameters p (kGraphSweeps sweeps and one
+// sweep), captured again only when p or an option that shapes the launches
+// has changed.  The kernels read the sweep index and the series pointers
+// from the device control block, so one capture serves every later call.
 int ensure_graph(sl_lattice* h, const SweepParams& p)
 {
     uint64_t key[4];
@@ -190,26 +224,13 @@ int ensure_graph(sl_lattice* h, const SweepParams& p)
              ((uint64_t)h->fast_math << 24) ^ ((uint64_t)h->update << 40) ^
              (uint64_t)h->renorm_every;
     key[3] = ((uint64_t)h->multihit << 16) ^ (uint64_t)h->tile;
-    if (h->graph && std::memcmp(key, h->graph_key, sizeof key) == 0) return SL_OK;
-    if (h->graph) {
-        cudaGraphExecDestroy(h->graph);
-        h->graph = nullptr;
-    }
-    cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
-    const int st = model_sweeps(h, p, kGraphSweeps, h->cap_stream);
-    cudaGraph_t g = nullptr;
-    e = cudaStreamEndCapture(h->cap_stream, &g);
+    if (h->graph && h->graph1 && std::memcmp(key, h->graph_key, sizeof key) == 0) return SL_OK;
+    drop_graphs(h);
+    int st = capture_sweeps(h, p, kGraphSweeps, &h->graph);
+    if (st == SL_OK) st = capture_sweeps(h, p, 1, &h->graph1);
     if (st != SL_OK) {
-        if (g) cudaGraphDestroy(g);
+        drop_graphs(h);
         return st;
-    }
-    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(&h->graph, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) {
-        h->graph = nullptr;
-        return cuda_fail(e, "cudaGraphInstantiate");
     }
     h->graph_sweeps = kGraphSweeps;
     std::memcpy(h->graph_key, key, sizeof key);
@@ -288,6 +309,14 @@ int sl_create(int d, int L, int n, int j_layout, int storage, double J, const vo
     h->replica = replica;
     h->sweeps_done = 0;
     h->stream = (cudaStream_t)stream;
+    {
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            sms < 1)
+            sms = 1;
+        h->sms = sms;
+    }
     for (int c = 0; c < 2; ++c) {
         h->spins[c] = base + y.off_spins[c];
         for (int mu = 0; mu < 3; ++mu)
@@ -308,6 +337,7 @@ int sl_create(int d, int L, int n, int j_layout, int storage, double J, const vo
     h->multihit = 0;
     h->tile = 16;
     h->graph = nullptr;
+    h->graph1 = nullptr;
     h->graph_sweeps = 0;
     h->owned_buf = owned;
     h->ws = nullptr;
@@ -379,13 +409,15 @@ int sl_sweep_series(sl_lattice* h, double beta, int64_t nsweeps, uint64_t seed, 
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "series setup");
     int64_t left = nsweeps;
-    if (h->use_graph && nsweeps >= 2 * kGraphSweeps) {
+    if (h->use_graph && nsweeps >= 2) {
+        // whole runs of kGraphSweeps sweeps, then single-sweep replays
         const int st = ensure_graph(h, p);
         if (st != SL_OK) return st;
-        while (left >= h->graph_sweeps) {
-            e = cudaGraphLaunch(h->graph, h->stream);
+        while (left > 0) {
+            const bool big = left >= h->graph_sweeps;
+            e = cudaGraphLaunch(big ? h->graph : h->graph1, h->stream);
             if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
-            left -= h->graph_sweeps;
+            left -= big ? h->graph_sweeps : 1;
         }
     }
     if (left > 0) {
@@ -565,7 +597,7 @@ void sl_destroy(sl_lattice* h)
 {
     if (!h) return;
     cudaStreamSynchronize(h->stream);
-    if (h->graph) cudaGraphExecDestroy(h->graph);
+    drop_graphs(h);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->owned_buf) cudaFree(h->owned_buf);
     if (h->ws_owned) cudaFree(h->ws_owned);
@@ -597,10 +629,7 @@ int sl_attach_workspace(sl_lattice* h, void* dev_buf, size_t bytes)
     }
     h->ws = dev_buf;
     h->ws_bytes = dev_buf ? bytes : 0;
-    if (h->graph) {
-        cudaGraphExecDestroy(h->graph);
-        h->graph = nullptr;
-    }
+    drop_graphs(h);
     return SL_OK;
 }
 

@@ -1082,7 +1082,7 @@ int on_rows(const sl_lattice* h, long long cols)
     if (h->rows > 0) return h->rows;
     const long long cross = h->d == 3 ? h->L : 1;
     int R = 32;
-    while (R > 1 && (h->L % R != 0 || cols * cross * (h->L / R) < 152LL * 1024)) R >>= 1;
+    while (R > 1 && (h->L % R != 0 || cols * cross * (h->L / R) < (long long)h->sms * 1024)) R >>= 1;
     return R;
 }
 
@@ -1138,7 +1138,8 @@ cudaError_t launch_on(const sl_lattice* h, OnArgs a, cudaStream_t s)
         return cudaGetLastError();
     }
     const long long rows = (long long)h->L * (h->d == 3 ? h->L : 1);
-    int grid = (int)(rows < 152LL * 8 ? rows : 152LL * 8);
+    const long long cap = (long long)h->sms * 8;
+    int grid = (int)(rows < cap ? rows : cap);
     if (grid > kMaxBlocks) grid = kMaxBlocks;
     if (h->d == 2) {
         if (var == 2) on_generic<NC, 2, false, true><<<grid, 128, 0, s>>>(a);

@@ -14,8 +14,17 @@
 // that overlap on the GPU (on different streams, or from different threads)
 // race; calls issued one after another on a stream are safe.  The arrival
 // counter is cleared at the start of every call.
+//
+// The host needs the array's device address, which it looks up with the
+// device current on the first call there.  The address belongs to the
+// device's context: after cudaDeviceReset a new context loads the module
+// again, possibly elsewhere, so the cache keys each address by the context's
+// unique id and looks the address up again when the id changes.
 #include <cmath>
 #include <mutex>
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
 
 #include "internal.h"
 
@@ -36,8 +45,9 @@ static __device__ __align__(256) StaticScratch g_static_scratch;
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 StaticScratch* g_scratch_addr[kMaxDevices];
+unsigned long long g_scratch_ctx[kMaxDevices];  // context id the address belongs to
 
-// E = -J sum_i sum_mu s_i s_{i+e_mu} (Eq. 1) and M = sum_i s_i of a
+// E = -J sum_i sum_mu s_i s_{i+e_mu} (nearest-neighbour pairs, each once) and M = sum_i s_i of a
 // natural-order +-1 configuration; block b reduces sites
 // [b * kStaticSitesPerBlock, (b + 1) * kStaticSitesPerBlock).
 __global__ void __launch_bounds__(256) static_measure_kernel(const int8_t* s, long long N, int L,
@@ -71,20 +81,50 @@ __global__ void __launch_bounds__(256) static_measure_kernel(const int8_t* s, lo
     });
 }
 
-// Device address of the static scratch on the current device, looked up once
-// per device with that device current.
+// The driver's cuCtxGetId, fetched through the runtime (no link against the
+// driver library), or null where the driver does not offer it.
+PFN_cuCtxGetId_v12000 ctx_get_id_fn()
+{
+    static PFN_cuCtxGetId_v12000 fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return (PFN_cuCtxGetId_v12000)p;
+    }();
+    return fn;
+}
+
+// Unique id of the current context, or 0 if there is none yet (or no way to ask).
+unsigned long long current_ctx_id()
+{
+    unsigned long long id = 0;
+    const PFN_cuCtxGetId_v12000 fn = ctx_get_id_fn();
+    if (!fn || fn(nullptr, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+// Device address of the static scratch on the current device.  It is looked
+// up (cudaGetSymbolAddress, with the device current) on the first call on a
+// device and again only when the device's context has changed since, as
+// after cudaDeviceReset.
 int scratch_for_current_device(StaticScratch** out)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
     if (dev < 0 || dev >= kMaxDevices) return fail(SL_EINVAL, "device %d out of range", dev);
+    unsigned long long ctx = current_ctx_id();
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_addr[dev]) {
+    if (!g_scratch_addr[dev] || ctx == 0 || g_scratch_ctx[dev] != ctx) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_static_scratch);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
+        if (ctx == 0) ctx = current_ctx_id();  // the lookup made the primary context current
         g_scratch_addr[dev] = (StaticScratch*)p;
+        g_scratch_ctx[dev] = ctx;
     }
     *out = g_scratch_addr[dev];
     return SL_OK;
@@ -102,11 +142,13 @@ extern "C" int sl_ising_measure_static(int d, int L, double J, const int8_t* dev
     if (L < 2 || (L & 1)) return fail(SL_EINVAL, "L must be even and >= 2 (got %d)", L);
     if (!dev_spins || !dev_out) return fail(SL_EINVAL, "NULL device pointer");
     if (!std::isfinite(J)) return fail(SL_EINVAL, "J must be finite");
-    const long long N = (long long)L * L * (d == 3 ? L : 1);
-    if (N > kStaticMaxSites)
+    // the site count in FP64 first: L^3 overflows 64-bit integers for L near 2^21
+    const double Nd = std::pow((double)L, d);
+    if (Nd > (double)kStaticMaxSites)
         return fail(SL_EINVAL,
-                    "%lld sites exceed the %lld this entry point's static scratch serves",
-                    N, kStaticMaxSites);
+                    "%.0f sites exceed the %lld this entry point's static scratch serves",
+                    Nd, kStaticMaxSites);
+    const long long N = (long long)L * L * (d == 3 ? L : 1);
     StaticScratch* scr = nullptr;
     const int st = scratch_for_current_device(&scr);
     if (st != SL_OK) return st;

@@ -283,6 +283,28 @@ __global__ void walk_gather_kernel(const uint32_t* spins, long long N, int walke
         nat[i] = ((col[i] >> (walker & 31)) & 1u) ? (int8_t)-1 : (int8_t)1;
 }
 
+// Writes one walker's bit of every site word from a natural-order +-1
+// configuration (1 = down; the other walkers' bits are kept) and sets the
+// walker's level to k = (E + 2N) / 4 of that configuration (one block).
+__global__ void __launch_bounds__(256) walk_scatter_kernel(uint32_t* spins, const int8_t* nat,
+                                                           long long N, int L, int log2L,
+                                                           int walker, int32_t* level)
+{
+    __shared__ long long red[32];
+    uint32_t* col = spins + (size_t)(walker >> 5) * (size_t)N;
+    const uint32_t bit = 1u << (walker & 31);
+    long long bond = 0;
+    for (long long i = threadIdx.x; i < N; i += blockDim.x) {
+        col[i] = (col[i] & ~bit) | (nat[i] < 0 ? bit : 0u);
+        const int x = (int)(i & (L - 1)), y = (int)(i >> log2L);
+        const long long xp = (long long)y * L + ((x + 1) & (L - 1));
+        const long long yp = (long long)((y + 1) & (L - 1)) * L + x;
+        bond += (long long)nat[i] * (nat[xp] + nat[yp]);
+    }
+    const long long tot = block_sum(bond, red);
+    if (threadIdx.x == 0) level[walker] = (int32_t)((-tot + 2 * N) / 4);
+}
+
 struct WalkLayout {
     size_t off_spins, off_level, off_stage, off_visited, off_S, off_H, off_klo, off_khi, off_thr,
         off_err, off_nat, total;
@@ -643,6 +665,72 @@ int sl_walkers_get_spins(sl_walkers* w, int walker, int8_t* dst)
     if (e == cudaSuccess) e = cudaMemcpyAsync(dst, nat, (size_t)w->N, cudaMemcpyDefault, w->stream);
     if (e != cudaSuccess) return cuda_fail(e, "sl_walkers_get_spins");
     return walk_sync(w);
+}
+
+int sl_walkers_set_spins(sl_walkers* w, int walker, const int8_t* src)
+{
+    if (!w || !src) return fail(SL_EINVAL, "NULL argument");
+    if (walker < 0 || walker >= w->nwalk) return fail(SL_EINVAL, "walker %d out of range", walker);
+    int8_t* nat = (int8_t*)(w->base + w->y.off_nat);
+    int32_t* level = (int32_t*)(w->base + w->y.off_level);
+    cudaError_t e = cudaMemcpyAsync(nat, src, (size_t)w->N, cudaMemcpyDefault, w->stream);
+    if (e == cudaSuccess) {
+        walk_scatter_kernel<<<1, 256, 0, w->stream>>>((uint32_t*)(w->base + w->y.off_spins), nat,
+                                                       w->N, w->L, w->log2L, walker, level);
+        e = cudaGetLastError();
+    }
+    int32_t k = -1;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&k, level + walker, sizeof k, cudaMemcpyDeviceToHost, w->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(w->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "sl_walkers_set_spins");
+    const int win = walker / w->wpw;
+    if (k < w->klo_host[win] || k > w->khi_host[win])
+        return fail(SL_EINVAL, "walker %d: the configuration's level %d lies outside its window "
+                               "[%d, %d]", walker, k, w->klo_host[win], w->khi_host[win]);
+    return SL_OK;
+}
+
+int sl_walkers_write(sl_walkers* w, const int64_t* S, const uint32_t* H, const int32_t* stage,
+                     const uint64_t* visited)
+{
+    if (!w) return fail(SL_EINVAL, "walkers handle is NULL");
+    int st = walk_sync(w);
+    if (st != SL_OK) return st;
+    const size_t nw = (size_t)w->nwalk, km = (size_t)w->kmax;
+    cudaError_t e = cudaSuccess;
+    if (stage) e = cudaMemcpy(w->base + w->y.off_stage, stage, nw * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && visited)
+        e = cudaMemcpy(w->base + w->y.off_visited, visited, nw * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && (S || H)) {
+        // the caller's arrays are [walker][level]; the device keeps [level][walker]
+        char* tmp = new (std::nothrow) char[km * nw * 8];
+        if (!tmp) return fail(SL_ENOMEM, "host allocation failed");
+        if (S) {
+            int64_t* dst = (int64_t*)tmp;
+            for (size_t q = 0; q < km; ++q)
+                for (size_t j = 0; j < nw; ++j) dst[q * nw + j] = S[j * km + q];
+            e = cudaMemcpy(w->base + w->y.off_S, tmp, km * nw * 8, cudaMemcpyHostToDevice);
+        }
+        if (e == cudaSuccess && H) {
+            uint32_t* dst = (uint32_t*)tmp;
+            for (size_t q = 0; q < km; ++q)
+                for (size_t j = 0; j < nw; ++j) dst[q * nw + j] = H[j * km + q];
+            e = cudaMemcpy(w->base + w->y.off_H, tmp, km * nw * 4, cudaMemcpyHostToDevice);
+        }
+        delete[] tmp;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "sl_walkers_write");
+    return SL_OK;
+}
+
+int sl_walkers_set_sweeps_done(sl_walkers* w, int64_t sweeps_done)
+{
+    if (!w) return fail(SL_EINVAL, "walkers handle is NULL");
+    if (sweeps_done < 0 || sweeps_done > 4294967295LL)
+        return fail(SL_EINVAL, "sweeps_done out of range");
+    w->sweeps_done = sweeps_done;
+    return SL_OK;
 }
 
 int sl_walkers_set_option(sl_walkers* w, int option, int64_t value)

@@ -60,11 +60,14 @@ _sig("sl_destroy", None, _vp)
 _sig("sl_workspace_bytes", _int, _vp, _int, ctypes.POINTER(_sz))
 _sig("sl_attach_workspace", _int, _vp, _vp, _sz)
 _sig("sl_batch_required_bytes", _int, _int, _vp, _int, _int, _vp, ctypes.POINTER(_sz))
-_sig("sl_batch_create", _int, _int, _vp, _int, _int, _vp, _u64, _vp, _sz, _vp, ctypes.POINTER(_vp))
+_sig("sl_batch_create", _int, _int, _vp, _int, _int, _vp, _u64, _u32, _vp, _sz, _vp,
+     ctypes.POINTER(_vp))
 _sig("sl_batch_run", _int, _vp, _i64, _u64, _vp)
 _sig("sl_batch_get", _int, _vp, _int, _int, _vp, ctypes.POINTER(_int))
 _sig("sl_batch_get_bonds", _int, _vp, _int, _vp)
 _sig("sl_batch_sweeps_done", _int, _vp, ctypes.POINTER(_i64))
+_sig("sl_batch_set", _int, _vp, _int, _vp, _vp)
+_sig("sl_batch_set_sweeps_done", _int, _vp, _i64)
 _sig("sl_batch_destroy", None, _vp)
 _sig("sl_batch_set_option", _int, _vp, _int, _i64)
 _sig("sl_batch_tuning", _int, _vp, _int, ctypes.POINTER(_int), ctypes.POINTER(_int),
@@ -79,6 +82,9 @@ _sig("sl_wl_run", _int, _vp, _i64, _int, _int, _u64)
 _sig("sl_muca_run", _int, _vp, _vp, _i64, _u64)
 _sig("sl_walkers_read", _int, _vp, _vp, _vp, _vp, _vp, _vp)
 _sig("sl_walkers_get_spins", _int, _vp, _int, _vp)
+_sig("sl_walkers_set_spins", _int, _vp, _int, _vp)
+_sig("sl_walkers_write", _int, _vp, _vp, _vp, _vp, _vp)
+_sig("sl_walkers_set_sweeps_done", _int, _vp, _i64)
 _sig("sl_walkers_info", _int, _vp, ctypes.POINTER(_int), ctypes.POINTER(_int),
      ctypes.POINTER(_i64))
 _sig("sl_walkers_destroy", None, _vp)
@@ -204,12 +210,13 @@ def sl_batch_required_bytes(d, L_per_sample, ntemps, betas):
     return out.value
 
 
-def sl_batch_create(d, L_per_sample, ntemps, betas, seed, dev_buf, dev_buf_bytes, stream):
+def sl_batch_create(d, L_per_sample, ntemps, betas, seed, first_sample, dev_buf, dev_buf_bytes,
+                    stream):
     Ls, pL = _i32_array(L_per_sample)
     bs, pb = _f64_array(betas)
     h = _vp()
-    _check(_lib.sl_batch_create(d, pL, Ls.size, ntemps, pb, seed, _addr(dev_buf), dev_buf_bytes,
-                                stream, ctypes.byref(h)), "sl_batch_create")
+    _check(_lib.sl_batch_create(d, pL, Ls.size, ntemps, pb, seed, first_sample, _addr(dev_buf),
+                                dev_buf_bytes, stream, ctypes.byref(h)), "sl_batch_create")
     return h.value
 
 
@@ -231,6 +238,16 @@ def sl_batch_sweeps_done(h):
     t = _i64()
     _check(_lib.sl_batch_sweeps_done(h, ctypes.byref(t)), "sl_batch_sweeps_done")
     return t.value
+
+
+def sl_batch_set(h, sample, spins, slot_of_temp):
+    """Load a sample's slots (ntemps x N int8 +-1) and slot-of-temperature map."""
+    perm, pp = _i32_array(slot_of_temp)
+    _check(_lib.sl_batch_set(h, sample, _addr(spins), pp), "sl_batch_set")
+
+
+def sl_batch_set_sweeps_done(h, sweeps_done):
+    _check(_lib.sl_batch_set_sweeps_done(h, sweeps_done), "sl_batch_set_sweeps_done")
 
 
 def sl_batch_destroy(h):
@@ -330,6 +347,23 @@ def sl_walkers_read(h):
 
 def sl_walkers_get_spins(h, walker, dst):
     _check(_lib.sl_walkers_get_spins(h, walker, _addr(dst)), "sl_walkers_get_spins")
+
+
+def sl_walkers_set_spins(h, walker, src):
+    _check(_lib.sl_walkers_set_spins(h, walker, _addr(src)), "sl_walkers_set_spins")
+
+
+def sl_walkers_write(h, S=None, H=None, stage=None, visited=None):
+    """Set S, H ([walker][kmax]), stages and visited masks (None keeps one)."""
+    arrs = []
+    for a, dt in ((S, np.int64), (H, np.uint32), (stage, np.int32), (visited, np.uint64)):
+        arrs.append(None if a is None else np.ascontiguousarray(a, dt))
+    _check(_lib.sl_walkers_write(h, *[None if a is None else a.ctypes.data for a in arrs]),
+           "sl_walkers_write")
+
+
+def sl_walkers_set_sweeps_done(h, sweeps_done):
+    _check(_lib.sl_walkers_set_sweeps_done(h, sweeps_done), "sl_walkers_set_sweeps_done")
 
 
 def sl_walkers_destroy(h):
@@ -484,21 +518,37 @@ class Walkers:
         sl_walkers_get_spins(self.h, walker, out)
         return out
 
+    def save(self):
+        """Checkpoint: (spins [walker][N], S, H, stage, visited, sweeps done)."""
+        S, H, _, stage, vis = self.read()
+        spins = np.stack([self.spins(j) for j in range(self.nwalk)])
+        return spins, S, H, stage, vis, sl_walkers_info(self.h)[2]
+
+    def load(self, ckpt):
+        spins, S, H, stage, vis, t = ckpt
+        for j in range(self.nwalk):
+            sl_walkers_set_spins(self.h, j, np.ascontiguousarray(spins[j], np.int8))
+        sl_walkers_write(self.h, S, H, stage, vis)
+        sl_walkers_set_sweeps_done(self.h, t)
+
 
 class Batch:
     """A batch of Edwards-Anderson samples with replica exchange, its device
-    buffer a torch CUDA tensor."""
+    buffer a torch CUDA tensor.  L_per_sample[q] is the side of the sample with
+    global index first_sample + q."""
 
-    def __init__(self, d, L_per_sample, ntemps, betas, seed=0, stream=None, device="cuda"):
+    def __init__(self, d, L_per_sample, ntemps, betas, seed=0, first_sample=0, stream=None,
+                 device="cuda"):
         import torch
         self.d = d
         self.L = [int(x) for x in L_per_sample]
         self.ntemps = ntemps
         self.nsamples = len(self.L)
+        self.first_sample = first_sample
         nbytes = sl_batch_required_bytes(d, self.L, ntemps, betas)
         self.buf = torch.empty(nbytes, dtype=torch.uint8, device=device)
         self.stream = torch.cuda.current_stream(self.buf.device) if stream is None else stream
-        self.h = sl_batch_create(d, self.L, ntemps, betas, seed, self.buf, nbytes,
+        self.h = sl_batch_create(d, self.L, ntemps, betas, seed, first_sample, self.buf, nbytes,
                                  self.stream.cuda_stream)
 
     def close(self):
@@ -542,3 +592,22 @@ class Batch:
 
     def sweeps_done(self):
         return sl_batch_sweeps_done(self.h)
+
+    def save(self):
+        """Checkpoint: per sample (spins [slot][N], slot of each temperature),
+        and the sweeps done."""
+        state = []
+        for s in range(self.nsamples):
+            spins, perm = [], np.zeros(self.ntemps, np.int32)
+            for r in range(self.ntemps):
+                sp, k = self.get(s, r)
+                spins.append(sp)
+                perm[k] = r
+            state.append((np.stack(spins), perm))
+        return state, self.sweeps_done()
+
+    def load(self, ckpt):
+        state, t = ckpt
+        for s, (spins, perm) in enumerate(state):
+            sl_batch_set(self.h, s, np.ascontiguousarray(spins, np.int8), perm)
+        sl_batch_set_sweeps_done(self.h, t)

@@ -4,13 +4,20 @@ queue, every sample's replicas multispin-coded in shared memory) against the
 oracle's per-sample, per-replica loops: couplings, start states, every slot's
 spins, the slot-to-temperature assignment and the energy series at every
 temperature, bit for bit, whatever pack sizes the autotuner picks."""
+import json
+import os
+import hashlib
+
 import numpy as np
 import pytest
 
 import oracle
 from paper_1107_5463_gb300 import inputs
+from tests import oracle_pool
 
 pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "ea_long_runs.json")
 
 
 @pytest.fixture(scope="module")
@@ -138,4 +145,127 @@ def test_autotuner_reports_and_keeps_the_chain(sm):
         np.testing.assert_array_equal(gs, spins)
         np.testing.assert_array_equal(gp, perm)
         np.testing.assert_array_equal(E[s], Er)
+    b.close()
+
+
+def test_split_batches_equal_the_whole_batch(sm):
+    """Random numbers are keyed by the global sample index: two batches over
+    samples 0..5 and 6..10 (one per GPU, say) hold exactly the samples of one
+    batch over 0..10 (couplings, every slot, permutation, energy series)."""
+    d, nt = 3, 8
+    betas = inputs.geometric_betas(nt)
+    Ls = inputs.ea_sample_sizes(11)
+    whole = sm.Batch(d, Ls, nt, betas, seed=9)
+    Ew = whole.run(7, 3, series=True).cpu().numpy()
+    lo = sm.Batch(d, Ls[:6], nt, betas, seed=9, first_sample=0)
+    hi = sm.Batch(d, Ls[6:], nt, betas, seed=9, first_sample=6)
+    El = lo.run(7, 3, series=True).cpu().numpy()
+    Eh = hi.run(7, 3, series=True).cpu().numpy()
+    np.testing.assert_array_equal(np.concatenate([El, Eh]), Ew)
+    for s in range(11):
+        part, q = (lo, s) if s < 6 else (hi, s - 6)
+        np.testing.assert_array_equal(part.bonds(q), whole.bonds(s))
+        ps, pp = gpu_state(part, q)
+        ws, wp = gpu_state(whole, s)
+        np.testing.assert_array_equal(ps, ws)
+        np.testing.assert_array_equal(pp, wp)
+    # and the upper half is the oracle's samples 6..10
+    for q in (0, 4):
+        jb, spins, perm, Er = oracle_sample(d, Ls[6 + q], nt, betas, 9, 3, 6 + q, 7)
+        gs, gp = gpu_state(hi, q)
+        np.testing.assert_array_equal(gs, spins)
+        np.testing.assert_array_equal(gp, perm)
+        np.testing.assert_array_equal(Eh[q], Er)
+    for b in (whole, lo, hi):
+        b.close()
+
+
+def test_first_sample_beyond_replica_ids_is_rejected(sm):
+    with pytest.raises(sm.SpinMCError):
+        sm.Batch(3, [8, 8], 32, inputs.geometric_betas(32), first_sample=(1 << 27) - 1)
+
+
+def test_checkpoint_resume(sm):
+    """2n sweeps equal n sweeps, a checkpoint (every slot, the slot of every
+    temperature, the sweeps done) loaded into a fresh batch, then n more."""
+    d, nt = 3, 12
+    betas = inputs.geometric_betas(nt)
+    Ls = [8, 12, 16, 8]
+    a = sm.Batch(d, Ls, nt, betas, seed=4)
+    Ea = a.run(16, 5, series=True).cpu().numpy()
+    b = sm.Batch(d, Ls, nt, betas, seed=4)
+    b.run(8, 5)
+    ckpt = b.save()
+    b.close()
+    c = sm.Batch(d, Ls, nt, betas, seed=4)
+    c.load(ckpt)
+    assert c.sweeps_done() == 8
+    Ec = c.run(8, 5, series=True).cpu().numpy()
+    np.testing.assert_array_equal(Ec, Ea[:, 8:])
+    for s in range(len(Ls)):
+        sa, pa = gpu_state(a, s)
+        sc, pc = gpu_state(c, s)
+        np.testing.assert_array_equal(sc, sa)
+        np.testing.assert_array_equal(pc, pa)
+    with pytest.raises(sm.SpinMCError):
+        sm.sl_batch_set(c.h, 0, ckpt[0][0][0], np.zeros(nt, np.int32))  # not a permutation
+    a.close()
+    c.close()
+
+
+@pytest.mark.slow
+def test_full_workload_ten_sweeps_every_sample(sm):
+    """The batched workload at its full size: 1024 samples of sides
+    [8,12,16,24,32][s mod 5] x 32 temperatures geometric in [0.5, 3], 10
+    sweeps with exchange, every spin of every slot, every permutation and the
+    whole energy series of every sample against the oracle (run sample by
+    sample over the host cores)."""
+    d, nt, nsw, seed, run_seed = 3, 32, 10, inputs.DEFAULT_SEED, 0x11075463
+    betas = inputs.geometric_betas(nt)
+    Ls = inputs.ea_sample_sizes(1024)
+    b = sm.Batch(d, Ls, nt, betas, seed=seed)
+    E = b.run(nsw, run_seed, series=True).cpu().numpy()
+    tasks = [(d, L, nt, betas, seed, run_seed, s, nsw) for s, L in enumerate(Ls)]
+    checked = 0
+    for s, (jb, spins, perm, Er) in enumerate(oracle_pool.imap_spawn(oracle_pool.ea_sample_run,
+                                                                     tasks)):
+        np.testing.assert_array_equal(E[s], Er, err_msg="energy series, sample %d" % s)
+        gs, gp = gpu_state(b, s)
+        np.testing.assert_array_equal(gp, perm, err_msg="permutation, sample %d" % s)
+        np.testing.assert_array_equal(gs, spins, err_msg="spins, sample %d" % s)
+        if s % 97 == 0:
+            np.testing.assert_array_equal(b.bonds(s), jb)
+        checked += 1
+    assert checked == 1024
+    b.close()
+
+
+def _sha(a):
+    return hashlib.sha256(np.ascontiguousarray(a).tobytes()).hexdigest()
+
+
+@pytest.mark.slow
+def test_long_runs_one_sample_per_size(sm):
+    """One sample of each side of the batched workload for the full 10^4
+    sweeps, 32 temperatures, exchange every sweep: final spins of every slot,
+    the permutation and the whole energy series against the oracle's runs
+    recorded in tests/golden/ea_long_runs.json (written by
+    tests/golden/make_ea_long_runs.py, which calls only the oracle)."""
+    with open(GOLDEN) as f:
+        g = json.load(f)
+    d, nt, nsw = g["d"], g["ntemps"], g["nsweeps"]
+    betas = inputs.geometric_betas(nt)
+    Ls = [row["L"] for row in g["samples"]]
+    assert Ls == list(inputs.EA_SIZES)
+    b = sm.Batch(d, Ls, nt, betas, seed=g["create_seed"])
+    E = b.run(nsw, g["run_seed"], series=True).cpu().numpy()
+    for row in g["samples"]:
+        s = row["sample"]
+        for t, v in row["E_probe"].items():
+            np.testing.assert_array_equal(E[s, int(t)], np.array(v), err_msg="L=%d sweep %s"
+                                          % (row["L"], t))
+        assert _sha(E[s].astype(np.float64)) == row["E_sha256"], row["L"]
+        gs, gp = gpu_state(b, s)
+        assert gp.tolist() == row["slot_of_temp"], row["L"]
+        assert _sha(gs.astype(np.int8)) == row["spins_sha256"], row["L"]
     b.close()

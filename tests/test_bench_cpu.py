@@ -40,3 +40,16 @@ def test_workload_table():
         assert wl["desc"], name
         if wl["storage"] in ("i8", "bits", "vec", "angle"):
             assert wl["n"] == {"i8": 1, "bits": 1, "vec": 3, "angle": 2}[wl["storage"]], name
+
+
+@pytest.mark.parametrize("world", [1, 2, 3, 4, 8])
+def test_batch_sample_ranges_partition_the_batch(world):
+    """Each rank's contiguous block of global samples; together they cover
+    0..nsamples-1 once, in order (the batch's first_sample is lo)."""
+    n = bench.WORKLOADS["ea3d_batch_1024x32"]["samples"]
+    got = []
+    for r in range(world):
+        lo, hi = bench.sample_range(n, r, world)
+        assert hi - lo in (n // world, n // world + 1)
+        got.extend(range(lo, hi))
+    assert got == list(range(n))

@@ -3,11 +3,24 @@ FP32 spins, FP64 observable totals) against the FP64 oracle.
 
 Accepted spins are fresh proposals, so spin errors do not accumulate: every
 component must agree within 1e-5 of the oracle except inside the light cone
-of a near-tie, a decision whose margin |u - exp(-beta dE)| is so small that
-FP32 rounding may flip it (the oracle logs them; a difference then spreads by
-at most two lattice steps per sweep).  Energies must agree within 1e-5 per
-site when no near-tie occurred, and the FP64 energy the kernels track must
+of a near-tie that went the other way.  A near-tie is a decision whose
+margin |u - p|, p = exp(-beta dE), lies within the error FP32 can make in p.
+The oracle reports, for every decision it screens, the margin and a
+condition factor K = p (beta (A + |dE|) + 1) (A sums the field components
+and the proposal's change against the couplings, see oracle.h): if every
+spin component and every FP32 operation errs by at most EPS, p errs by at
+most EPS K.  The kernels' spin components differ from the oracle's by at most
+2.4e-7 (FP32 storage of fresh proposals and of sin / cos of stored turns,
+measured at most 1.4e-7 and 2e-7), and the FP32 sums over 2d neighbours and
+the n-term dot product round by at most 2d 2^-24 = 3.6e-7 relative, so
+EPS = 1e-6 bounds both with room to spare.  Only a near-tie can go the other
+way, and one that did shows at the end of its sweep as an O(1) difference at
+its own site: those sites seed the excluded cones, which grow by two lattice
+steps per sweep (one colour pass each).  Energies must agree within 1e-5 per
+site when no near-tie diverged, and the FP64 energy the kernels track must
 match an FP64 recomputation from the final FP32 spins within 1e-4 per site.
+The fast-math kernels (hardware sin/cos/exp) have no such bound and keep a
+flat screen: every decision within TIE_TOL_FAST counts as a near-tie.
 """
 import math
 
@@ -20,7 +33,8 @@ from paper_1107_5463_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-5
-TIE_TOL = 2e-5
+EPS = 1e-6           # error bound of an FP32 evaluation of p, in units of K
+TIE_SCREEN = 1e-4    # the oracle reports decisions with margins below this (>= EPS K)
 TIE_TOL_FAST = 5e-5
 
 
@@ -59,13 +73,15 @@ def start_state(n, d, L, seed):
 class Pair:
     """GPU and oracle runs from one FP32 start, compared after every sweep.
 
-    A near-tie decided in sweep t may make the two runs differ at its site;
-    the difference spreads by at most two lattice steps per sweep (one
-    colour pass each), so after sweep t' the sites within distance
-    2 (t' - t) + 2 are excluded from the component check."""
+    A near-tie decided in sweep t that went the other way makes the two runs
+    differ at its site; the difference spreads by at most two lattice steps
+    per sweep (one colour pass each), so after sweep t' the sites within
+    distance 2 (t' - t) + 2 of it are excluded from the component check.
+    tie_tol=None takes the derived near-tie rule (margin < EPS K); a number
+    takes a flat screen (margin < tie_tol)."""
 
     def __init__(self, sm, n, d, L, beta, nsw, seed=3, sweep_seed=11, J=1.0, Jb=None, fast=0,
-                 renorm=16, tie_tol=TIE_TOL, kernel=0):
+                 renorm=16, tie_tol=None, kernel=0):
         N = L ** d
         s32 = start_state(n, d, L, seed)
         lat = sm.Lattice(d, L, n=n, J=J, J_bonds=Jb, seed=seed)
@@ -77,47 +93,67 @@ class Pair:
         lat.set_spins(s32)
         ref = s32.astype(np.float64)
         cone = np.zeros(N, bool)
-        self.N, self.nsw, self.ntie = N, nsw, 0
+        self.N, self.nsw, self.ntie, self.ndiverged = N, nsw, 0, 0
         self.compared, self.max_err, self.max_dE_clean, self.max_dm_clean = 0, 0.0, 0.0, 0.0
-        self.max_dE = 0.0
+        self.max_dE = self.max_dm = 0.0
+        self.max_diverged_ratio = 0.0   # largest margin / K among decisions that diverged
+        screen = TIE_SCREEN if tie_tol is None else tie_tol
         for t in range(nsw):
             E, m = lat.sweep_series(beta, 1, sweep_seed)
             got = lat.get_spins()
+            kw = dict(J=J, Jb=Jb, tie_tol=screen, ties_cap=1 << 21, tie_info=True)
             if n == 2:
-                Er, mr, tt, nt = oracle.xy_sweeps(d, L, ref, beta, sweep_seed, t, 1, J=J, Jb=Jb,
-                                                  tie_tol=tie_tol, ties_cap=1 << 20)
+                Er, mr, tt, nt, info = oracle.xy_sweeps(d, L, ref, beta, sweep_seed, t, 1, **kw)
             else:
-                Er, mr, tt, nt = oracle.heis_sweeps(d, L, ref, beta, sweep_seed, t, 1, J=J, Jb=Jb,
-                                                    renorm_every=renorm, tie_tol=tie_tol,
-                                                    ties_cap=1 << 20)
-            assert nt <= 1 << 20
-            self.ntie += nt
-            new = np.zeros(N, bool)
-            new[tt[:, 1]] = True
-            cone = dilate(cone, d, L, 2) | dilate(new, d, L, 2)
+                Er, mr, tt, nt, info = oracle.heis_sweeps(d, L, ref, beta, sweep_seed, t, 1,
+                                                          renorm_every=renorm, **kw)
+            assert nt <= 1 << 21
+            if tie_tol is None:
+                near = info[:, 0] < EPS * info[:, 1]
+            else:
+                near = np.ones(len(tt), bool)
+            self.ntie += int(near.sum())
+            if n == 2:
+                err_all = angle_diff(got, ref)
+            else:
+                err_all = np.abs(got.astype(np.float64) - ref).max(axis=1)
+            sites = tt[:, 1]
+            # the reach, at the end of this sweep, of earlier divergences
+            grown = dilate(cone, d, L, 2)
+            diverged = ~grown[sites] & (err_all[sites] > TOL)
+            seeds = np.zeros(N, bool)
+            seeds[sites[diverged & near]] = True
+            self.ndiverged += int((diverged & near).sum())
+            cone = grown | dilate(seeds, d, L, 2)
+            # a screened decision outside every cone that diverged must be a near-tie
+            bad = ~cone[sites] & diverged & ~near
+            assert not bad.any(), ("sweep %d: decisions outside the near-tie bound diverged" % t,
+                                   sites[bad][:8], info[bad][:8])
+            if (diverged & near).any():
+                r = info[diverged & near]
+                self.max_diverged_ratio = max(self.max_diverged_ratio, float((r[:, 0] / r[:, 1]).max()))
             ok = ~cone
-            if n == 2:
-                err = angle_diff(got, ref)[ok]
-            else:
-                err = np.abs(got.astype(np.float64) - ref)[ok]
+            err = err_all[ok]
             self.compared += int(ok.sum())
             if err.size:
                 self.max_err = max(self.max_err, float(err.max()))
             dE = abs(float(E[0].item()) - float(Er[0])) / N
+            dm = abs(float(m[0].item()) - float(mr[0]))
             self.max_dE = max(self.max_dE, dE)
-            self.max_dm = max(getattr(self, "max_dm", 0.0), abs(float(m[0].item()) - float(mr[0])))
-            if self.ntie == 0:
+            self.max_dm = max(self.max_dm, dm)
+            if self.ndiverged == 0:
                 self.max_dE_clean = max(self.max_dE_clean, dE)
-                self.max_dm_clean = max(self.max_dm_clean, abs(float(m[0].item()) - float(mr[0])))
+                self.max_dm_clean = max(self.max_dm_clean, dm)
         lat.close()
 
-    def check(self, min_fraction=0.5):
-        """Components within TOL outside near-tie cones after every sweep;
-        energy per site and |m| within TOL while no near-tie has happened."""
-        assert self.max_err <= TOL, (self.max_err, self.ntie)
+    def check(self, min_fraction=0.95):
+        """Components within TOL outside the cones of diverged near-ties after
+        every sweep; energy per site and |m| within TOL while no near-tie has
+        diverged; at least min_fraction of all site-sweeps compared."""
+        assert self.max_err <= TOL, (self.max_err, self.ntie, self.ndiverged)
         assert self.max_dE_clean < TOL and self.max_dm_clean < TOL
         assert self.compared >= min_fraction * self.N * self.nsw, \
-            ("too many near-ties to compare", self.ntie)
+            ("too many diverged near-ties to compare", self.ntie, self.ndiverged)
 
 
 @pytest.mark.parametrize("n,d,L", [(2, 2, 2), (2, 2, 6), (2, 2, 32), (2, 3, 4), (2, 3, 8),
@@ -253,9 +289,10 @@ def test_equilibrium_energy_agrees_statistically(sm, n, d, L, beta):
 @pytest.mark.parametrize("n,d,L,beta", [(3, 3, 256, 0.693), (2, 2, 4096, 1.12)])
 def test_full_size_first_ten_sweeps(sm, n, d, L, beta):
     """The paper-shaped workloads at full size: 3D Heisenberg L = 256 and 2D XY
-    L = 4096, first 10 sweeps against the FP64 oracle."""
+    L = 4096, first 10 sweeps against the FP64 oracle, at least 95% of all
+    site-sweeps compared."""
     p = Pair(sm, n, d, L, beta, 10, seed=inputs.DEFAULT_SEED)
-    p.check(min_fraction=0.3)
+    p.check(min_fraction=0.95)
     # after near-ties the energies differ by a few units per cone
     assert p.max_dE < 1e-4
 
@@ -267,14 +304,16 @@ def test_precision_report(sm, n, d, L, beta, capsys):
     """FP32 kernels against the FP64 oracle per observable on the paper-shaped
     workloads (XY at the three temperatures of the workload, Heisenberg with
     renormalisation every 16 sweeps), first 10 sweeps: the largest spin
-    component error outside near-tie cones, |dE|/N and |d|m|| after every
-    sweep, and the number of near-ties; printed as one line per workload."""
+    component error outside the cones of diverged near-ties, |dE|/N and
+    |d|m|| after every sweep, the number of near-ties and of those that
+    diverged, and the largest margin / K of a diverged decision (below EPS by
+    the check); printed as one line per workload."""
     p = Pair(sm, n, d, L, beta, 10, seed=inputs.DEFAULT_SEED)
     with capsys.disabled():
         print("\nprecision n=%d d=%d L=%d beta=%g: component %.2e (%s), |dE|/N %.2e, |d|m|| %.2e, "
-              "near-ties %d, sites compared %.3f" % (n, d, L, beta, p.max_err,
-                                                     "rad" if n == 2 else "per component",
-                                                     p.max_dE, p.max_dm, p.ntie,
-                                                     p.compared / (p.N * p.nsw)))
-    p.check(min_fraction=0.3)
+              "near-ties %d, diverged %d (largest margin/K %.2e), sites compared %.4f"
+              % (n, d, L, beta, p.max_err, "rad" if n == 2 else "per component", p.max_dE,
+                 p.max_dm, p.ntie, p.ndiverged, p.max_diverged_ratio,
+                 p.compared / (p.N * p.nsw)))
+    p.check(min_fraction=0.95)
     assert p.max_dE < 1e-4 and p.max_dm < 1e-4

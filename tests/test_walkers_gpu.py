@@ -163,3 +163,45 @@ def test_walker_argument_checks(sm):
             # only gluing rejects them
             S, _, _, _, vis = w.read()
             sm.sl_dos_glue(L, w.klo, w.khi, S[::wpw].astype(float), vis[::wpw])
+
+
+@pytest.mark.parametrize("spins_smem", [0, 1])
+def test_checkpoint_resume(sm, spins_smem):
+    """2n Wang-Landau sweeps equal n sweeps, a checkpoint (every walker's
+    spins, ln g, histogram, stage, visited levels and the sweeps done) loaded
+    into a fresh walker set, then n more; the loaded level is recomputed from
+    the spins and must lie in the walker's window."""
+    L = 8
+    klo, khi = windows(L * L, 4)
+    a = sm.Walkers(L, klo, khi, 32, seed=6)
+    a.set_option(sm.SL_WOPT_SPINS_SMEM, spins_smem)
+    a.wl(24, final_stage=12, seed=2)
+    b = sm.Walkers(L, klo, khi, 32, seed=6)
+    b.set_option(sm.SL_WOPT_SPINS_SMEM, spins_smem)
+    b.wl(12, final_stage=12, seed=2)
+    ckpt = b.save()
+    b.close()
+    c = sm.Walkers(L, klo, khi, 32, seed=123)   # another start: the checkpoint replaces it
+    c.set_option(sm.SL_WOPT_SPINS_SMEM, spins_smem)
+    c.load(ckpt)
+    c.wl(12, final_stage=12, seed=2)
+    ra, rc = a.read(), c.read()
+    for x, y in zip(ra, rc):
+        np.testing.assert_array_equal(x, y)
+    for j in range(0, a.nwalk, 5):
+        np.testing.assert_array_equal(a.spins(j), c.spins(j))
+    assert sm.sl_walkers_info(c.h)[2] == 24
+    # a configuration whose level is outside walker 0's window is refused
+    with pytest.raises(sm.SpinMCError):
+        sm.sl_walkers_set_spins(c.h, 0, _far_state(L, klo[0], khi[0]))
+    a.close()
+    c.close()
+
+
+def _far_state(L, klo, khi):
+    """All up (level 0) unless that lies in [klo, khi]; then a Neel state (level N)."""
+    s = np.ones(L * L, np.int8)
+    if klo <= 0 <= khi:
+        x, y = np.meshgrid(np.arange(L), np.arange(L))
+        s = np.where((x + y) % 2 == 0, 1, -1).astype(np.int8).reshape(-1)
+    return s
