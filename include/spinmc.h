@@ -207,6 +207,82 @@ int sl_attach_workspace(sl_lattice* lat, void* dev_buf, size_t bytes);
  * Synchronises the handle's stream first. */
 void sl_destroy(sl_lattice* lat);
 
+/* ---- Domain decomposition: one lattice split into slabs ------------------
+ *
+ * Section 2 of the paper decomposes the lattice so that different processors
+ * update different parts of it in parallel.  Here an Ising lattice (Eq. 1
+ * with a uniform J) is split along its slowest axis (y in 2D, z in 3D) into
+ * slabs, one per GPU or per rank.  A slab owns the global planes
+ * z0 .. z0 + Lz - 1 and keeps one halo plane of each colour on either side
+ * of them (the last plane of the slab below and the first of the slab
+ * above, periodically).  A sweep is: every slab's colour-0 pass; the
+ * exchange of colour 0 (each slab's first own plane of that colour into the
+ * lower neighbour's upper halo, its last into the upper neighbour's lower
+ * halo); every slab's colour-1 pass, which also measures the slab's part of
+ * E and M; the exchange of colour 1.  Random numbers are keyed by the global
+ * site, so the slabs reproduce the whole lattice's trajectory bit for bit
+ * and their E and M add up to the lattice's.  A slab handle works with
+ * sl_get_spins / sl_set_spins (its own sites, local natural order
+ * i = x + L*(y - z0) in 2D, x + L*y + L*L*(z - z0) in 3D), sl_measure (its
+ * share; the halos must be current), sl_get_state / sl_set_state,
+ * sl_set_option (Metropolis or heat-bath, kernel and rows) and sl_destroy;
+ * sl_sweep and sl_sweep_series refuse it. */
+
+/* Device bytes of a slab: d in {2,3}; L % 8 == 0 (% 64 for bits);
+ * storage SL_STORE_I8 or SL_STORE_BITS; 0 <= z0, 1 <= Lz, z0 + Lz <= L. */
+int sl_slab_required_bytes(int d, int L, int storage, int z0, int Lz, size_t* bytes);
+
+/* Create a slab (uniform coupling J) and draw its sites' start spins exactly
+ * as sl_create draws those sites of the whole lattice.  The halos are filled
+ * by the first exchange.  dev_buf and stream as for sl_create. */
+int sl_slab_create(int d, int L, int storage, double J, uint64_t seed, uint32_t replica, int z0,
+                   int Lz, void* dev_buf, size_t dev_buf_bytes, void* stream, sl_lattice** out);
+
+/* Device addresses of a slab's planes of one colour: send_lo / send_hi its
+ * first / last own plane, recv_lo / recv_hi the halo planes below / above
+ * them; *bytes the size of one plane (L^(d-1) / 2 bytes, or / 16 for bits).
+ * An exchange copies send_lo into the lower neighbour's recv_hi and send_hi
+ * into the upper neighbour's recv_lo (NCCL send / receive, a peer copy ...),
+ * on an order with the passes that both sides see. */
+int sl_slab_planes(const sl_lattice* lat, int colour, void** send_lo, void** send_hi,
+                   void** recv_lo, void** recv_hi, size_t* bytes);
+
+/* From the next sweep on, the colour-1 pass of sweep k (counted from 0 at
+ * this call) writes the slab's share of the energy to dev_E[k] and of
+ * M = sum_i s_i to dev_M[k] (device pointers, either may be NULL).
+ * Asynchronous on the slab's stream. */
+int sl_slab_series(sl_lattice* lat, double* dev_E, double* dev_M);
+
+/* One colour pass of a slab (asynchronous).  Colours alternate, 0 first;
+ * the colour-1 pass ends the sweep.  The halos of the other colour must
+ * hold the neighbours' current boundary planes. */
+int sl_slab_pass(sl_lattice* lat, double beta, uint64_t seed, int colour);
+
+/* For slabs held by one process (on one or several devices): the exchange
+ * of one colour between slabs[0..nslabs-1], which must tile the lattice in
+ * order (slab 0 from plane 0, each starting where the previous ends, the
+ * last ending at L).  Each slab's stream waits for its neighbours' last
+ * passes (events) and then copies their planes into its halos
+ * (cudaMemcpyAsync, or cudaMemcpyPeerAsync across devices). */
+int sl_slabs_exchange(sl_lattice* const* slabs, int nslabs, int colour);
+
+/* nsweeps sweeps of slabs held by one process: both exchanges first (the
+ * halos need not be current), then per sweep the colour-0 passes, the
+ * colour-0 exchange, the colour-1 passes and the colour-1 exchange.
+ * dev_EM[i] (device, on slab i's device, or NULL for every slab) receives
+ * slab i's energy shares in [0, nsweeps) and M shares in
+ * [nsweeps, 2 nsweeps).  Asynchronous. */
+int sl_slabs_sweep(sl_lattice* const* slabs, int nslabs, double beta, int64_t nsweeps,
+                   uint64_t seed, double* const* dev_EM);
+
+/* Sum 1 to 64 parts laid out as sl_slabs_sweep writes them (nsweeps
+ * energies, then nsweeps magnetisations; device memory readable from the
+ * stream's device) in order: dev_E[k] = sum of the energies, dev_absm[k] =
+ * |sum of the M| / N for the whole lattice's N sites.  After an all-reduce
+ * across ranks, nparts = 1.  Asynchronous. */
+int sl_series_reduce(const double* const* parts, int nparts, int64_t nsweeps, double N,
+                     double* dev_E, double* dev_absm, void* stream);
+
 /* ---- Edwards-Anderson +-J spin glass, batched, with replica exchange ----
  *
  * Section 2 of the paper: for quenched disorder, independent disorder samples

@@ -45,6 +45,15 @@ struct sl_lattice {
     int64_t N, H;            // sites, sites per colour
     int W;                   // sites of one colour in one row (L / 2)
     int sms;                 // multiprocessors of the device the handle was created on
+    // A slab of a larger lattice split along its slowest axis (y in 2D, z in
+    // 3D): it owns global planes z0 .. z0 + Lz - 1, stores one halo plane on
+    // each side of each colour array, and keys its random numbers by global
+    // site.  A whole lattice has slab = 0, z0 = 0, Lz = L.
+    int slab, z0, Lz;
+    int64_t P;               // sites of one colour in one plane (L/2 in 2D, L*L/2 in 3D)
+    int next_colour;         // slab passes: the colour the next pass updates
+    int device;              // the CUDA device the handle was created on
+    cudaEvent_t ev;          // slab exchanges: marks the end of this slab's last pass
     double J;
     uint64_t init_seed;
     uint32_t replica;
@@ -80,6 +89,13 @@ namespace spinmc {
 int fail(int status, const char* fmt, ...);
 int cuda_fail(cudaError_t e, const char* what);
 
+// the lattice constructor behind sl_create and sl_slab_create (lattice.cu)
+int create_lattice(int d, int L, int n, int j_layout, int storage, double J, const void* J_bonds,
+                   uint64_t seed, uint32_t replica, bool slab, int z0, int Lz, void* dev_buf,
+                   size_t dev_buf_bytes, void* stream, sl_lattice** out);
+size_t slab_required_bytes(int d, int L, int storage, int Lz);
+int ising_table(const sl_lattice* h, double beta, IsingTable* tab);
+
 // ---- Ising int8 (ising_i8.cu) ----
 cudaError_t ising_i8_init(const sl_lattice* h, cudaStream_t s);
 cudaError_t ising_i8_scatter(const sl_lattice* h, const int8_t* nat, cudaStream_t s);
@@ -88,6 +104,8 @@ cudaError_t ising_bonds_scatter(const sl_lattice* h, const int8_t* nat, unsigned
                                 cudaStream_t s);
 cudaError_t ising_i8_sweeps(const sl_lattice* h, const SweepParams& p, int64_t count,
                             cudaStream_t s);
+// one colour pass (c = 1 measures and advances the sweep counter)
+cudaError_t ising_i8_pass(const sl_lattice* h, const SweepParams& p, int c, cudaStream_t s);
 cudaError_t ising_i8_measure(const sl_lattice* h, cudaStream_t s);
 // measurement that also closes a sweep (series entry, sweep counter + 1)
 cudaError_t ising_i8_measure_advance(const sl_lattice* h, cudaStream_t s);
@@ -107,6 +125,7 @@ cudaError_t ising_bits_scatter(const sl_lattice* h, const int8_t* nat, cudaStrea
 cudaError_t ising_bits_gather(const sl_lattice* h, int8_t* nat, cudaStream_t s);
 cudaError_t ising_bits_sweeps(const sl_lattice* h, const SweepParams& p, int64_t count,
                               cudaStream_t s);
+cudaError_t ising_bits_pass(const sl_lattice* h, const SweepParams& p, int c, cudaStream_t s);
 cudaError_t ising_bits_measure(const sl_lattice* h, cudaStream_t s);
 
 // ---- XY / Heisenberg FP32 (on_f32.cu) ----

@@ -13,6 +13,10 @@
 // b0, b1, b2); the Philox outputs of the 32 sites are compared with the d
 // thresholds into planes g_k = [u > T_k]; the move is accepted where
 // na >= k + 1 for every k with g_k set, which equals u <= T[na].
+//
+// Slabs (a lattice split along its slowest axis) are handled as in the byte
+// kernels: Lz local planes between halo planes, global Philox groups and
+// colour parity.
 #include "internal.h"
 
 namespace spinmc {
@@ -30,6 +34,10 @@ struct BitArgs {
     Partial* partials;
     double J;
     int measure, update;
+    int Lz;          // planes along the slowest axis (L, or the slab's planes)
+    int wrap;        // 1: periodic along the slowest axis; 0: halo planes at -1 and Lz
+    int par;         // parity of the first plane's global index
+    long long gofs;  // global colour index of local colour entry 0
 };
 
 __device__ __forceinline__ void bits_finish(const BitArgs& a, const Partial& tot)
@@ -44,7 +52,8 @@ __device__ __forceinline__ void bits_finish(const BitArgs& a, const Partial& tot
     if (a.update) {
         const long long k = (long long)C->t - C->series_base;
         if (C->series_E) C->series_E[k] = E;
-        if (C->series_absm) C->series_absm[k] = fabs(M) / (double)a.N;
+        // a slab records its own M (summed over slabs, |M| / N is |m|)
+        if (C->series_absm) C->series_absm[k] = a.wrap ? fabs(M) / (double)a.N : M;
         C->t = C->t + 1;
     }
 }
@@ -63,9 +72,12 @@ __global__ void __launch_bounds__(128) bits_stream(const BitArgs a)
 {
     __shared__ long long red[32];
     const uint32_t t = (uint32_t)a.ctrl->t;
-    const int L = a.L, R = a.R;
+    const int L = a.L, R = a.R, Lz = a.Lz;
     const int WW = a.W >> 5;  // words per row
-    const long long nseg = L / R;
+    const long long nseg = Lz / R;
+    // neighbouring plane along the slowest axis: periodic, or a halo plane
+    auto zprev = [&](int m) { return m == 0 ? (a.wrap ? Lz - 1 : -1) : m - 1; };
+    auto znext = [&](int m) { return m == Lz - 1 ? (a.wrap ? 0 : Lz) : m + 1; };
     const long long nitems = (long long)WW * (D == 3 ? L : 1) * nseg;
     const uint32_t ctr_w = (kSweep << 1) | (uint32_t)a.c;
     const uint32_t inv = JNEG ? 0xFFFFFFFFu : 0u;
@@ -80,7 +92,7 @@ __global__ void __launch_bounds__(128) bits_stream(const BitArgs a)
         const int m0 = seg * R;
         auto row = [&](int yy, int zz) -> long long { return (long long)zz * L + yy; };
         auto mrow = [&](int m) -> long long { return D == 3 ? row(y3, m) : row(m, 0); };
-        const int mprev = m0 == 0 ? L - 1 : m0 - 1;
+        const int mprev = zprev(m0);
         uint32_t prev = __ldg(a.oth + mrow(mprev) * WW + w);
         uint32_t cur = __ldg(a.oth + mrow(m0) * WW + w);
         const int wl = w == 0 ? WW - 1 : w - 1, wr = w == WW - 1 ? 0 : w + 1;
@@ -89,8 +101,8 @@ __global__ void __launch_bounds__(128) bits_stream(const BitArgs a)
         // software pipeline: the next row of the other colour, the own word,
         // the x-neighbour word and (3D) the y -/+ 1 words are loaded one row ahead
         auto rowof = [&](int m) -> long long { return D == 3 ? row(y3, m) : row(m, 0); };
-        auto par = [&](int m) -> int { return ((D == 3 ? y3 + m : m) + a.c) & 1; };
-        uint32_t next_nx = __ldg(a.oth + mrow(m0 == L - 1 ? 0 : m0 + 1) * WW + w);
+        auto par = [&](int m) -> int { return ((D == 3 ? y3 + m : m) + a.c + a.par) & 1; };
+        uint32_t next_nx = __ldg(a.oth + mrow(znext(m0)) * WW + w);
         uint32_t A_nx = a.own[rowof(m0) * WW + w];
         uint32_t hw_nx = __ldg(a.oth + rowof(m0) * WW + (par(m0) ? wr : wl));
         uint32_t ym_nx = 0, yp_nx = 0;
@@ -102,11 +114,11 @@ __global__ void __launch_bounds__(128) bits_stream(const BitArgs a)
             const int m = m0 + r;
             const int yy = D == 3 ? y3 : m;
             const int zz = D == 3 ? m : 0;
-            const int p = (yy + zz + a.c) & 1;
+            const int p = (yy + zz + a.c + a.par) & 1;
             const long long rr = row(yy, zz);
             const uint32_t next = next_nx, A = A_nx, hw = hw_nx, ym = ym_nx, yp = yp_nx;
             if (r + 1 < R) {
-                const int m1 = m + 1, m2 = m1 == L - 1 ? 0 : m1 + 1;
+                const int m1 = m + 1, m2 = znext(m1);
                 next_nx = __ldg(a.oth + mrow(m2) * WW + w);
                 A_nx = a.own[rowof(m1) * WW + w];
                 hw_nx = __ldg(a.oth + rowof(m1) * WW + (par(m1) ? wr : wl));
@@ -139,7 +151,7 @@ __global__ void __launch_bounds__(128) bits_stream(const BitArgs a)
             if (a.update) {
                 const uint32_t ge1 = b0 | b1 | b2, ge2 = b1 | b2, ge3 = b2 | (b1 & b0);
                 uint32_t g0 = 0, g1 = 0, g2 = 0;
-                const uint32_t grp = (uint32_t)((rr * a.W + 32 * w) >> 2);
+                const uint32_t grp = (uint32_t)((rr * a.W + a.gofs + 32 * w) >> 2);
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
                     const uint4 rnd = philox4x32_10(make_uint4(grp + q, t, a.replica, ctr_w), a.rk);
@@ -194,8 +206,9 @@ __global__ void __launch_bounds__(kFinishThreads) bits_finish_kernel(const BitAr
     if (threadIdx.x == 0) bits_finish(a, tot);
 }
 
+// wofs: global index of local word 0 (the global colour index of entry 0 / 32)
 __global__ void bits_init_kernel(uint32_t* s0, uint32_t* s1, long long nwords, uint32_t replica,
-                                 RoundKeys rk)
+                                 RoundKeys rk, long long wofs)
 {
     for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < 2 * nwords;
          q += (long long)gridDim.x * blockDim.x) {
@@ -205,7 +218,8 @@ __global__ void bits_init_kernel(uint32_t* s0, uint32_t* s1, long long nwords, u
 #pragma unroll
         for (int g = 0; g < 8; ++g) {
             const uint4 r = philox4x32_10(
-                make_uint4((uint32_t)(8 * w + g), 0u, replica, (kInit << 1) | (uint32_t)c), rk);
+                make_uint4((uint32_t)(8 * (w + wofs) + g), 0u, replica, (kInit << 1) | (uint32_t)c),
+                rk);
             const uint32_t o[4] = {r.x, r.y, r.z, r.w};
 #pragma unroll
             for (int b = 0; b < 4; ++b)
@@ -218,7 +232,7 @@ __global__ void bits_init_kernel(uint32_t* s0, uint32_t* s1, long long nwords, u
 // natural +-1 bytes -> bit words: word (row r, w) of colour c holds natural
 // sites r L + 64 w + 2 b + p, p = (y + z + c) & 1
 __global__ void bits_scatter_kernel(uint32_t* s0, uint32_t* s1, const int8_t* nat, long long nwords,
-                                    int L, int WW)
+                                    int L, int WW, int par)
 {
     for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < 2 * nwords;
          q += (long long)gridDim.x * blockDim.x) {
@@ -227,7 +241,7 @@ __global__ void bits_scatter_kernel(uint32_t* s0, uint32_t* s1, const int8_t* na
         const long long r = wi / WW;
         const int w = (int)(wi % WW);
         const int y = (int)(r % L), z = (int)(r / L);
-        const int p = (y + z + c) & 1;
+        const int p = (y + z + c + par) & 1;
         const long long base = r * L + 64LL * w + p;
         uint32_t word = 0;
         for (int b = 0; b < 32; ++b)
@@ -237,14 +251,14 @@ __global__ void bits_scatter_kernel(uint32_t* s0, uint32_t* s1, const int8_t* na
 }
 
 __global__ void bits_gather_kernel(const uint32_t* s0, const uint32_t* s1, int8_t* nat, long long N,
-                                   int L)
+                                   int L, int par)
 {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
          i += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(i % L);
         const long long r = i / L;
         const int y = (int)(r % L), z = (int)(r / L);
-        const int c = (x + y + z) & 1;
+        const int c = (x + y + z + par) & 1;
         const long long j = i >> 1;  // = r W + (x >> 1)
         const uint32_t word = (c ? s1 : s0)[j >> 5];
         nat[i] = ((word >> (j & 31)) & 1u) ? (int8_t)-1 : (int8_t)1;
@@ -267,7 +281,8 @@ int pick_rows(const sl_lattice* h)
     const long long WW = h->W / 32;
     const long long cross = h->d == 3 ? h->L : 1;
     int R = h->d == 3 ? 4 : 8;
-    while (R > 1 && (h->L % R != 0 || WW * cross * (h->L / R) < (long long)h->sms * 512)) R >>= 1;
+    while (R > 1 && (h->Lz % R != 0 || WW * cross * (h->Lz / R) < (long long)h->sms * 512))
+        R >>= 1;
     return R;
 }
 
@@ -289,12 +304,16 @@ BitArgs make_args(const sl_lattice* h, int c)
     a.J = h->J;
     a.measure = c == 1;
     a.update = 1;
+    a.Lz = h->Lz;
+    a.wrap = !h->slab;
+    a.par = h->z0 & 1;
+    a.gofs = (long long)h->z0 * h->P;
     return a;
 }
 
 cudaError_t launch(const sl_lattice* h, const BitArgs& a, cudaStream_t s)
 {
-    const long long items = (long long)(h->W / 32) * (h->d == 3 ? h->L : 1) * (h->L / a.R);
+    const long long items = (long long)(h->W / 32) * (h->d == 3 ? h->L : 1) * (h->Lz / a.R);
     const int grid = grid_for(items, 128);
     const bool jneg = a.tab.sigma_neg != 0;
 #define SPINMC_BITS(D, N)                                                     \
@@ -325,7 +344,7 @@ cudaError_t ising_bits_init(const sl_lattice* h, cudaStream_t s)
     const long long nwords = h->H / 32;
     bits_init_kernel<<<grid_for(2 * nwords, 256), 256, 0, s>>>(
         (uint32_t*)h->spins[0], (uint32_t*)h->spins[1], nwords, h->replica,
-        make_round_keys(h->init_seed));
+        make_round_keys(h->init_seed), (long long)h->z0 * h->P / 32);
     return cudaGetLastError();
 }
 
@@ -333,14 +352,14 @@ cudaError_t ising_bits_scatter(const sl_lattice* h, const int8_t* nat, cudaStrea
 {
     const long long nwords = h->H / 32;
     bits_scatter_kernel<<<grid_for(2 * nwords, 256), 256, 0, s>>>(
-        (uint32_t*)h->spins[0], (uint32_t*)h->spins[1], nat, nwords, h->L, h->W / 32);
+        (uint32_t*)h->spins[0], (uint32_t*)h->spins[1], nat, nwords, h->L, h->W / 32, h->z0 & 1);
     return cudaGetLastError();
 }
 
 cudaError_t ising_bits_gather(const sl_lattice* h, int8_t* nat, cudaStream_t s)
 {
     bits_gather_kernel<<<grid_for(h->N, 256), 256, 0, s>>>(
-        (const uint32_t*)h->spins[0], (const uint32_t*)h->spins[1], nat, h->N, h->L);
+        (const uint32_t*)h->spins[0], (const uint32_t*)h->spins[1], nat, h->N, h->L, h->z0 & 1);
     return cudaGetLastError();
 }
 
@@ -356,6 +375,14 @@ cudaError_t ising_bits_sweeps(const sl_lattice* h, const SweepParams& p, int64_t
             if (e != cudaSuccess) return e;
         }
     return cudaSuccess;
+}
+
+cudaError_t ising_bits_pass(const sl_lattice* h, const SweepParams& p, int c, cudaStream_t s)
+{
+    BitArgs a = make_args(h, c);
+    a.tab = p.tab;
+    a.rk = p.rk;
+    return launch(h, a, s);
 }
 
 cudaError_t ising_bits_measure(const sl_lattice* h, cudaStream_t s)

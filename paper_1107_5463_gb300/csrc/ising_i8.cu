@@ -23,6 +23,13 @@
 //               with a rolling window of the other colour's rows in registers,
 //               128-bit loads and stores, SIMD-within-a-word neighbour
 //               counts; needs W % 16 == 0 and +-1 couplings.
+//
+// Slabs (a lattice split along its slowest axis, y in 2D or z in 3D): the
+// kernels see Lz local planes with a halo plane before the first and after
+// the last in each colour array (no wrap along that axis), add the slab's
+// global plane offset to every Philox group (gofs colour entries) and its
+// parity to every colour, so each site makes the decisions it makes in the
+// whole lattice.
 #include "internal.h"
 
 namespace spinmc {
@@ -45,6 +52,10 @@ struct I8Args {
     int update;   // 0: standalone measurement (no moves, no sweep advance)
     int advance;  // a measurement that closes a sweep: write the series, t + 1
     int defer;    // i8_stream: store block partials for i8_finish_kernel
+    int Lz;       // planes along the slowest axis (L, or the slab's planes)
+    int wrap;     // 1: periodic along the slowest axis; 0: halo planes at -1 and Lz
+    int par;      // parity of the first plane's global index
+    long long gofs;  // global colour index of local colour entry 0
 };
 
 __device__ __forceinline__ void i8_finish(const I8Args& a, const Partial& tot)
@@ -59,7 +70,8 @@ __device__ __forceinline__ void i8_finish(const I8Args& a, const Partial& tot)
     if (a.update || a.advance) {
         const long long k = (long long)C->t - C->series_base;
         if (C->series_E) C->series_E[k] = E;
-        if (C->series_absm) C->series_absm[k] = fabs(M) / (double)a.N;
+        // a slab records its own M (summed over slabs, |M| / N is |m|)
+        if (C->series_absm) C->series_absm[k] = a.wrap ? fabs(M) / (double)a.N : M;
         C->t = C->t + 1;
     }
 }
@@ -91,7 +103,8 @@ __global__ void __launch_bounds__(256) i8_generic(const I8Args a)
         uint32_t rr[4] = {0u, 0u, 0u, 0u};
         if (a.update) {
             const uint4 r = philox4x32_10(
-                make_uint4((uint32_t)g, t, a.replica, (kSweep << 1) | (uint32_t)a.c), a.rk);
+                make_uint4((uint32_t)(g + (a.gofs >> 2)), t, a.replica,
+                           (kSweep << 1) | (uint32_t)a.c), a.rk);
             rr[0] = r.x; rr[1] = r.y; rr[2] = r.z; rr[3] = r.w;
         }
 #pragma unroll
@@ -103,13 +116,16 @@ __global__ void __launch_bounds__(256) i8_generic(const I8Args a)
             const long long rrow = i0 / L;
             const int y = (int)(rrow % L);
             const int z = (int)(rrow / L);
-            x += (a.c + y + z) & 1;
+            x += (a.c + y + z + a.par) & 1;
             int hs = 0;
 #pragma unroll
             for (int mu = 0; mu < D; ++mu) {
                 int cm[3] = {x, y, z}, cp[3] = {x, y, z};
-                cm[mu] = cm[mu] == 0 ? L - 1 : cm[mu] - 1;
-                cp[mu] = cp[mu] == L - 1 ? 0 : cp[mu] + 1;
+                // the slowest axis of a slab ends in halo planes -1 and Lz
+                const bool wr = mu != D - 1 || a.wrap;
+                const int ext = mu == D - 1 ? a.Lz : L;
+                cm[mu] = cm[mu] == 0 ? (wr ? ext - 1 : -1) : cm[mu] - 1;
+                cp[mu] = cp[mu] == ext - 1 ? (wr ? 0 : ext) : cp[mu] + 1;
                 const long long nm =
                     (cm[0] + (long long)L * (cm[1] + (long long)L * cm[2])) >> 1;
                 const long long np =
@@ -207,9 +223,12 @@ __global__ void __launch_bounds__(128) i8_stream(const I8Args a)
         __syncthreads();
     }
     const uint32_t t = (uint32_t)a.ctrl->t;
-    const int W = a.W, L = a.L, R = a.R;
+    const int W = a.W, L = a.L, R = a.R, Lz = a.Lz;
     const int W16 = W >> 4;
-    const long long nseg = L / R;
+    const long long nseg = Lz / R;
+    // neighbouring plane along the slowest axis: periodic, or a halo plane
+    auto zprev = [&](int m) { return m == 0 ? (a.wrap ? Lz - 1 : -1) : m - 1; };
+    auto znext = [&](int m) { return m == Lz - 1 ? (a.wrap ? 0 : Lz) : m + 1; };
     const long long nitems = (long long)W16 * (D == 3 ? L : 1) * nseg;
     const uint32_t ctr_w = (kSweep << 1) | (uint32_t)a.c;
     const uint32_t two_d = 0x01010101u * (uint32_t)(2 * D);
@@ -232,7 +251,7 @@ __global__ void __launch_bounds__(128) i8_stream(const I8Args a)
         const int m0 = seg * R;
         auto off = [&](int yy, int zz) -> long long { return ((long long)zz * L + yy) * W; };
         auto moff = [&](int m) -> long long { return D == 3 ? off(y3, m) : off(m, 0); };
-        const int mprev = m0 == 0 ? L - 1 : m0 - 1;
+        const int mprev = zprev(m0);
         uint4 prev = ld_rows(a.oth + moff(mprev) + k0);
         uint4 cur = ld_rows(a.oth + moff(m0) + k0);
         uint4 jprev = make_uint4(0, 0, 0, 0);
@@ -257,10 +276,10 @@ __global__ void __launch_bounds__(128) i8_stream(const I8Args a)
         };
         int yy0, zz0;
         row_of(m0, yy0, zz0);
-        uint4 next = ld_rows(a.oth + moff(m0 == L - 1 ? 0 : m0 + 1) + k0);
+        uint4 next = ld_rows(a.oth + moff(znext(m0)) + k0);
         uint4 A_nx = *reinterpret_cast<const uint4*>(a.own + off(yy0, zz0) + k0);
         uint32_t edge_nx =
-            (uint8_t)a.oth[off(yy0, zz0) + edge_idx((yy0 + zz0 + a.c) & 1)];
+            (uint8_t)a.oth[off(yy0, zz0) + edge_idx((yy0 + zz0 + a.c + a.par) & 1)];
         // 3D: rows y -/+ 1 of the current plane, also one iteration ahead
         const int y_m = y3 == 0 ? L - 1 : y3 - 1, y_p = y3 == L - 1 ? 0 : y3 + 1;
         uint4 ym_nx = make_uint4(0, 0, 0, 0), yp_nx = ym_nx;
@@ -272,7 +291,7 @@ __global__ void __launch_bounds__(128) i8_stream(const I8Args a)
             const int m = m0 + r;
             int yy, zz;
             row_of(m, yy, zz);
-            const int p = (yy + zz + a.c) & 1;
+            const int p = (yy + zz + a.c + a.par) & 1;
             const long long ro = off(yy, zz);
             const int eidx = edge_idx(p);
             const uint4 A = A_nx;
@@ -281,12 +300,12 @@ __global__ void __launch_bounds__(128) i8_stream(const I8Args a)
             const uint4 ym = ym_nx, yp = yp_nx;
             if (r + 1 < R) {
                 const int m1 = m + 1;
-                const int m2 = m1 == L - 1 ? 0 : m1 + 1;
+                const int m2 = znext(m1);
                 int y1, z1;
                 row_of(m1, y1, z1);
                 next = ld_rows(a.oth + moff(m2) + k0);
                 A_nx = *reinterpret_cast<const uint4*>(a.own + off(y1, z1) + k0);
-                edge_nx = (uint8_t)a.oth[off(y1, z1) + edge_idx((y1 + z1 + a.c) & 1)];
+                edge_nx = (uint8_t)a.oth[off(y1, z1) + edge_idx((y1 + z1 + a.c + a.par) & 1)];
                 if (D == 3) {
                     ym_nx = ld_rows(a.oth + off(y_m, z1) + k0);
                     yp_nx = ld_rows(a.oth + off(y_p, z1) + k0);
@@ -313,7 +332,7 @@ __global__ void __launch_bounds__(128) i8_stream(const I8Args a)
                     jnext = ld_rows(a.Joth[2] + ro + k0);
                 }
             }
-            const uint32_t g0 = (uint32_t)((ro + k0) >> 2);
+            const uint32_t g0 = (uint32_t)((ro + a.gofs + k0) >> 2);
             uint4 Anew;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -446,7 +465,9 @@ __global__ void __launch_bounds__(kFinishThreads) i8_finish_kernel(const I8Args 
 
 // ------------------------------------------------------ init / layout ----
 
-__global__ void i8_init_kernel(int8_t* s0, int8_t* s1, long long H, uint32_t replica, RoundKeys rk)
+// gofs: global colour index of local entry 0 (a multiple of 4; 0 for a whole lattice)
+__global__ void i8_init_kernel(int8_t* s0, int8_t* s1, long long H, uint32_t replica, RoundKeys rk,
+                               long long gofs)
 {
     const long long ng = (H + 3) >> 2;
     for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < 2 * ng;
@@ -454,7 +475,7 @@ __global__ void i8_init_kernel(int8_t* s0, int8_t* s1, long long H, uint32_t rep
         const int c = (int)(g / ng);
         const long long gg = g % ng;
         const uint4 r = philox4x32_10(
-            make_uint4((uint32_t)gg, 0u, replica, (kInit << 1) | (uint32_t)c), rk);
+            make_uint4((uint32_t)(gg + (gofs >> 2)), 0u, replica, (kInit << 1) | (uint32_t)c), rk);
         const uint32_t rr[4] = {r.x, r.y, r.z, r.w};
         int8_t* s = c ? s1 : s0;
 #pragma unroll
@@ -465,25 +486,28 @@ __global__ void i8_init_kernel(int8_t* s0, int8_t* s1, long long H, uint32_t rep
     }
 }
 
-__device__ __forceinline__ int colour_of(long long i, int L)
+// colour of local natural site i; par = parity of the first plane's global index
+__device__ __forceinline__ int colour_of(long long i, int L, int par)
 {
     const int x = (int)(i % L);
     const long long r = i / L;
-    return (x + (int)(r % L) + (int)(r / L)) & 1;
+    return (x + (int)(r % L) + (int)(r / L) + par) & 1;
 }
 
-__global__ void i8_scatter_kernel(int8_t* s0, int8_t* s1, const int8_t* nat, long long N, int L)
+__global__ void i8_scatter_kernel(int8_t* s0, int8_t* s1, const int8_t* nat, long long N, int L,
+                                  int par)
 {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
          i += (long long)gridDim.x * blockDim.x)
-        (colour_of(i, L) ? s1 : s0)[i >> 1] = (int8_t)(nat[i] < 0);
+        (colour_of(i, L, par) ? s1 : s0)[i >> 1] = (int8_t)(nat[i] < 0);
 }
 
-__global__ void i8_gather_kernel(const int8_t* s0, const int8_t* s1, int8_t* nat, long long N, int L)
+__global__ void i8_gather_kernel(const int8_t* s0, const int8_t* s1, int8_t* nat, long long N,
+                                 int L, int par)
 {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
          i += (long long)gridDim.x * blockDim.x)
-        nat[i] = (colour_of(i, L) ? s1 : s0)[i >> 1] ? (int8_t)-1 : (int8_t)1;
+        nat[i] = (colour_of(i, L, par) ? s1 : s0)[i >> 1] ? (int8_t)-1 : (int8_t)1;
 }
 
 struct BondPtrs {
@@ -501,7 +525,7 @@ __global__ void bonds_scatter_kernel(BondPtrs bp, const int8_t* nat, long long N
         const int8_t v = nat[k];
         if (v == 0) f |= 1u;
         if (v < -1 || v > 1) f |= 2u;
-        bp.p[colour_of(i, L)][mu][i >> 1] = (int8_t)(v == 0 ? 2 : (v < 0 ? 1 : 0));
+        bp.p[colour_of(i, L, 0)][mu][i >> 1] = (int8_t)(v == 0 ? 2 : (v < 0 ? 1 : 0));
     }
     if (f) atomicOr(flags, f);
 }
@@ -538,6 +562,10 @@ I8Args make_args(const sl_lattice* h, int c)
     a.update = 1;
     a.advance = 0;
     a.defer = 0;
+    a.Lz = h->Lz;
+    a.wrap = !h->slab;
+    a.par = h->z0 & 1;
+    a.gofs = (long long)h->z0 * h->P;
     return a;
 }
 
@@ -556,7 +584,8 @@ int pick_rows(const sl_lattice* h)
     const long long W16 = h->W / 16;
     const long long cross = h->d == 3 ? h->L : 1;
     int R = h->d == 3 ? 8 : 16;
-    while (R > 1 && (h->L % R != 0 || W16 * cross * (h->L / R) < (long long)h->sms * 512)) R >>= 1;
+    while (R > 1 && (h->Lz % R != 0 || W16 * cross * (h->Lz / R) < (long long)h->sms * 512))
+        R >>= 1;
     return R;
 }
 
@@ -564,7 +593,7 @@ cudaError_t launch_pass(const sl_lattice* h, I8Args a, cudaStream_t s, bool stre
 {
     if (stream) {
         a.R = pick_rows(h);
-        const long long items = (long long)(h->W / 16) * (h->d == 3 ? h->L : 1) * (h->L / a.R);
+        const long long items = (long long)(h->W / 16) * (h->d == 3 ? h->L : 1) * (h->Lz / a.R);
         const int grid = grid_for(items, 128);
         const bool bonds = a.Jown[0] != nullptr;
         const bool jneg = a.tab.sigma_neg != 0;
@@ -607,21 +636,21 @@ cudaError_t ising_i8_init(const sl_lattice* h, cudaStream_t s)
 {
     i8_init_kernel<<<grid_for(2 * ((h->H + 3) >> 2), 256), 256, 0, s>>>(
         (int8_t*)h->spins[0], (int8_t*)h->spins[1], h->H, h->replica,
-        make_round_keys(h->init_seed));
+        make_round_keys(h->init_seed), (long long)h->z0 * h->P);
     return cudaGetLastError();
 }
 
 cudaError_t ising_i8_scatter(const sl_lattice* h, const int8_t* nat, cudaStream_t s)
 {
-    i8_scatter_kernel<<<grid_for(h->N, 256), 256, 0, s>>>((int8_t*)h->spins[0],
-                                                          (int8_t*)h->spins[1], nat, h->N, h->L);
+    i8_scatter_kernel<<<grid_for(h->N, 256), 256, 0, s>>>(
+        (int8_t*)h->spins[0], (int8_t*)h->spins[1], nat, h->N, h->L, h->z0 & 1);
     return cudaGetLastError();
 }
 
 cudaError_t ising_i8_gather(const sl_lattice* h, int8_t* nat, cudaStream_t s)
 {
     i8_gather_kernel<<<grid_for(h->N, 256), 256, 0, s>>>(
-        (const int8_t*)h->spins[0], (const int8_t*)h->spins[1], nat, h->N, h->L);
+        (const int8_t*)h->spins[0], (const int8_t*)h->spins[1], nat, h->N, h->L, h->z0 & 1);
     return cudaGetLastError();
 }
 
@@ -659,6 +688,15 @@ cudaError_t ising_i8_sweeps(const sl_lattice* h, const SweepParams& p, int64_t c
         }
     }
     return cudaSuccess;
+}
+
+cudaError_t ising_i8_pass(const sl_lattice* h, const SweepParams& p, int c, cudaStream_t s)
+{
+    const bool stream = h->kernel == 2 || (h->kernel == 0 && stream_ok(h));
+    I8Args a = make_args(h, c);
+    a.tab = p.tab;
+    a.rk = p.rk;
+    return launch_pass(h, a, s, stream);
 }
 
 cudaError_t ising_i8_measure_advance(const sl_lattice* h, cudaStream_t s)

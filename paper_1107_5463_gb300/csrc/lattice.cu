@@ -71,18 +71,23 @@ int check_config(int d, int L, int n, int j_layout, int storage)
     return SL_OK;
 }
 
-Layout make_layout(int d, int L, int n, int j_layout, int storage)
+// Lz planes along the slowest axis (L for a whole lattice); a slab stores Lz + 2
+// planes per colour (halo planes before and after its own).
+Layout make_layout(int d, int L, int n, int j_layout, int storage, int Lz = 0, bool slab = false)
 {
     Layout y;
-    const size_t N = (size_t)L * L * (d == 3 ? L : 1), H = N / 2;
+    if (Lz <= 0) Lz = L;
+    const size_t P = (size_t)L * (d == 3 ? L : 1) / 2;  // sites of one colour per plane
+    const size_t H = P * Lz, N = 2 * H;
+    const size_t Hs = P * (Lz + (slab ? 2 : 0));          // stored entries per colour
     switch (storage) {
-    case SL_STORE_I8: y.spin_colour = H; break;
-    case SL_STORE_BITS: y.spin_colour = H / 8; break;
-    case SL_STORE_F32_ANGLE: y.spin_colour = 4 * H; break;
-    default: y.spin_colour = 12 * H; break;
+    case SL_STORE_I8: y.spin_colour = Hs; break;
+    case SL_STORE_BITS: y.spin_colour = Hs / 8; break;
+    case SL_STORE_F32_ANGLE: y.spin_colour = 4 * Hs; break;
+    default: y.spin_colour = 12 * Hs; break;
     }
     const size_t bond_elem = n == 1 ? 1 : 4;
-    y.bond_array = j_layout == SL_J_BONDS ? H * bond_elem : 0;
+    y.bond_array = j_layout == SL_J_BONDS ? H * bond_elem : 0;  // slabs have uniform J
     const size_t nat_elem = n == 1 ? 1 : (n == 2 ? 4 : 12);
     y.staging = N * nat_elem;
     if (j_layout == SL_J_BONDS && d * N * bond_elem > y.staging) y.staging = d * N * bond_elem;
@@ -114,6 +119,13 @@ __global__ void set_series_kernel(Ctrl* c, long long base, double* E, double* m)
 }
 
 __global__ void set_t_kernel(Ctrl* c, unsigned long long t) { c->t = t; }
+
+}  // namespace
+
+size_t slab_required_bytes(int d, int L, int storage, int Lz)
+{
+    return make_layout(d, L, 1, SL_J_UNIFORM, storage, Lz, true).total;
+}
 
 // Exact integer thresholds for the Ising classes (see ising_i8.cu).  Class k
 // has s_i h_i sign(J) = 2d - 2k (+-1 couplings) or 2d - k (couplings that may
@@ -171,6 +183,8 @@ int ising_table(const sl_lattice* h, double beta, IsingTable* tab)
     }
     return SL_OK;
 }
+
+namespace {
 
 int model_sweeps(const sl_lattice* h, const SweepParams& p, int64_t count, cudaStream_t s)
 {
@@ -268,13 +282,25 @@ int sl_create(int d, int L, int n, int j_layout, int storage, double J, const vo
               uint64_t seed, uint32_t replica, void* dev_buf, size_t dev_buf_bytes, void* stream,
               sl_lattice** out)
 {
+    return create_lattice(d, L, n, j_layout, storage, J, J_bonds, seed, replica, false, 0, L,
+                          dev_buf, dev_buf_bytes, stream, out);
+}
+
+}  // extern "C"
+
+namespace spinmc {
+
+int create_lattice(int d, int L, int n, int j_layout, int storage, double J, const void* J_bonds,
+                   uint64_t seed, uint32_t replica, bool slab, int z0, int Lz, void* dev_buf,
+                   size_t dev_buf_bytes, void* stream, sl_lattice** out)
+{
     if (!out) return fail(SL_EINVAL, "out is NULL");
     *out = nullptr;
     int st = check_config(d, L, n, j_layout, storage);
     if (st != SL_OK) return st;
     if (!std::isfinite(J)) return fail(SL_EINVAL, "J must be finite");
     if (j_layout == SL_J_BONDS && !J_bonds) return fail(SL_EINVAL, "SL_J_BONDS needs J_bonds");
-    const Layout y = make_layout(d, L, n, j_layout, storage);
+    const Layout y = make_layout(d, L, n, j_layout, storage, Lz, slab);
     void* owned = nullptr;
     if (!dev_buf) {
         const cudaError_t e = cudaMalloc(&owned, y.total);
@@ -301,7 +327,11 @@ int sl_create(int d, int L, int n, int j_layout, int storage, double J, const vo
     h->n = n;
     h->j_layout = j_layout;
     h->storage = storage;
-    h->N = (int64_t)L * L * (d == 3 ? L : 1);
+    h->P = (int64_t)L * (d == 3 ? L : 1) / 2;
+    h->slab = slab ? 1 : 0;
+    h->z0 = z0;
+    h->Lz = Lz;
+    h->N = 2 * h->P * Lz;
     h->H = h->N / 2;
     h->W = L / 2;
     h->J = J;
@@ -316,9 +346,14 @@ int sl_create(int d, int L, int n, int j_layout, int storage, double J, const vo
             sms < 1)
             sms = 1;
         h->sms = sms;
+        h->device = dev;
     }
+    // a slab's colour arrays start with a halo plane: spins[c] points at its
+    // first own plane, the halos sit at planes -1 and Lz
+    const size_t halo_bytes =
+        !slab ? 0 : (storage == SL_STORE_I8 ? (size_t)h->P : (size_t)h->P / 8);
     for (int c = 0; c < 2; ++c) {
-        h->spins[c] = base + y.off_spins[c];
+        h->spins[c] = base + y.off_spins[c] + halo_bytes;
         for (int mu = 0; mu < 3; ++mu)
             h->bonds[c][mu] =
                 (j_layout == SL_J_BONDS && mu < d) ? (void*)(base + y.off_bonds[c][mu]) : nullptr;
@@ -339,6 +374,8 @@ int sl_create(int d, int L, int n, int j_layout, int storage, double J, const vo
     h->graph = nullptr;
     h->graph1 = nullptr;
     h->graph_sweeps = 0;
+    h->next_colour = 0;
+    h->ev = nullptr;
     h->owned_buf = owned;
     h->ws = nullptr;
     h->ws_bytes = 0;
@@ -383,10 +420,17 @@ int sl_create(int d, int L, int n, int j_layout, int storage, double J, const vo
     return SL_OK;
 }
 
+}  // namespace spinmc
+
+extern "C" {
+
 int sl_sweep_series(sl_lattice* h, double beta, int64_t nsweeps, uint64_t seed, double* dev_E,
                     double* dev_absm)
 {
     if (!h) return fail(SL_EINVAL, "lattice is NULL");
+    if (h->slab)
+        return fail(SL_EINVAL, "a slab sweeps by sl_slab_pass between halo exchanges "
+                               "(or sl_slabs_sweep)");
     if (nsweeps < 0) return fail(SL_EINVAL, "nsweeps must be >= 0");
     if (!(beta >= 0.0) || !std::isfinite(beta))
         return fail(SL_EINVAL, "beta must be finite and >= 0 (got %g)", beta);
@@ -503,6 +547,7 @@ int sl_set_state(sl_lattice* h, int64_t sweeps_done)
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "sl_set_state");
     h->sweeps_done = sweeps_done;
+    h->next_colour = 0;
     return SL_OK;
 }
 
@@ -548,6 +593,8 @@ int sl_set_option(sl_lattice* h, int option, int64_t value)
             return fail(SL_EINVAL, "the heat-bath rule needs byte (Ising) or FP32 storage");
         if (value == SL_UPDATE_SW && h->storage != SL_STORE_I8)
             return fail(SL_EINVAL, "Swendsen-Wang updates need Ising byte storage");
+        if (value == SL_UPDATE_SW && h->slab)
+            return fail(SL_EINVAL, "Swendsen-Wang updates need the whole lattice, not a slab");
         if (value != SL_UPDATE_METROPOLIS && h->multihit > 0)
             return fail(SL_EINVAL, "multi-hit sweeps use the Metropolis rule");
         if (value == SL_UPDATE_SW) {
@@ -575,8 +622,9 @@ int sl_set_option(sl_lattice* h, int option, int64_t value)
     case SL_OPT_MULTIHIT:
         if (value < 0 || value > 65536) return fail(SL_EINVAL, "multihit must be in [0, 65536]");
         if (value > 0 && (h->storage != SL_STORE_I8 || h->j_layout != SL_J_UNIFORM ||
-                          h->update != 0))
-            return fail(SL_EINVAL, "multi-hit sweeps need Ising bytes, uniform J and Metropolis");
+                          h->update != 0 || h->slab))
+            return fail(SL_EINVAL, "multi-hit sweeps need a whole lattice of Ising bytes, "
+                                   "uniform J and Metropolis");
         if (value > 0 && !tile_size_ok(h->d, h->L, h->tile))
             return fail(SL_EINVAL, "tile side %d does not fit L = %d (L %% 2T == 0)", h->tile,
                         h->L);
@@ -598,6 +646,7 @@ void sl_destroy(sl_lattice* h)
     if (!h) return;
     cudaStreamSynchronize(h->stream);
     drop_graphs(h);
+    if (h->ev) cudaEventDestroy(h->ev);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->owned_buf) cudaFree(h->owned_buf);
     if (h->ws_owned) cudaFree(h->ws_owned);

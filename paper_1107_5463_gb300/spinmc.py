@@ -59,6 +59,16 @@ _sig("sl_set_option", _int, _vp, _int, _i64)
 _sig("sl_destroy", None, _vp)
 _sig("sl_workspace_bytes", _int, _vp, _int, ctypes.POINTER(_sz))
 _sig("sl_attach_workspace", _int, _vp, _vp, _sz)
+_sig("sl_slab_required_bytes", _int, _int, _int, _int, _int, _int, ctypes.POINTER(_sz))
+_sig("sl_slab_create", _int, _int, _int, _int, _dbl, _u64, _u32, _int, _int, _vp, _sz, _vp,
+     ctypes.POINTER(_vp))
+_sig("sl_slab_planes", _int, _vp, _int, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+     ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_sz))
+_sig("sl_slab_series", _int, _vp, _vp, _vp)
+_sig("sl_slab_pass", _int, _vp, _dbl, _u64, _int)
+_sig("sl_slabs_exchange", _int, _vp, _int, _int)
+_sig("sl_slabs_sweep", _int, _vp, _int, _dbl, _i64, _u64, _vp)
+_sig("sl_series_reduce", _int, _vp, _int, _i64, _dbl, _vp, _vp, _vp)
 _sig("sl_batch_required_bytes", _int, _int, _vp, _int, _int, _vp, ctypes.POINTER(_sz))
 _sig("sl_batch_create", _int, _int, _vp, _int, _int, _vp, _u64, _u32, _vp, _sz, _vp,
      ctypes.POINTER(_vp))
@@ -189,6 +199,58 @@ def sl_workspace_bytes(h, update):
 
 def sl_attach_workspace(h, dev_buf, nbytes):
     _check(_lib.sl_attach_workspace(h, _addr(dev_buf), nbytes), "sl_attach_workspace")
+
+
+def sl_slab_required_bytes(d, L, storage, z0, Lz):
+    out = _sz()
+    _check(_lib.sl_slab_required_bytes(d, L, storage, z0, Lz, ctypes.byref(out)),
+           "sl_slab_required_bytes")
+    return out.value
+
+
+def sl_slab_create(d, L, storage, J, seed, replica, z0, Lz, dev_buf, dev_buf_bytes, stream):
+    h = _vp()
+    _check(_lib.sl_slab_create(d, L, storage, J, seed, replica, z0, Lz, _addr(dev_buf),
+                               dev_buf_bytes, stream, ctypes.byref(h)), "sl_slab_create")
+    return h.value
+
+
+def sl_slab_planes(h, colour):
+    """(send_lo, send_hi, recv_lo, recv_hi) device addresses and the plane bytes."""
+    p = [_vp() for _ in range(4)]
+    nb = _sz()
+    _check(_lib.sl_slab_planes(h, colour, *[ctypes.byref(x) for x in p], ctypes.byref(nb)),
+           "sl_slab_planes")
+    return [x.value for x in p], nb.value
+
+
+def sl_slab_series(h, dev_E, dev_M):
+    _check(_lib.sl_slab_series(h, _addr(dev_E), _addr(dev_M)), "sl_slab_series")
+
+
+def sl_slab_pass(h, beta, seed, colour):
+    _check(_lib.sl_slab_pass(h, beta, seed, colour), "sl_slab_pass")
+
+
+def _ptr_array(xs):
+    arr = (_vp * len(xs))(*[_addr(x) for x in xs])
+    return arr
+
+
+def sl_slabs_exchange(handles, colour):
+    _check(_lib.sl_slabs_exchange(_ptr_array(handles), len(handles), colour),
+           "sl_slabs_exchange")
+
+
+def sl_slabs_sweep(handles, beta, nsweeps, seed, parts=None):
+    p = None if parts is None else _ptr_array(parts)
+    _check(_lib.sl_slabs_sweep(_ptr_array(handles), len(handles), beta, nsweeps, seed, p),
+           "sl_slabs_sweep")
+
+
+def sl_series_reduce(parts, nsweeps, N, dev_E, dev_absm, stream):
+    _check(_lib.sl_series_reduce(_ptr_array(parts), len(parts), nsweeps, N, _addr(dev_E),
+                                 _addr(dev_absm), stream), "sl_series_reduce")
 
 
 def _i32_array(xs):
@@ -468,6 +530,64 @@ class Lattice:
             self.ws = torch.empty(need, dtype=torch.uint8, device=self.buf.device)
             sl_attach_workspace(self.h, self.ws, need)
         sl_set_option(self.h, SL_OPT_UPDATE, rule)
+
+
+class Slab(Lattice):
+    """One slab (planes z0 .. z0 + Lz - 1 along the slowest axis) of an L^d
+    Ising lattice, its device buffer a torch CUDA tensor.  The planes of the
+    halo exchange are exposed as uint8 tensor views of that buffer."""
+
+    def __init__(self, d, L, z0, Lz, J=1.0, seed=0, replica=0, storage=SL_STORE_I8, stream=None,
+                 device="cuda"):
+        import torch
+        self.d, self.L, self.n = d, L, 1
+        self.z0, self.Lz = z0, Lz
+        self.N = L ** (d - 1) * Lz
+        self.storage = storage
+        nbytes = sl_slab_required_bytes(d, L, storage, z0, Lz)
+        self.buf = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        self.stream = torch.cuda.current_stream(self.buf.device) if stream is None else stream
+        self._bonds_keepalive = None
+        self.h = sl_slab_create(d, L, storage, J, seed, replica, z0, Lz, self.buf, nbytes,
+                                self.stream.cuda_stream)
+
+    def planes(self, colour):
+        """(send_lo, send_hi, recv_lo, recv_hi) as uint8 views of the buffer."""
+        addrs, nb = sl_slab_planes(self.h, colour)
+        base = self.buf.data_ptr()
+        return [self.buf[a - base:a - base + nb] for a in addrs]
+
+    def series(self, dev_E, dev_M):
+        sl_slab_series(self.h, dev_E, dev_M)
+
+    def pass_(self, beta, seed, colour):
+        sl_slab_pass(self.h, beta, seed, colour)
+
+    def reduce_series(self, EM, nsweeps, N):
+        """(E, |m|) from summed shares (nsweeps energies, then nsweeps M)."""
+        import torch
+        E = torch.empty(nsweeps, dtype=torch.float64, device=self.buf.device)
+        m = torch.empty_like(E)
+        sl_series_reduce([EM], nsweeps, N, E, m, self.stream.cuda_stream)
+        return E, m
+
+
+def slabs_sweep(slabs, beta, nsweeps, seed):
+    """nsweeps sweeps of in-process slabs (which tile the lattice in order)
+    with the library's exchanges; returns (E, |m|) of the whole lattice as
+    torch float64 tensors on slab 0's device."""
+    import torch
+    dev = slabs[0].buf.device
+    if any(s.buf.device != dev for s in slabs):
+        raise ValueError("slabs_sweep sums the series on one device; call sl_slabs_sweep "
+                         "and sl_series_reduce for slabs on several devices")
+    parts = [torch.empty(2 * nsweeps, dtype=torch.float64, device=dev) for s in slabs]
+    sl_slabs_sweep([s.h for s in slabs], beta, nsweeps, seed, parts)
+    E = torch.empty(nsweeps, dtype=torch.float64, device=dev)
+    m = torch.empty_like(E)
+    N = float(slabs[0].L ** slabs[0].d)
+    sl_series_reduce(parts, nsweeps, N, E, m, slabs[0].stream.cuda_stream)
+    return E, m
 
 
 class Walkers:
