@@ -31,9 +31,24 @@ UNIT = "flips/ns"
 
 # bytes: algorithmic HBM bytes per site update of one colour pass (read the
 # updated colour and the other colour, write the updated colour)
-# ops: algorithmic 32-bit integer operations per site update (Ising: a quarter
-# of a Philox4x32-10 call = 10 rounds x (2 mulhi + 2 mullo + 4 xor) / 4 = 20,
-# plus about 8 for the neighbour count, threshold compares and flip)
+# ops: algorithmic 32-bit lane operations (integer and FP32) per site update:
+#   Ising bytes 28: a quarter of a Philox4x32-10 call = 10 rounds x (2 mulhi +
+#     2 mullo + 4 xor) / 4 = 20, plus about 8 for the neighbour count,
+#     threshold compares and flip (30 in 3D: two more neighbours);
+#   Ising bits 26 (2D) / 28 (3D): the quarter call, the d threshold compares
+#     with their bit insertion, a share of the word-wide neighbour logic;
+#   XY 66: half a call (40), sin/cos of the proposal (and the own and one
+#     neighbour angle, computed once per value) and the FP32 field, dE and
+#     acceptance (about 26); heat-bath 100 (about 1.3 Best-Fisher attempts of
+#     half a call each, the sampler's setup and the new angle);
+#   Heisenberg 120 in 3D / 110 in 2D: one call (80), the sphere point, the
+#     FP32 field of 2d neighbours and dE, the acceptance; heat-bath 140 (the
+#     exponential inverse and the basis around h);
+#   spin-glass batch 28 per (site, replica): the quarter call and d threshold
+#     compares; the neighbour logic is word-wide over 32 replicas;
+#   walkers 40 (Wang-Landau) / 36 (multicanonical) per attempted flip: the
+#     quarter call, five lattice words, the level step, the decision and the
+#     histogram and ln g updates.
 WORKLOADS = {
     "ising2d_L16384_i8": dict(d=2, L=16384, n=1, beta=0.440687, storage="i8", bytes=3.0, ops=28,
                               desc="2D Ising ferromagnet J=1, L=16384 periodic, int8 spins, "
@@ -45,12 +60,14 @@ WORKLOADS = {
                                        bytes=3.0, ops=28, update=1,
                                        desc="2D Ising, L=16384, int8 spins, heat-bath rule"),
     "ising2d_L16384_i8_k100": dict(d=2, L=16384, n=1, beta=0.440687, storage="i8", bytes=0.0,
-                                   multihit=100, tile=16, paper_flips_per_ns=1 / 0.034,
+                                   ops=28, multihit=100, tile=16, paper_flips_per_ns=1 / 0.034,
                                    desc="2D Ising, L=16384, int8 spins, k=100 multi-hit in "
                                         "16x16 tiles (the mode of the paper's Table 1)"),
     "ising2d_L16384_bits": dict(d=2, L=16384, n=1, beta=0.440687, storage="bits", bytes=0.375,
+                                ops=26,
                                 desc="2D Ising, L=16384, one bit per spin"),
     "ising3d_L512_bits": dict(d=3, L=512, n=1, beta=0.2216546, storage="bits", bytes=0.375,
+                              ops=28,
                               desc="3D Ising, L=512, one bit per spin"),
     "ising2d_L8192_sw": dict(d=2, L=8192, n=1, beta=0.440687, storage="i8", bytes=16.0,
                              update=2, paper_flips_per_ns=1 / 4.62,
@@ -58,42 +75,45 @@ WORKLOADS = {
                              desc="2D Ising ferromagnet J=1, L=8192, int8 spins, beta_c, "
                                   "Swendsen-Wang cluster updates (the paper's Table 1 "
                                   "cluster row)"),
-    "wl2d_L64_windows": dict(d=2, L=64, n=1, beta=None, storage="walkers", bytes=0.0,
+    "wl2d_L64_windows": dict(d=2, L=64, n=1, beta=None, storage="walkers", bytes=0.0, ops=40,
                              kind="wl", wpw=128, width=4, paper_flips_per_ns=1 / 0.94,
                              desc="2D Ising L=64, Wang-Landau walkers in 1023 windows of 5 "
                                   "levels (dE = 16) sharing edge levels, 128 walkers each "
                                   "(the paper's Table 1 Wang-Landau row)"),
-    "muca2d_L64_windows": dict(d=2, L=64, n=1, beta=None, storage="walkers", bytes=0.0,
+    "muca2d_L64_windows": dict(d=2, L=64, n=1, beta=None, storage="walkers", bytes=0.0, ops=36,
                                kind="muca", wpw=128, width=4, paper_flips_per_ns=1 / 0.33,
                                desc="2D Ising L=64, multicanonical walkers in 1023 windows of 5 "
                                     "levels sharing edge levels, 128 walkers each, weights from "
                                     "a Wang-Landau run (the paper's Table 1 multicanonical row)"),
-    "heis3d_L256_f32": dict(d=3, L=256, n=3, beta=0.693, storage="vec", bytes=36.0,
+    "heis3d_L256_f32": dict(d=3, L=256, n=3, beta=0.693, storage="vec", bytes=36.0, ops=120,
                             desc="3D Heisenberg J=1, L=256, FP32 unit vectors, beta=0.693, "
                                  "renormalised every 16 sweeps"),
-    "heis2d_L4096_f32": dict(d=2, L=4096, n=3, beta=0.693, storage="vec", bytes=24.0,
+    "heis2d_L4096_f32": dict(d=2, L=4096, n=3, beta=0.693, storage="vec", bytes=24.0, ops=110,
                              paper_flips_per_ns=1 / 0.50,
                              desc="2D Heisenberg J=1, L=4096, FP32 unit vectors, FP64 aggregates "
                                   "(the paper's Table 1 single-precision row)"),
     "heis2d_L4096_f32_fast": dict(d=2, L=4096, n=3, beta=0.693, storage="vec", bytes=24.0,
+                                  ops=110,
                                   fast=1, paper_flips_per_ns=1 / 0.18,
                                   desc="2D Heisenberg L=4096 with hardware sin/cos/exp "
                                        "intrinsics (the paper's Table 1 fast-math row)"),
-    "ising2d_L32_i8_k100": dict(d=2, L=32, n=1, beta=0.440687, storage="i8", bytes=0.0,
+    "ising2d_L32_i8_k100": dict(d=2, L=32, n=1, beta=0.440687, storage="i8", bytes=0.0, ops=28,
                                 multihit=100, tile=16, paper_flips_per_ns=1 / 1.60,
                                 desc="2D Ising L=32, k=100 multi-hit in 16x16 tiles (the paper's "
                                      "Table 1 small-lattice row)"),
-    "xy2d_L4096_f32": dict(d=2, L=4096, n=2, beta=1.12, storage="angle", bytes=12.0,
+    "xy2d_L4096_f32": dict(d=2, L=4096, n=2, beta=1.12, storage="angle", bytes=12.0, ops=66,
                            desc="2D XY J=1, L=4096, FP32 angles, beta=1.12"),
     "heis3d_L256_f32_heatbath": dict(d=3, L=256, n=3, beta=0.693, storage="vec", bytes=36.0,
+                                     ops=140,
                                      update=1,
                                      desc="3D Heisenberg L=256, FP32 vectors, heat-bath rule "
                                           "(exponential draws about the local field)"),
     "xy2d_L4096_f32_heatbath": dict(d=2, L=4096, n=2, beta=1.12, storage="angle", bytes=12.0,
+                                    ops=100,
                                     update=1,
                                     desc="2D XY L=4096, FP32 angles, heat-bath rule (Best-Fisher "
                                          "von Mises draws)"),
-    "ea3d_batch_1024x32": dict(d=3, L=32, n=1, beta=None, storage="batch", bytes=0.0,
+    "ea3d_batch_1024x32": dict(d=3, L=32, n=1, beta=None, storage="batch", bytes=0.0, ops=28,
                                samples=1024, temps=32,
                                desc="3D Edwards-Anderson +-J, 1024 samples of sides "
                                     "[8,12,16,24,32][s mod 5] x 32 temperatures geometric in "
@@ -282,33 +302,54 @@ def time_batch(spinmc, wl, steps, warmup, want_clocks, local, rank=0, world=1):
     return ms, cl, tuning
 
 
-def roofline_line(wl, N, hits, launch_ms, achieved_gbs, hbm, peak_kind, traffic, kernel_name,
-                  bytes_per_launch):
-    """The binding roofline of the dominant kernel: the slower of the HBM
-    bound (algorithmic bytes) and the integer-issue bound (algorithmic ops)
-    for the Ising byte paths, which are ALU-bound; the HBM roofline
-    otherwise.  Both figures are per launch (one colour pass)."""
-    hbm_obj = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
-               "frac": achieved_gbs / hbm, "peak_kind": peak_kind, "traffic": traffic,
-               "kernel": kernel_name, "bytes_per_launch": bytes_per_launch,
-               "launch_ms": launch_ms}
-    if not wl.get("ops"):
-        return hbm_obj
-    ops_per_launch = wl["ops"] * hits * (N // 2)
-    achieved = ops_per_launch / (launch_ms * 1e-3) / 1e12
-    peak = alu_peak_tops()
-    alu_bound = peak * 1e12 / wl["ops"] / 1e9          # flips/ns at the issue peak
-    hbm_bound = hbm * 1e9 / wl["bytes"] / 1e9 if wl["bytes"] else float("inf")
-    if hbm_bound < alu_bound:
-        return hbm_obj
-    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-            "frac": achieved / peak, "peak_kind": "unit counts x max SM clock",
-            "ops_per_site": wl["ops"], "ops_per_launch": ops_per_launch,
-            "traffic": traffic, "kernel": kernel_name, "launch_ms": launch_ms,
-            "bound_flips_per_ns": {"alu": alu_bound, "hbm": hbm_bound},
-            "hbm": {"achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
-                    "frac": achieved_gbs / hbm, "peak_kind": peak_kind,
-                    "bytes_per_launch": bytes_per_launch}}
+def roofline_for(wl, flips_per_ns, launch_ms=None, hbm=None, peak_kind="measured",
+                 traffic=None, kernel_name=None, hits=1, N=None):
+    """The binding roofline of a workload's dominant kernel: the slower of its
+    HBM bound (algorithmic bytes per site update) and its issue bound
+    (algorithmic lane operations per site update against 128 lanes per SM
+    per clock at the maximum SM clock).  The achieved figure is the measured
+    site updates per ns times that bound's unit cost; the other bound is
+    reported beside it.  Per launch (one colour pass of N/2 sites) where a
+    launch time is given."""
+    if hbm is None:
+        hbm = peaks()[0]
+    ops = wl.get("ops")
+    bts = wl.get("bytes") or 0.0
+    peak_ops = alu_peak_tops() if torch_cuda() else None
+    alu_bound = peak_ops * 1e3 / ops if (ops and peak_ops) else float("inf")
+    hbm_bound = hbm / bts if bts else float("inf")
+    hbm_obj = {"achieved": flips_per_ns * bts, "peak": hbm, "unit": "GB/s",
+               "frac": flips_per_ns * bts / hbm if bts else 0.0, "peak_kind": peak_kind,
+               "bytes_per_site": bts, "bound_flips_per_ns": hbm_bound}
+    alu_obj = {"achieved": flips_per_ns * ops / 1e3 if ops else None, "peak": peak_ops,
+               "unit": "Tops/s",
+               "frac": flips_per_ns / alu_bound if alu_bound != float("inf") else None,
+               "peak_kind": "unit counts x max SM clock", "ops_per_site": ops,
+               "bound_flips_per_ns": alu_bound}
+    if hbm_bound <= alu_bound:
+        out = {"bound": "hbm"}
+        out.update({k: v for k, v in hbm_obj.items() if k != "bound_flips_per_ns"})
+        out["alu"] = alu_obj
+    else:
+        out = {"bound": "alu"}
+        out.update({k: v for k, v in alu_obj.items() if k != "bound_flips_per_ns"})
+        out["hbm"] = hbm_obj
+    out["bound_flips_per_ns"] = min(hbm_bound, alu_bound)
+    out["traffic"] = traffic
+    if kernel_name:
+        out["kernel"] = kernel_name
+    if launch_ms is not None and N is not None:
+        out["launch_ms"] = launch_ms
+        out["sites_per_launch"] = hits * (N // 2)
+    return out
+
+
+def torch_cuda():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
 
 
 def launch_shape(wl):
@@ -764,7 +805,7 @@ def main():
                        "l2": "shared-memory resident samples; no HBM traffic per sweep",
                        "parallelism": "samples split across ranks" if world > 1 else
                        "single GPU"},
-            "roofline": None,
+            "roofline": roofline_for(wl, value / world, kernel_name="ea_pt_persistent<3>"),
             "gpu_launches": 1,
             "tuning": [{"L": L, "samples_per_cta": k, "ms_per_sample_sweep": c}
                        for L, k, c in tuning],
@@ -794,7 +835,9 @@ def main():
                        "step": "one sweep of every walker",
                        "l2": "64 MB of walker lattices, L2-resident by design",
                        "parallelism": "replica per GPU" if world > 1 else "single GPU"},
-            "roofline": None, "gpu_launches": 1, "clocks": cl,
+            "roofline": roofline_for(wl, flips / (ms * 1e6) / world,
+                                     kernel_name="walk_kernel<%s>" % wl["kind"]),
+            "gpu_launches": 1, "clocks": cl,
             "over_paper_gtx480": r["over_paper_gtx480"],
         }
         if rank == 0:
@@ -823,8 +866,8 @@ def main():
                    "sites": N, "beta": wl["beta"], "step": "one full sweep + fused E,|m|",
                    "l2": "inputs larger than L2 (%d MB of spins)" % (N // 2**20),
                    "parallelism": "replica per GPU" if world > 1 else "single GPU"},
-        "roofline": roofline_line(wl, N, hits, launch_ms, achieved_gbs, hbm, peak_kind, traffic,
-                                  kernel_name, bytes_per_launch),
+        "roofline": roofline_for(wl, value / world, launch_ms, hbm, peak_kind, traffic,
+                                 kernel_name, hits, N),
         "gpu_launches": args.steps * launches_per_step + 1,
         "clocks": clocks,
         "check": {"E_per_site_last": e_last / N},
@@ -852,6 +895,8 @@ def main():
                     continue
                 if w["storage"] == "walkers":
                     var[name] = walkers_run(spinmc, w)
+                    var[name]["roofline"] = roofline_for(w, var[name]["value"],
+                                                         kernel_name="walk_kernel<%s>" % w["kind"])
                     continue
                 n_sites = w["L"] ** w["d"]
                 if w.get("multihit"):
@@ -865,18 +910,24 @@ def main():
                 gbs = w["bytes"] * (n // 2) / (vms / (2 * k) * 1e-3) / 1e9
                 var[name] = {"value": n * k * hits / (vms * 1e6), "unit": UNIT,
                              "ms_per_step": vms / k, "achieved_gbs": gbs, "hbm_frac": gbs / hbm}
-                if w.get("ops"):
-                    var[name]["alu_frac"] = (w["ops"] * var[name]["value"] * 1e9 /
-                                             (alu_peak_tops() * 1e12))
+                var[name]["roofline"] = roofline_for(w, var[name]["value"], hbm=hbm,
+                                                     peak_kind=peak_kind,
+                                                     traffic=recorded_traffic(name),
+                                                     kernel_name=launch_shape(w)[1])
                 if w.get("paper_flips_per_ns"):
                     var[name]["paper_gtx480_flips_per_ns"] = w["paper_flips_per_ns"]
                     var[name]["over_paper_gtx480"] = var[name]["value"] / w["paper_flips_per_ns"]
             var["ea3d_batch_1024x32"] = batch_run(spinmc)
+            var["ea3d_batch_1024x32"]["roofline"] = roofline_for(
+                WORKLOADS["ea3d_batch_1024x32"], var["ea3d_batch_1024x32"]["value"],
+                kernel_name="ea_pt_persistent<3>")
             # the paper's 2D spin-glass rows (L = 32; 64-bit multi-spin coding:
             # 0.0023 ns per flip on the GTX 480)
             v2 = batch_run(spinmc, plain_lattices=0, d=2, sizes=[32] * 1024)
             v2["paper_gtx480_flips_per_ns"] = 1 / 0.0023
             v2["over_paper_gtx480"] = v2["value"] / v2["paper_gtx480_flips_per_ns"]
+            v2["roofline"] = roofline_for(dict(WORKLOADS["ea3d_batch_1024x32"], d=2, ops=26),
+                                          v2["value"], kernel_name="ea_pt_persistent<2>")
             var["ea2d_batch_L32_1024x32"] = v2
             line["variants"] = var
         print(json.dumps(line), flush=True)
