@@ -419,14 +419,19 @@ def configure(spinmc, lat, wl):
         lat.set_option(spinmc.SL_OPT_MULTIHIT, wl["multihit"])
 
 
-def time_sweeps(spinmc, wl, steps, warmup, replica, want_clocks, local):
-    """Device-timed K sweeps of one lattice; returns (ms, clocks)."""
+def time_sweeps(spinmc, wl, steps, warmup, replica, want_clocks, local, shape=None):
+    """Device-timed K sweeps of one lattice, after the launch-shape autotuner
+    picked rows per thread and the grid cap (outside the timed region);
+    returns (ms, clocks, E of the last sweep) and fills `shape`."""
     import torch
     from paper_1107_5463_gb300 import inputs
     storage = spinmc.SL_STORE_BITS if wl["storage"] == "bits" else None
     lat = spinmc.Lattice(wl["d"], wl["L"], n=wl["n"], seed=inputs.DEFAULT_SEED, replica=replica,
                          storage=storage)
     configure(spinmc, lat, wl)
+    R, cap = lat.autotune(wl["beta"], 3)
+    if shape is not None:
+        shape.update(rows_per_thread=R, blocks_per_sm=cap, tuned_by="sl_autotune")
     E = torch.empty(max(steps, warmup, 1), dtype=torch.float64, device="cuda")
     m = torch.empty_like(E)
     spinmc.sl_sweep_series(lat.h, wl["beta"], warmup, inputs.DEFAULT_SEED, E, m)
@@ -846,7 +851,9 @@ def main():
         dist_teardown(world)
         return
     N = L ** d
-    ms, clocks, e_last = time_sweeps(spinmc, wl, args.steps, args.warmup, rank, rank == 0, local)
+    shape = {}
+    ms, clocks, e_last = time_sweeps(spinmc, wl, args.steps, args.warmup, rank, rank == 0, local,
+                                     shape)
     ms = max_over_ranks(ms, world)
     hits = wl.get("multihit") or 1
     value = N * hits * args.steps * world / (ms * 1e6)
@@ -869,6 +876,7 @@ def main():
         "roofline": roofline_for(wl, value / world, launch_ms, hbm, peak_kind, traffic,
                                  kernel_name, hits, N),
         "gpu_launches": args.steps * launches_per_step + 1,
+        "launch_shape": shape,
         "clocks": clocks,
         "check": {"E_per_site_last": e_last / N},
     }

@@ -83,6 +83,9 @@ extern "C" {
                                   uniform J, Metropolis); 0 = plain sweeps (default) */
 #define SL_OPT_TILE 8          /* big-tile side T for multi-hit sweeps: 8, 16 (default), 32 or
                                   64 in 2D, 8 or 16 in 3D; L % 2T == 0 */
+#define SL_OPT_BLOCKS_PER_SM 9 /* cap of a streaming kernel's grid, in blocks per SM (each
+                                  thread then takes several row segments); 0 = no cap
+                                  (default): one segment per thread up to 4096 blocks */
 
 /* update rules for SL_OPT_UPDATE */
 #define SL_UPDATE_METROPOLIS 0 /* Eq. 2 */
@@ -174,6 +177,25 @@ int sl_set_state(sl_lattice* lat, int64_t sweeps_done);
 /* sl_set_option — set one SL_OPT_* value; SL_EINVAL for unknown options or
  * values out of range. */
 int sl_set_option(sl_lattice* lat, int option, int64_t value);
+
+/*
+ * sl_autotune — pick the launch shape of the row-streaming sweep kernels for
+ * this lattice: rows per thread R (SL_OPT_ROWS, every R in {1, 2, 4, 8, 16,
+ * 32} dividing L) and the grid cap (SL_OPT_BLOCKS_PER_SM in {0, 2, 4, 8,
+ * 16}), by timing trial_sweeps sweeps at inverse temperature beta of each
+ * shape (CUDA events on the lattice's stream, after one warm-up sweep).  The
+ * spins and the sweep counter are restored afterwards and the shape never
+ * changes a decision, so the run continues as if the call had not happened.
+ * cache_path (or NULL): a file of JSON lines keyed by the device name, its
+ * SM count and (d, L, n, storage, couplings, update rule, fast math); a
+ * matching line is used without timing, and a new choice is appended.  The
+ * chosen values are returned in *rows and *blocks_per_sm (either may be
+ * NULL).  Lattices whose sweeps do not use the streaming kernels (slabs,
+ * multi-hit, Swendsen-Wang, short rows, zero couplings) keep their options.
+ * Synchronises.
+ */
+int sl_autotune(sl_lattice* lat, double beta, int trial_sweeps, const char* cache_path,
+                int* rows, int* blocks_per_sm);
 
 /*
  * sl_workspace_bytes — device bytes of workspace an update rule needs on this

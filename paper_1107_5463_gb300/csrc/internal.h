@@ -70,6 +70,7 @@ struct sl_lattice {
     bool bonds_have_zero;
     // options
     int renorm_every, fast_math, kernel, rows, use_graph;
+    int blocks_per_sm;       // cap of the streaming kernels' grids per SM (0 = none)
     int update;              // SL_UPDATE_METROPOLIS, _HEATBATH or _SW
     int multihit, tile;      // k-fold multi-hit sweeps in tiles of side `tile` (0 = off)
     // cached graphs of kGraphSweeps sweeps and of one sweep
@@ -95,6 +96,15 @@ int create_lattice(int d, int L, int n, int j_layout, int storage, double J, con
                    size_t dev_buf_bytes, void* stream, sl_lattice** out);
 size_t slab_required_bytes(int d, int L, int storage, int Lz);
 int ising_table(const sl_lattice* h, double beta, IsingTable* tab);
+// plain (uncaptured) sweeps, their parameters, and control-block setters (lattice.cu)
+int sweep_plain(const sl_lattice* h, const SweepParams& p, int64_t count, cudaStream_t s);
+int sweep_params(const sl_lattice* h, double beta, uint64_t seed, SweepParams* p);
+cudaError_t set_sweep_index(const sl_lattice* h, int64_t t, cudaStream_t s);
+cudaError_t clear_series(const sl_lattice* h, cudaStream_t s);
+void forget_graphs(sl_lattice* h);
+// whether a lattice's sweeps run the row-streaming kernels (ising_i8.cu, on_f32.cu)
+bool i8_streams(const sl_lattice* h);
+bool on_streams(const sl_lattice* h);
 
 // ---- Ising int8 (ising_i8.cu) ----
 cudaError_t ising_i8_init(const sl_lattice* h, cudaStream_t s);

@@ -67,17 +67,20 @@ __device__ __forceinline__ void fadd(uint32_t a, uint32_t b, uint32_t c, uint32_
 
 // MEAS: the measuring (colour-1) pass, which stores its block partials for
 // bits_finish_kernel; the other pass is compiled without the counters.
-template <int D, int JNEG, bool MEAS>
+// SLAB: a slab of a split lattice (halo planes, global offsets).
+template <int D, int JNEG, bool MEAS, bool SLAB = false>
 __global__ void __launch_bounds__(128) bits_stream(const BitArgs a)
 {
     __shared__ long long red[32];
     const uint32_t t = (uint32_t)a.ctrl->t;
-    const int L = a.L, R = a.R, Lz = a.Lz;
+    const int L = a.L, R = a.R, Lz = SLAB ? a.Lz : a.L;
     const int WW = a.W >> 5;  // words per row
     const long long nseg = Lz / R;
+    const int spar = SLAB ? a.par : 0;
+    const long long gofs = SLAB ? a.gofs : 0;
     // neighbouring plane along the slowest axis: periodic, or a halo plane
-    auto zprev = [&](int m) { return m == 0 ? (a.wrap ? Lz - 1 : -1) : m - 1; };
-    auto znext = [&](int m) { return m == Lz - 1 ? (a.wrap ? 0 : Lz) : m + 1; };
+    auto zprev = [&](int m) { return m == 0 ? (SLAB ? -1 : Lz - 1) : m - 1; };
+    auto znext = [&](int m) { return m == Lz - 1 ? (SLAB ? Lz : 0) : m + 1; };
     const long long nitems = (long long)WW * (D == 3 ? L : 1) * nseg;
     const uint32_t ctr_w = (kSweep << 1) | (uint32_t)a.c;
     const uint32_t inv = JNEG ? 0xFFFFFFFFu : 0u;
@@ -101,7 +104,7 @@ __global__ void __launch_bounds__(128) bits_stream(const BitArgs a)
         // software pipeline: the next row of the other colour, the own word,
         // the x-neighbour word and (3D) the y -/+ 1 words are loaded one row ahead
         auto rowof = [&](int m) -> long long { return D == 3 ? row(y3, m) : row(m, 0); };
-        auto par = [&](int m) -> int { return ((D == 3 ? y3 + m : m) + a.c + a.par) & 1; };
+        auto par = [&](int m) -> int { return ((D == 3 ? y3 + m : m) + a.c + spar) & 1; };
         uint32_t next_nx = __ldg(a.oth + mrow(znext(m0)) * WW + w);
         uint32_t A_nx = a.own[rowof(m0) * WW + w];
         uint32_t hw_nx = __ldg(a.oth + rowof(m0) * WW + (par(m0) ? wr : wl));
@@ -114,7 +117,7 @@ __global__ void __launch_bounds__(128) bits_stream(const BitArgs a)
             const int m = m0 + r;
             const int yy = D == 3 ? y3 : m;
             const int zz = D == 3 ? m : 0;
-            const int p = (yy + zz + a.c + a.par) & 1;
+            const int p = (yy + zz + a.c + spar) & 1;
             const long long rr = row(yy, zz);
             const uint32_t next = next_nx, A = A_nx, hw = hw_nx, ym = ym_nx, yp = yp_nx;
             if (r + 1 < R) {
@@ -151,7 +154,7 @@ __global__ void __launch_bounds__(128) bits_stream(const BitArgs a)
             if (a.update) {
                 const uint32_t ge1 = b0 | b1 | b2, ge2 = b1 | b2, ge3 = b2 | (b1 & b0);
                 uint32_t g0 = 0, g1 = 0, g2 = 0;
-                const uint32_t grp = (uint32_t)((rr * a.W + a.gofs + 32 * w) >> 2);
+                const uint32_t grp = (uint32_t)((rr * a.W + gofs + 32 * w) >> 2);
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
                     const uint4 rnd = philox4x32_10(make_uint4(grp + q, t, a.replica, ctr_w), a.rk);
@@ -314,12 +317,18 @@ BitArgs make_args(const sl_lattice* h, int c)
 cudaError_t launch(const sl_lattice* h, const BitArgs& a, cudaStream_t s)
 {
     const long long items = (long long)(h->W / 32) * (h->d == 3 ? h->L : 1) * (h->Lz / a.R);
-    const int grid = grid_for(items, 128);
+    int grid = grid_for(items, 128);
+    if (h->blocks_per_sm > 0 && grid > h->sms * h->blocks_per_sm) grid = h->sms * h->blocks_per_sm;
     const bool jneg = a.tab.sigma_neg != 0;
-#define SPINMC_BITS(D, N)                                                     \
-    do {                                                                      \
-        if (a.measure) bits_stream<D, N, true><<<grid, 128, 0, s>>>(a);        \
-        else bits_stream<D, N, false><<<grid, 128, 0, s>>>(a);                 \
+#define SPINMC_BITS(D, N)                                                          \
+    do {                                                                           \
+        if (h->slab) {                                                             \
+            if (a.measure) bits_stream<D, N, true, true><<<grid, 128, 0, s>>>(a);  \
+            else bits_stream<D, N, false, true><<<grid, 128, 0, s>>>(a);           \
+        } else {                                                                   \
+            if (a.measure) bits_stream<D, N, true><<<grid, 128, 0, s>>>(a);        \
+            else bits_stream<D, N, false><<<grid, 128, 0, s>>>(a);                 \
+        }                                                                          \
     } while (0)
     if (h->d == 2) {
         if (jneg) SPINMC_BITS(2, 1);

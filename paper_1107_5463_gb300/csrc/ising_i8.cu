@@ -213,7 +213,9 @@ __device__ __forceinline__ uint32_t q_bias(const uint4& r, const IsingTable& tab
 
 // MEAS: the measuring (colour-1) pass; the other pass is compiled without the
 // counters, which keeps its register count, and so its occupancy, lower.
-template <int D, int BONDS, int JNEG, int HB, bool MEAS>
+// SLAB: a slab of a split lattice (halo planes, global offsets); a whole
+// lattice compiles without them.
+template <int D, int BONDS, int JNEG, int HB, bool MEAS, bool SLAB = false>
 __global__ void __launch_bounds__(128) i8_stream(const I8Args a)
 {
     __shared__ long long red[32];
@@ -223,12 +225,14 @@ __global__ void __launch_bounds__(128) i8_stream(const I8Args a)
         __syncthreads();
     }
     const uint32_t t = (uint32_t)a.ctrl->t;
-    const int W = a.W, L = a.L, R = a.R, Lz = a.Lz;
+    const int W = a.W, L = a.L, R = a.R, Lz = SLAB ? a.Lz : a.L;
     const int W16 = W >> 4;
     const long long nseg = Lz / R;
+    const int par = SLAB ? a.par : 0;
+    const long long gofs = SLAB ? a.gofs : 0;
     // neighbouring plane along the slowest axis: periodic, or a halo plane
-    auto zprev = [&](int m) { return m == 0 ? (a.wrap ? Lz - 1 : -1) : m - 1; };
-    auto znext = [&](int m) { return m == Lz - 1 ? (a.wrap ? 0 : Lz) : m + 1; };
+    auto zprev = [&](int m) { return m == 0 ? (SLAB ? -1 : Lz - 1) : m - 1; };
+    auto znext = [&](int m) { return m == Lz - 1 ? (SLAB ? Lz : 0) : m + 1; };
     const long long nitems = (long long)W16 * (D == 3 ? L : 1) * nseg;
     const uint32_t ctr_w = (kSweep << 1) | (uint32_t)a.c;
     const uint32_t two_d = 0x01010101u * (uint32_t)(2 * D);
@@ -279,7 +283,7 @@ __global__ void __launch_bounds__(128) i8_stream(const I8Args a)
         uint4 next = ld_rows(a.oth + moff(znext(m0)) + k0);
         uint4 A_nx = *reinterpret_cast<const uint4*>(a.own + off(yy0, zz0) + k0);
         uint32_t edge_nx =
-            (uint8_t)a.oth[off(yy0, zz0) + edge_idx((yy0 + zz0 + a.c + a.par) & 1)];
+            (uint8_t)a.oth[off(yy0, zz0) + edge_idx((yy0 + zz0 + a.c + par) & 1)];
         // 3D: rows y -/+ 1 of the current plane, also one iteration ahead
         const int y_m = y3 == 0 ? L - 1 : y3 - 1, y_p = y3 == L - 1 ? 0 : y3 + 1;
         uint4 ym_nx = make_uint4(0, 0, 0, 0), yp_nx = ym_nx;
@@ -291,7 +295,7 @@ __global__ void __launch_bounds__(128) i8_stream(const I8Args a)
             const int m = m0 + r;
             int yy, zz;
             row_of(m, yy, zz);
-            const int p = (yy + zz + a.c + a.par) & 1;
+            const int p = (yy + zz + a.c + par) & 1;
             const long long ro = off(yy, zz);
             const int eidx = edge_idx(p);
             const uint4 A = A_nx;
@@ -305,7 +309,7 @@ __global__ void __launch_bounds__(128) i8_stream(const I8Args a)
                 row_of(m1, y1, z1);
                 next = ld_rows(a.oth + moff(m2) + k0);
                 A_nx = *reinterpret_cast<const uint4*>(a.own + off(y1, z1) + k0);
-                edge_nx = (uint8_t)a.oth[off(y1, z1) + edge_idx((y1 + z1 + a.c + a.par) & 1)];
+                edge_nx = (uint8_t)a.oth[off(y1, z1) + edge_idx((y1 + z1 + a.c + par) & 1)];
                 if (D == 3) {
                     ym_nx = ld_rows(a.oth + off(y_m, z1) + k0);
                     yp_nx = ld_rows(a.oth + off(y_p, z1) + k0);
@@ -332,7 +336,7 @@ __global__ void __launch_bounds__(128) i8_stream(const I8Args a)
                     jnext = ld_rows(a.Joth[2] + ro + k0);
                 }
             }
-            const uint32_t g0 = (uint32_t)((ro + a.gofs + k0) >> 2);
+            const uint32_t g0 = (uint32_t)((ro + gofs + k0) >> 2);
             uint4 Anew;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -594,14 +598,22 @@ cudaError_t launch_pass(const sl_lattice* h, I8Args a, cudaStream_t s, bool stre
     if (stream) {
         a.R = pick_rows(h);
         const long long items = (long long)(h->W / 16) * (h->d == 3 ? h->L : 1) * (h->Lz / a.R);
-        const int grid = grid_for(items, 128);
+        int grid = grid_for(items, 128);
+        if (h->blocks_per_sm > 0 && grid > h->sms * h->blocks_per_sm)
+            grid = h->sms * h->blocks_per_sm;
         const bool bonds = a.Jown[0] != nullptr;
         const bool jneg = a.tab.sigma_neg != 0;
         a.defer = a.measure;
-#define SPINMC_LAUNCH(D, B, N, HB)                                          \
-    do {                                                                    \
-        if (a.measure) i8_stream<D, B, N, HB, true><<<grid, 128, 0, s>>>(a);  \
-        else i8_stream<D, B, N, HB, false><<<grid, 128, 0, s>>>(a);           \
+        // slabs have uniform couplings: their instantiations have BONDS = 0
+#define SPINMC_LAUNCH(D, B, N, HB)                                                        \
+    do {                                                                                  \
+        if (h->slab && !(B)) {                                                            \
+            if (a.measure) i8_stream<D, 0, N, HB, true, true><<<grid, 128, 0, s>>>(a);    \
+            else i8_stream<D, 0, N, HB, false, true><<<grid, 128, 0, s>>>(a);             \
+        } else {                                                                          \
+            if (a.measure) i8_stream<D, B, N, HB, true><<<grid, 128, 0, s>>>(a);          \
+            else i8_stream<D, B, N, HB, false><<<grid, 128, 0, s>>>(a);                   \
+        }                                                                                 \
     } while (0)
         if (a.tab.heatbath && a.update) {
             if (h->d == 2) {
@@ -688,6 +700,12 @@ cudaError_t ising_i8_sweeps(const sl_lattice* h, const SweepParams& p, int64_t c
         }
     }
     return cudaSuccess;
+}
+
+bool i8_streams(const sl_lattice* h)
+{
+    return h->multihit == 0 && h->update != SL_UPDATE_SW &&
+           (h->kernel == 2 || (h->kernel == 0 && stream_ok(h)));
 }
 
 cudaError_t ising_i8_pass(const sl_lattice* h, const SweepParams& p, int c, cudaStream_t s)

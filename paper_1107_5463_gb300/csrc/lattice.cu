@@ -237,7 +237,8 @@ int ensure_graph(sl_lattice* h, const SweepParams& p)
     key[2] = ((uint64_t)h->kernel << 48) ^ ((uint64_t)h->rows << 32) ^
              ((uint64_t)h->fast_math << 24) ^ ((uint64_t)h->update << 40) ^
              (uint64_t)h->renorm_every;
-    key[3] = ((uint64_t)h->multihit << 16) ^ (uint64_t)h->tile;
+    key[3] = ((uint64_t)h->multihit << 16) ^ (uint64_t)h->tile ^
+             ((uint64_t)h->blocks_per_sm << 40);
     if (h->graph && h->graph1 && std::memcmp(key, h->graph_key, sizeof key) == 0) return SL_OK;
     drop_graphs(h);
     int st = capture_sweeps(h, p, kGraphSweeps, &h->graph);
@@ -367,6 +368,7 @@ int create_lattice(int d, int L, int n, int j_layout, int storage, double J, con
     h->fast_math = 0;
     h->kernel = 0;
     h->rows = 0;
+    h->blocks_per_sm = 0;
     h->use_graph = 1;
     h->update = 0;
     h->multihit = 0;
@@ -419,6 +421,35 @@ int create_lattice(int d, int L, int n, int j_layout, int storage, double J, con
     *out = h;
     return SL_OK;
 }
+
+int sweep_plain(const sl_lattice* h, const SweepParams& p, int64_t count, cudaStream_t s)
+{
+    return model_sweeps(h, p, count, s);
+}
+
+int sweep_params(const sl_lattice* h, double beta, uint64_t seed, SweepParams* p)
+{
+    std::memset(p, 0, sizeof *p);
+    p->beta = beta;
+    p->seed = seed;
+    p->rk = make_round_keys(seed);
+    p->beta_f = (float)beta;
+    return h->n == 1 ? ising_table(h, beta, &p->tab) : SL_OK;
+}
+
+cudaError_t set_sweep_index(const sl_lattice* h, int64_t t, cudaStream_t s)
+{
+    set_t_kernel<<<1, 1, 0, s>>>(h->ctrl, (unsigned long long)t);
+    return cudaGetLastError();
+}
+
+cudaError_t clear_series(const sl_lattice* h, cudaStream_t s)
+{
+    set_series_kernel<<<1, 1, 0, s>>>(h->ctrl, (long long)h->sweeps_done, nullptr, nullptr);
+    return cudaGetLastError();
+}
+
+void forget_graphs(sl_lattice* h) { drop_graphs(h); }
 
 }  // namespace spinmc
 
@@ -577,9 +608,13 @@ int sl_set_option(sl_lattice* h, int option, int64_t value)
         h->kernel = (int)value;
         return SL_OK;
     case SL_OPT_ROWS:
-        if (value < 0 || (value > 0 && (h->L % value != 0)))
-            return fail(SL_EINVAL, "rows must be 0 (automatic) or divide L");
+        if (value < 0 || (value > 0 && (h->Lz % value != 0)))
+            return fail(SL_EINVAL, "rows must be 0 (automatic) or divide the planes held");
         h->rows = (int)value;
+        return SL_OK;
+    case SL_OPT_BLOCKS_PER_SM:
+        if (value < 0 || value > 64) return fail(SL_EINVAL, "blocks_per_sm must be in [0, 64]");
+        h->blocks_per_sm = (int)value;
         return SL_OK;
     case SL_OPT_GRAPH:
         if (value != 0 && value != 1) return fail(SL_EINVAL, "graph must be 0 or 1");

@@ -1077,6 +1077,12 @@ bool on_stream_ok(const sl_lattice* h)
     return h->d == 2 && h->W % 64 == 0;
 }
 
+}  // namespace
+
+bool on_streams(const sl_lattice* h) { return on_stream_ok(h); }
+
+namespace {
+
 int on_rows(const sl_lattice* h, long long cols)
 {
     if (h->rows > 0) return h->rows;
@@ -1098,7 +1104,9 @@ cudaError_t launch_on(const sl_lattice* h, OnArgs a, cudaStream_t s)
         const long long cols = pairs ? h->W / 2 : h->W;
         a.R = on_rows(h, cols);
         const long long items = cols * (h->d == 3 ? h->L : 1) * (h->L / a.R);
-        const int grid = grid_for(items, 256);
+        int grid = grid_for(items, 256);
+        if (h->blocks_per_sm > 0 && grid > h->sms * h->blocks_per_sm)
+            grid = h->sms * h->blocks_per_sm;
 #define SPINMC_ON(K, ...)                                                      \
     do {                                                                       \
         if (a.measure) K<__VA_ARGS__, true><<<grid, 256, 0, s>>>(a);          \

@@ -21,7 +21,7 @@ SL_OK, SL_EINVAL, SL_ENOMEM, SL_ECUDA, SL_ETIMEOUT, SL_EDEVICE = 0, -1, -2, -3, 
 SL_J_UNIFORM, SL_J_BONDS = 0, 1
 SL_STORE_I8, SL_STORE_BITS, SL_STORE_F32_ANGLE, SL_STORE_F32_VEC = 0, 1, 2, 3
 SL_OPT_RENORM_EVERY, SL_OPT_FAST_MATH, SL_OPT_KERNEL, SL_OPT_ROWS, SL_OPT_GRAPH = 1, 2, 3, 4, 5
-SL_OPT_UPDATE, SL_OPT_MULTIHIT, SL_OPT_TILE = 6, 7, 8
+SL_OPT_UPDATE, SL_OPT_MULTIHIT, SL_OPT_TILE, SL_OPT_BLOCKS_PER_SM = 6, 7, 8, 9
 SL_UPDATE_METROPOLIS, SL_UPDATE_HEATBATH, SL_UPDATE_SW = 0, 1, 2
 SL_WOPT_SPINS_SMEM = 1
 SL_BOPT_AUTOTUNE, SL_BOPT_PACK = 1, 2
@@ -56,6 +56,8 @@ _sig("sl_set_spins", _int, _vp, _vp)
 _sig("sl_get_state", _int, _vp, ctypes.POINTER(_u64), ctypes.POINTER(_i64))
 _sig("sl_set_state", _int, _vp, _i64)
 _sig("sl_set_option", _int, _vp, _int, _i64)
+_sig("sl_autotune", _int, _vp, _dbl, _int, ctypes.c_char_p, ctypes.POINTER(_int),
+     ctypes.POINTER(_int))
 _sig("sl_destroy", None, _vp)
 _sig("sl_workspace_bytes", _int, _vp, _int, ctypes.POINTER(_sz))
 _sig("sl_attach_workspace", _int, _vp, _vp, _sz)
@@ -185,6 +187,15 @@ def sl_set_state(h, sweeps_done):
 
 def sl_set_option(h, option, value):
     _check(_lib.sl_set_option(h, option, value), "sl_set_option")
+
+
+def sl_autotune(h, beta, trial_sweeps, cache_path=None):
+    """Tune the streaming kernels' launch shape; returns (rows, blocks_per_sm)."""
+    r, c = _int(), _int()
+    path = None if cache_path is None else os.fsencode(cache_path)
+    _check(_lib.sl_autotune(h, beta, trial_sweeps, path, ctypes.byref(r), ctypes.byref(c)),
+           "sl_autotune")
+    return r.value, c.value
 
 
 def sl_destroy(h):
@@ -520,6 +531,10 @@ class Lattice:
 
     def set_option(self, option, value):
         sl_set_option(self.h, option, value)
+
+    def autotune(self, beta, trial_sweeps=4, cache_path=None):
+        """Pick rows per thread and the grid cap by timing; (rows, blocks_per_sm)."""
+        return sl_autotune(self.h, beta, trial_sweeps, cache_path)
 
     def set_update(self, rule):
         """Select an SL_UPDATE_* rule, attaching a torch-allocated workspace
