@@ -75,7 +75,9 @@ extern "C" {
 /* options for sl_set_option */
 #define SL_OPT_RENORM_EVERY 1  /* Heisenberg: renormalise every k sweeps (default 16, 0 = never) */
 #define SL_OPT_FAST_MATH 2     /* continuous spins: 1 = hardware sin/cos/exp intrinsics */
-#define SL_OPT_KERNEL 3        /* 0 = automatic, 1 = generic per-site kernel, 2 = row-streaming kernel */
+#define SL_OPT_KERNEL 3        /* 0 = automatic, 1 = generic per-site kernel, 2 = row-streaming
+                                  kernel, 3 = row-streaming kernel on single columns
+                                  (Heisenberg; 2 takes column pairs where L % 128 == 0) */
 #define SL_OPT_ROWS 4          /* rows each thread marches through in the streaming kernel */
 #define SL_OPT_GRAPH 5         /* 1 = replay sweeps through CUDA graphs (default), 0 = plain launches */
 #define SL_OPT_UPDATE 6        /* one of SL_UPDATE_* below (default SL_UPDATE_METROPOLIS) */
@@ -181,9 +183,11 @@ int sl_set_option(sl_lattice* lat, int option, int64_t value);
 /*
  * sl_autotune — pick the launch shape of the row-streaming sweep kernels for
  * this lattice: rows per thread R (SL_OPT_ROWS, every R in {1, 2, 4, 8, 16,
- * 32} dividing L) and the grid cap (SL_OPT_BLOCKS_PER_SM in {0, 2, 4, 8,
- * 16}), by timing trial_sweeps sweeps at inverse temperature beta of each
- * shape (CUDA events on the lattice's stream, after one warm-up sweep).  The
+ * 32} dividing L), the grid cap (SL_OPT_BLOCKS_PER_SM in {0, 2, 4, 8, 16})
+ * and, for Heisenberg spins with L % 128 == 0, column pairs or single
+ * columns (SL_OPT_KERNEL 2 or 3), by timing trial_sweeps sweeps at inverse
+ * temperature beta of each shape (CUDA events on the lattice's stream, after
+ * one warm-up sweep).  The
  * spins and the sweep counter are restored afterwards and the shape never
  * changes a decision, so the run continues as if the call had not happened.
  * cache_path (or NULL): a file of JSON lines keyed by the device name, its

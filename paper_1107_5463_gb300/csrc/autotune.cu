@@ -5,8 +5,10 @@
 // change only the launch shape, never a decision (every random number is
 // keyed by its site), so any choice gives the same chain.  sl_autotune times
 // trial sweeps of every shape in a small set (R dividing the planes, grids
-// capped at 0, 2, 4, 8 or 16 blocks per SM) on the lattice itself, restores
-// its spins and sweep counter, and keeps the fastest.  Choices can be cached
+// capped at 0, 2, 4, 8 or 16 blocks per SM, and for Heisenberg spins on
+// rows of a multiple of 64 colour columns the column-pair or the
+// single-column kernel) on the lattice itself, restores its spins and sweep
+// counter, and keeps the fastest.  Choices can be cached
 // in a file of JSON lines, one per (device, d, L, n, storage, couplings,
 // update rule, fast math), read before timing and appended after.
 #include <cstdio>
@@ -74,7 +76,7 @@ bool int_field(const char* line, const char* name, int* v)
     return true;
 }
 
-bool cache_lookup(const char* path, const TuneKey& k, int* rows, int* caps)
+bool cache_lookup(const char* path, const TuneKey& k, int* rows, int* caps, int* kernel)
 {
     FILE* f = std::fopen(path, "r");
     if (!f) return false;
@@ -87,12 +89,13 @@ bool cache_lookup(const char* path, const TuneKey& k, int* rows, int* caps)
                                "rows"};
         bool ok = field(line, "device", &dev) && dev == k.device;
         for (int q = 0; q < 9 && ok; ++q) ok = int_field(line, names[q], &v[q]);
-        int cap = 0;
-        ok = ok && int_field(line, "blocks_per_sm", &cap);
+        int cap = 0, kern = 0;
+        ok = ok && int_field(line, "blocks_per_sm", &cap) && int_field(line, "kernel", &kern);
         if (ok && v[0] == k.sms && v[1] == k.d && v[2] == k.L && v[3] == k.n &&
             v[4] == k.storage && v[5] == k.j_layout && v[6] == k.update && v[7] == k.fast) {
             *rows = v[8];
             *caps = cap;
+            *kernel = kern;
             found = true;  // the last matching line wins
         }
     }
@@ -100,16 +103,17 @@ bool cache_lookup(const char* path, const TuneKey& k, int* rows, int* caps)
     return found;
 }
 
-void cache_append(const char* path, const TuneKey& k, int rows, int caps, double ms)
+void cache_append(const char* path, const TuneKey& k, int rows, int caps, int kernel, double ms)
 {
     FILE* f = std::fopen(path, "a");
     if (!f) return;
     std::fprintf(f,
                  "{\"device\": \"%s\", \"sms\": %d, \"d\": %d, \"L\": %d, \"n\": %d, "
                  "\"storage\": %d, \"j_layout\": %d, \"update\": %d, \"fast\": %d, "
-                 "\"rows\": %d, \"blocks_per_sm\": %d, \"ms_per_sweep\": %.6f}\n",
+                 "\"rows\": %d, \"blocks_per_sm\": %d, \"kernel\": %d, "
+                 "\"ms_per_sweep\": %.6f}\n",
                  k.device.c_str(), k.sms, k.d, k.L, k.n, k.storage, k.j_layout, k.update, k.fast,
-                 rows, caps, ms);
+                 rows, caps, kernel, ms);
     std::fclose(f);
 }
 
@@ -139,10 +143,12 @@ extern "C" int sl_autotune(sl_lattice* h, double beta, int trial_sweeps, const c
     };
     if (!tunable(h)) return report();
     const TuneKey key = key_of(h);
-    int r = 0, c = 0;
-    if (cache_path && cache_lookup(cache_path, key, &r, &c) && r > 0 && h->Lz % r == 0) {
+    int r = 0, c = 0, kc = 0;
+    if (cache_path && cache_lookup(cache_path, key, &r, &c, &kc) && r > 0 && h->Lz % r == 0 &&
+        (kc == 0 || kc == 2 || (kc == 3 && h->n == 3))) {
         h->rows = r;
         h->blocks_per_sm = c;
+        if (kc) h->kernel = kc;
         forget_graphs(h);
         return report();
     }
@@ -167,13 +173,17 @@ extern "C" int sl_autotune(sl_lattice* h, double beta, int trial_sweeps, const c
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
-    const int saved_rows = h->rows, saved_caps = h->blocks_per_sm;
-    int best_r = saved_rows, best_c = saved_caps;
+    const int saved_rows = h->rows, saved_caps = h->blocks_per_sm, saved_kernel = h->kernel;
+    int best_r = saved_rows, best_c = saved_caps, best_k = saved_kernel;
     float best = -1.f;
+    // Heisenberg rows of a multiple of 64 colour columns: pairs (2) or single columns (3)
+    const bool two_kernels = h->n == 3 && h->W % 64 == 0 && h->kernel != 3;
+    for (int kern = 0; kern < (two_kernels ? 2 : 1); ++kern)
     for (int R : kRows) {
         if (h->Lz % R) continue;
         for (int cap : kCaps) {
             if (e != cudaSuccess || st != SL_OK) break;
+            if (two_kernels) h->kernel = kern ? 3 : saved_kernel;
             h->rows = R;
             h->blocks_per_sm = cap;
             st = sweep_plain(h, p, 1, s);  // warm-up
@@ -187,12 +197,14 @@ extern "C" int sl_autotune(sl_lattice* h, double beta, int trial_sweeps, const c
                 best = ms;
                 best_r = R;
                 best_c = cap;
+                best_k = h->kernel;
             }
         }
     }
     // put the state back whatever happened
     h->rows = best_r;
     h->blocks_per_sm = best_c;
+    h->kernel = best_k;
     cudaError_t e2 = cudaMemcpyAsync(h->spins[0], keep, colour_bytes, cudaMemcpyDeviceToDevice, s);
     if (e2 == cudaSuccess)
         e2 = cudaMemcpyAsync(h->spins[1], keep + colour_bytes, colour_bytes,
@@ -206,6 +218,6 @@ extern "C" int sl_autotune(sl_lattice* h, double beta, int trial_sweeps, const c
     if (e != cudaSuccess) return cuda_fail(e, "sl_autotune");
     if (e2 != cudaSuccess) return cuda_fail(e2, "sl_autotune: restore");
     if (cache_path && best >= 0.f)
-        cache_append(cache_path, key, best_r, best_c, best / trial_sweeps);
+        cache_append(cache_path, key, best_r, best_c, best_k, best / trial_sweeps);
     return report();
 }

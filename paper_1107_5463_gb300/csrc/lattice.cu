@@ -595,7 +595,10 @@ int sl_set_option(sl_lattice* h, int option, int64_t value)
         h->fast_math = (int)value;
         return SL_OK;
     case SL_OPT_KERNEL:
-        if (value < 0 || value > 2) return fail(SL_EINVAL, "kernel must be 0, 1 or 2");
+        if (value < 0 || value > 3) return fail(SL_EINVAL, "kernel must be 0, 1, 2 or 3");
+        if (value == 3 && (h->n != 3 || h->j_layout != SL_J_UNIFORM || h->W % 32 != 0))
+            return fail(SL_EINVAL, "kernel 3 (single-column streaming) is for Heisenberg spins "
+                                   "with uniform J and L %% 64 == 0");
         if (value == 1 && h->storage == SL_STORE_BITS)
             return fail(SL_EINVAL, "bit storage has only the streaming kernel");
         if (value == 2 && h->n == 1 && (h->W % 16 != 0 || h->bonds_have_zero))

@@ -3,9 +3,10 @@
 Rows per thread and the grid cap change only which thread updates which site
 and when; every random number is keyed by its site, so each shape the tuner
 may pick must give the same chain: bit-identical Ising spins and series,
-identical FP32 continuous spins (their FP64 energy totals differ by about
-1e-10 relative: each thread adds its sites' FP32 terms before the FP64 block
-sums, and the shape decides which sites a thread adds).  Tuning restores the spins
+identical FP32 continuous spins (their FP64 totals differ by about 1e-10
+relative in E and 1e-10 absolute in |m|: each thread adds its sites' FP32
+terms before the FP64 block sums, and the shape decides which sites a thread
+adds).  Tuning restores the spins
 and the sweep counter, so a tuned run continues exactly like an untuned one;
 its choice is cached by device and configuration."""
 import json
@@ -61,8 +62,8 @@ def test_every_shape_gives_the_same_chain(sm, d, L, n, storage, beta):
                 np.testing.assert_array_equal(got[1], ref[1])
                 np.testing.assert_array_equal(got[2], ref[2])
             else:
-                np.testing.assert_allclose(got[1], ref[1], rtol=1e-8)
-                np.testing.assert_allclose(got[2], ref[2], rtol=1e-8)
+                np.testing.assert_allclose(got[1], ref[1], rtol=1e-8)   # E
+                np.testing.assert_allclose(got[2], ref[2], rtol=0, atol=1e-9)   # |m|
 
 
 @pytest.mark.parametrize("d,L,n,storage,beta", CASES[:3] + CASES[4:6])
@@ -78,11 +79,13 @@ def test_tuning_leaves_the_run_unchanged(sm, d, L, n, storage, beta, tmp_path):
     assert L % R == 0 and cap in CAPS
     rb2 = run(b, beta, 3)
     b.close()
-    for x, y in zip(ra1 + ra2, rb1 + rb2):
-        if x.dtype == np.float64 and n > 1:
-            np.testing.assert_allclose(x, y, rtol=1e-8)
+    for q, (x, y) in enumerate(zip(ra1 + ra2, rb1 + rb2)):
+        if q % 3 == 0 or n == 1:
+            np.testing.assert_array_equal(x, y)                     # spins, Ising series
+        elif q % 3 == 1:
+            np.testing.assert_allclose(x, y, rtol=1e-8)             # E
         else:
-            np.testing.assert_array_equal(x, y)
+            np.testing.assert_allclose(x, y, rtol=0, atol=1e-9)     # |m|
     # the choice is cached: one line, reused by the next lattice of this shape
     lines = open(cache).read().splitlines()
     assert len(lines) == 1
