@@ -57,8 +57,8 @@ extern "C" {
 #define SL_EINVAL (-1)    /* invalid argument (message in sl_last_error) */
 #define SL_ENOMEM (-2)    /* buffer too small or allocation failed */
 #define SL_ECUDA (-3)     /* a CUDA runtime call failed */
-#define SL_ETIMEOUT (-4)  /* reserved for bounded device-side waits (no kernel of this
-                             library waits on another thread, block or device) */
+#define SL_ETIMEOUT (-4)  /* a kernel's bounded wait for its own asynchronous copies ran
+                             out (reported by the next synchronising call; sticky) */
 #define SL_EDEVICE (-5)   /* a kernel reported a failure it detected (a walker that did
                              not reach its window) */
 
@@ -77,7 +77,10 @@ extern "C" {
 #define SL_OPT_FAST_MATH 2     /* continuous spins: 1 = hardware sin/cos/exp intrinsics */
 #define SL_OPT_KERNEL 3        /* 0 = automatic, 1 = generic per-site kernel, 2 = row-streaming
                                   kernel, 3 = row-streaming kernel on single columns
-                                  (Heisenberg; 2 takes column pairs where L % 128 == 0) */
+                                  (Heisenberg; 2 takes column pairs where L % 128 == 0),
+                                  4 = staged tiles (3D Heisenberg, uniform J, L in {64, 128,
+                                  256, 512}, Metropolis, accurate functions: planes stream
+                                  into shared memory by bulk asynchronous copies) */
 #define SL_OPT_ROWS 4          /* rows each thread marches through in the streaming kernel */
 #define SL_OPT_GRAPH 5         /* 1 = replay sweeps through CUDA graphs (default), 0 = plain launches */
 #define SL_OPT_UPDATE 6        /* one of SL_UPDATE_* below (default SL_UPDATE_METROPOLIS) */
@@ -184,8 +187,8 @@ int sl_set_option(sl_lattice* lat, int option, int64_t value);
  * sl_autotune — pick the launch shape of the row-streaming sweep kernels for
  * this lattice: rows per thread R (SL_OPT_ROWS, every R in {1, 2, 4, 8, 16,
  * 32} dividing L), the grid cap (SL_OPT_BLOCKS_PER_SM in {0, 2, 4, 8, 16})
- * and, for Heisenberg spins with L % 128 == 0, column pairs or single
- * columns (SL_OPT_KERNEL 2 or 3), by timing trial_sweeps sweeps at inverse
+ * and, for Heisenberg spins, the kernel (SL_OPT_KERNEL 2, 3 or 4 where each
+ * applies), by timing trial_sweeps sweeps at inverse
  * temperature beta of each shape (CUDA events on the lattice's stream, after
  * one warm-up sweep).  The
  * spins and the sweep counter are restored afterwards and the shape never
@@ -558,6 +561,13 @@ int sl_last_error(char* msg, size_t cap);
  * the same stream).  SL_EINVAL for an unknown kind, iterations < 1, a short
  * buffer, or Philox counters beyond 32 bits; SL_ECUDA if the launch fails.
  */
+/* sl_wait_selftest — check the bounded wait of the staged kernels: a
+ * one-block kernel arms an mbarrier for 16 bytes that no copy ever delivers
+ * and polls it with the same limit the staged kernels use (a few seconds);
+ * *timed_out = 1 if the poll gave up and the kernel returned, as it must.  No
+ * copy is issued.  Synchronises the stream. */
+int sl_wait_selftest(void* stream, int* timed_out);
+
 #define SL_MB_PHILOX 0
 #define SL_MB_IMAD 1
 #define SL_MB_FFMA 2

@@ -5,10 +5,10 @@
 // change only the launch shape, never a decision (every random number is
 // keyed by its site), so any choice gives the same chain.  sl_autotune times
 // trial sweeps of every shape in a small set (R dividing the planes, grids
-// capped at 0, 2, 4, 8 or 16 blocks per SM, and for Heisenberg spins on
-// rows of a multiple of 64 colour columns the column-pair or the
-// single-column kernel) on the lattice itself, restores its spins and sweep
-// counter, and keeps the fastest.  Choices can be cached
+// capped at 0, 2, 4, 8 or 16 blocks per SM, and for Heisenberg spins the
+// column-pair, single-column or staged-tile kernel where each applies) on the
+// lattice itself, restores its spins and sweep counter, and keeps the
+// fastest.  Choices can be cached
 // in a file of JSON lines, one per (device, d, L, n, storage, couplings,
 // update rule, fast math), read before timing and appended after.
 #include <cstdio>
@@ -145,7 +145,7 @@ extern "C" int sl_autotune(sl_lattice* h, double beta, int trial_sweeps, const c
     const TuneKey key = key_of(h);
     int r = 0, c = 0, kc = 0;
     if (cache_path && cache_lookup(cache_path, key, &r, &c, &kc) && r > 0 && h->Lz % r == 0 &&
-        (kc == 0 || kc == 2 || (kc == 3 && h->n == 3))) {
+        (kc == 0 || kc == 2 || (kc == 3 && h->n == 3) || (kc == 4 && h->n == 3 && h->d == 3))) {
         h->rows = r;
         h->blocks_per_sm = c;
         if (kc) h->kernel = kc;
@@ -176,14 +176,21 @@ extern "C" int sl_autotune(sl_lattice* h, double beta, int trial_sweeps, const c
     const int saved_rows = h->rows, saved_caps = h->blocks_per_sm, saved_kernel = h->kernel;
     int best_r = saved_rows, best_c = saved_caps, best_k = saved_kernel;
     float best = -1.f;
-    // Heisenberg rows of a multiple of 64 colour columns: pairs (2) or single columns (3)
-    const bool two_kernels = h->n == 3 && h->W % 64 == 0 && h->kernel != 3;
-    for (int kern = 0; kern < (two_kernels ? 2 : 1); ++kern)
+    // Heisenberg: the kernel as set, single columns (3) where pairs are the
+    // default, and the staged 3D tiles (4) where they apply
+    int kernels[3] = {saved_kernel, -1, -1};
+    if (h->n == 3 && h->W % 64 == 0 && saved_kernel != 3) kernels[1] = 3;
+    h->kernel = 4;
+    if (on_tile_ok(h)) kernels[2] = 4;
+    h->kernel = saved_kernel;
+    for (int kern : kernels)
     for (int R : kRows) {
-        if (h->Lz % R) continue;
+        if (kern < 0 || h->Lz % R) continue;
+        if (kern == 4 && R != kRows[0]) continue;  // the staged tiles take no rows per thread
         for (int cap : kCaps) {
             if (e != cudaSuccess || st != SL_OK) break;
-            if (two_kernels) h->kernel = kern ? 3 : saved_kernel;
+            if (kern == 4 && cap > 2) continue;     // at most four resident blocks per SM
+            h->kernel = kern;
             h->rows = R;
             h->blocks_per_sm = cap;
             st = sweep_plain(h, p, 1, s);  // warm-up

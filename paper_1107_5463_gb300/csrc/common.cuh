@@ -51,6 +51,7 @@ struct Ctrl {
     double* series_E;          // per-sweep energy, or null
     double* series_absm;       // per-sweep |m|, or null
     unsigned int done;         // blocks finished in the measuring pass
+    unsigned int error;        // bit 0: a bounded device-side wait ran out (sticky)
     double obs[4];             // E, Mx, My, Mz after the last measured pass
 };
 

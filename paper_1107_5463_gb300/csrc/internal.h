@@ -105,6 +105,7 @@ void forget_graphs(sl_lattice* h);
 // whether a lattice's sweeps run the row-streaming kernels (ising_i8.cu, on_f32.cu)
 bool i8_streams(const sl_lattice* h);
 bool on_streams(const sl_lattice* h);
+bool on_tile_ok(const sl_lattice* h);  // the staged 3D Heisenberg kernel applies
 
 // ---- Ising int8 (ising_i8.cu) ----
 cudaError_t ising_i8_init(const sl_lattice* h, cudaStream_t s);

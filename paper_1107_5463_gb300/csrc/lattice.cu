@@ -254,8 +254,15 @@ int ensure_graph(sl_lattice* h, const SweepParams& p)
 
 int sync_and_check(sl_lattice* h)
 {
-    const cudaError_t e = cudaStreamSynchronize(h->stream);
-    return e == cudaSuccess ? SL_OK : cuda_fail(e, "cudaStreamSynchronize");
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    unsigned err = 0;
+    e = cudaMemcpy(&err, &h->ctrl->error, sizeof err, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "read error word");
+    if (err & 1u)
+        return fail(SL_ETIMEOUT, "a kernel's bounded wait for its staged copies ran out; the "
+                                 "configuration is not valid");
+    return SL_OK;
 }
 
 size_t nat_bytes(const sl_lattice* h)
@@ -595,7 +602,17 @@ int sl_set_option(sl_lattice* h, int option, int64_t value)
         h->fast_math = (int)value;
         return SL_OK;
     case SL_OPT_KERNEL:
-        if (value < 0 || value > 3) return fail(SL_EINVAL, "kernel must be 0, 1, 2 or 3");
+        if (value < 0 || value > 4) return fail(SL_EINVAL, "kernel must be 0, 1, 2, 3 or 4");
+        if (value == 4) {
+            const int kept = h->kernel;
+            h->kernel = 4;
+            const bool ok = on_tile_ok(h);
+            h->kernel = kept;
+            if (!ok)
+                return fail(SL_EINVAL, "kernel 4 (staged tiles) is for 3D Heisenberg spins with "
+                                       "uniform J, L in {64, 128, 256, 512}, Metropolis and "
+                                       "accurate functions");
+        }
         if (value == 3 && (h->n != 3 || h->j_layout != SL_J_UNIFORM || h->W % 32 != 0))
             return fail(SL_EINVAL, "kernel 3 (single-column streaming) is for Heisenberg spins "
                                    "with uniform J and L %% 64 == 0");

@@ -107,16 +107,17 @@ __device__ __forceinline__ void fill_turn_table(float2* tab)
     __syncthreads();
 }
 
+// (every rounding spelled out, so that each kernel gets the same values)
 __device__ __forceinline__ void sincos_from_table(const float2* tab, int k, float r, float* s,
                                                   float* c)
 {
-    const float x = r * (kTwoPiF / (float)kTurnTab);
-    const float x2 = x * x;
-    const float sb = x * fmaf(x2, -1.0f / 6.0f, 1.0f);
-    const float cm1 = -0.5f * x2;
+    const float x = __fmul_rn(r, kTwoPiF / (float)kTurnTab);
+    const float x2 = __fmul_rn(x, x);
+    const float sb = __fmul_rn(x, __fmaf_rn(x2, -1.0f / 6.0f, 1.0f));
+    const float cm1 = __fmul_rn(-0.5f, x2);
     const float2 e = tab[k];  // (cos, sin) of 2 pi k / kTurnTab
-    *s = e.y + fmaf(e.y, cm1, e.x * sb);
-    *c = e.x + fmaf(e.x, cm1, -e.y * sb);
+    *s = __fadd_rn(e.y, __fmaf_rn(e.y, cm1, __fmul_rn(e.x, sb)));
+    *c = __fadd_rn(e.x, __fmaf_rn(e.x, cm1, -__fmul_rn(e.y, sb)));
 }
 
 // t in turns, [0, 1)
@@ -169,11 +170,52 @@ __device__ __forceinline__ float3 sphere_point(uint32_t oz, uint32_t ophi)
 // The same point with sin and cos of the azimuth from the shared table.
 __device__ __forceinline__ float3 sphere_point_tab(const float2* tab, uint32_t oz, uint32_t ophi)
 {
-    const float z = 2.0f * u24(oz) - 1.0f;
-    const float r = sqrtf((1.0f - z) * (1.0f + z));
+    const float z = __fmaf_rn(2.0f, u24(oz), -1.0f);  // exact
+    const float r = sqrtf(__fmul_rn(1.0f - z, 1.0f + z));
     float sp, cp;
     sincos_turns_tab(tab, u24(ophi), &sp, &cp);
-    return make_float3(r * cp, r * sp, z);
+    return make_float3(__fmul_rn(r, cp), __fmul_rn(r, sp), z);
+}
+
+// One component of a Heisenberg site's field, every rounding spelled out so
+// that each kernel computes it identically whatever the compiler would fuse:
+// ((x- + x+) + a) + b along the marching axis, then + (c + d) across (3D),
+// times J.
+template <int D>
+__device__ __forceinline__ float heis_field(float xm, float xp, float a, float b, float c, float d,
+                                            float J)
+{
+    float h = __fadd_rn(__fadd_rn(__fadd_rn(xm, xp), a), b);
+    if (D == 3) h = __fadd_rn(h, __fadd_rn(c, d));
+    return __fmul_rn(h, J);
+}
+
+// The Metropolis step of one Heisenberg site with proposal v (Eq. 2, dE =
+// -(v - s) . h, accurate or intrinsic exp) and the optional renormalisation,
+// every rounding spelled out as in heis_field; true if s changed.
+template <bool FAST>
+__device__ __forceinline__ bool heis_metropolis(float& sx, float& sy, float& sz, const float3& v,
+                                                float hx, float hy, float hz, float u, float beta,
+                                                bool renorm)
+{
+    bool changed = false;
+    const float dE = -__fmaf_rn(__fsub_rn(v.z, sz), hz,
+                                __fmaf_rn(__fsub_rn(v.y, sy), hy,
+                                          __fmul_rn(__fsub_rn(v.x, sx), hx)));
+    if (dE <= 0.f || u < boltzmann<FAST>(__fmul_rn(-beta, dE))) {
+        sx = v.x;
+        sy = v.y;
+        sz = v.z;
+        changed = true;
+    }
+    if (renorm) {
+        const float inv = rsqrtf(__fmaf_rn(sz, sz, __fmaf_rn(sy, sy, __fmul_rn(sx, sx))));
+        sx = __fmul_rn(sx, inv);
+        sy = __fmul_rn(sy, inv);
+        sz = __fmul_rn(sz, inv);
+        changed = true;
+    }
+    return changed;
 }
 
 // Heat-bath draw of a Heisenberg spin in the local field h, kappa = beta |h|.
@@ -584,17 +626,9 @@ __global__ void __launch_bounds__(256, D == 2 && !HB ? 4 : 3) heis_stream(const 
                 xp = shfl3_down(cur);
                 if (lane == 31) xp = edge;
             }
-            float hx = xm.x + xp.x + prev.x + nxt.x;
-            float hy = xm.y + xp.y + prev.y + nxt.y;
-            float hz = xm.z + xp.z + prev.z + nxt.z;
-            if (D == 3) {
-                hx += vm.x + vp.x;
-                hy += vm.y + vp.y;
-                hz += vm.z + vp.z;
-            }
-            hx *= J;
-            hy *= J;
-            hz *= J;
+            const float hx = heis_field<D>(xm.x, xp.x, prev.x, nxt.x, vm.x, vp.x, J);
+            const float hy = heis_field<D>(xm.y, xp.y, prev.y, nxt.y, vm.y, vp.y, J);
+            const float hz = heis_field<D>(xm.z, xp.z, prev.z, nxt.z, vm.z, vp.z, J);
             if (a.update) {
                 const uint4 rnd = philox4x32_10(
                     make_uint4((uint32_t)j, t, a.replica, (kSweep << 1) | (uint32_t)a.c), a.rk);
@@ -602,23 +636,17 @@ __global__ void __launch_bounds__(256, D == 2 && !HB ? 4 : 3) heis_stream(const 
                 if (HB) {
                     s = heis_heatbath(hx, hy, hz, a.beta, rnd.x, rnd.y);
                     changed = true;
-                } else {
-                    const float u = u24(rnd.x);
-                    const float3 v = (TAB ? sphere_point_tab(tab, rnd.y, rnd.z) : sphere_point<FAST>(rnd.y, rnd.z));
-                    const float dE = -((v.x - s.x) * hx + (v.y - s.y) * hy + (v.z - s.z) * hz);
-                    if (dE <= 0.f || u < boltzmann<FAST>(-a.beta * dE)) {
-                        s.x = v.x;
-                        s.y = v.y;
-                        s.z = v.z;
-                        changed = true;
+                    if (renorm) {
+                        const float inv = rsqrtf(s.x * s.x + s.y * s.y + s.z * s.z);
+                        s.x *= inv;
+                        s.y *= inv;
+                        s.z *= inv;
                     }
-                }
-                if (renorm) {
-                    const float inv = rsqrtf(s.x * s.x + s.y * s.y + s.z * s.z);
-                    s.x *= inv;
-                    s.y *= inv;
-                    s.z *= inv;
-                    changed = true;
+                } else {
+                    const float3 v = TAB ? sphere_point_tab(tab, rnd.y, rnd.z)
+                                         : sphere_point<FAST>(rnd.y, rnd.z);
+                    changed = heis_metropolis<FAST>(s.x, s.y, s.z, v, hx, hy, hz, u24(rnd.x),
+                                                    a.beta, renorm);
                 }
                 if (changed) {
                     sx_[j] = s.x;
@@ -771,26 +799,12 @@ __global__ void __launch_bounds__(256, D == 2 ? 3 : 2) heis_pair(const OnArgs a)
                 }
             }
             V3 hA, hB;
-            hA.x = (p ? cur.x.y : ex) + cur.x.x + prev.x.x + nxt.x.x;
-            hA.y = (p ? cur.y.y : ey) + cur.y.x + prev.y.x + nxt.y.x;
-            hA.z = (p ? cur.z.y : ez) + cur.z.x + prev.z.x + nxt.z.x;
-            hB.x = (p ? ex : cur.x.x) + cur.x.y + prev.x.y + nxt.x.y;
-            hB.y = (p ? ey : cur.y.x) + cur.y.y + prev.y.y + nxt.y.y;
-            hB.z = (p ? ez : cur.z.x) + cur.z.y + prev.z.y + nxt.z.y;
-            if (D == 3) {
-                hA.x += vm.x.x + vp.x.x;
-                hA.y += vm.y.x + vp.y.x;
-                hA.z += vm.z.x + vp.z.x;
-                hB.x += vm.x.y + vp.x.y;
-                hB.y += vm.y.y + vp.y.y;
-                hB.z += vm.z.y + vp.z.y;
-            }
-            hA.x *= J;
-            hA.y *= J;
-            hA.z *= J;
-            hB.x *= J;
-            hB.y *= J;
-            hB.z *= J;
+            hA.x = heis_field<D>(p ? cur.x.y : ex, cur.x.x, prev.x.x, nxt.x.x, vm.x.x, vp.x.x, J);
+            hA.y = heis_field<D>(p ? cur.y.y : ey, cur.y.x, prev.y.x, nxt.y.x, vm.y.x, vp.y.x, J);
+            hA.z = heis_field<D>(p ? cur.z.y : ez, cur.z.x, prev.z.x, nxt.z.x, vm.z.x, vp.z.x, J);
+            hB.x = heis_field<D>(p ? ex : cur.x.x, cur.x.y, prev.x.y, nxt.x.y, vm.x.y, vp.x.y, J);
+            hB.y = heis_field<D>(p ? ey : cur.y.x, cur.y.y, prev.y.y, nxt.y.y, vm.y.y, vp.y.y, J);
+            hB.z = heis_field<D>(p ? ez : cur.z.x, cur.z.y, prev.z.y, nxt.z.y, vm.z.y, vp.z.y, J);
             if (a.update) {
                 bool changed = false;
 #pragma unroll
@@ -808,23 +822,18 @@ __global__ void __launch_bounds__(256, D == 2 ? 3 : 2) heis_pair(const OnArgs a)
                         sy = v.y;
                         sz = v.z;
                         changed = true;
-                    } else {
-                        const float u = u24(rnd.x);
-                        const float3 v = (TAB ? sphere_point_tab(tab, rnd.y, rnd.z) : sphere_point<FAST>(rnd.y, rnd.z));
-                        const float dE = -((v.x - sx) * h.x + (v.y - sy) * h.y + (v.z - sz) * h.z);
-                        if (dE <= 0.f || u < boltzmann<FAST>(-a.beta * dE)) {
-                            sx = v.x;
-                            sy = v.y;
-                            sz = v.z;
-                            changed = true;
+                        if (renorm) {
+                            const float inv = rsqrtf(sx * sx + sy * sy + sz * sz);
+                            sx *= inv;
+                            sy *= inv;
+                            sz *= inv;
                         }
-                    }
-                    if (renorm) {
-                        const float inv = rsqrtf(sx * sx + sy * sy + sz * sz);
-                        sx *= inv;
-                        sy *= inv;
-                        sz *= inv;
-                        changed = true;
+                    } else {
+                        const float3 v = TAB ? sphere_point_tab(tab, rnd.y, rnd.z)
+                                             : sphere_point<FAST>(rnd.y, rnd.z);
+                        changed = heis_metropolis<FAST>(sx, sy, sz, v, h.x, h.y, h.z, u24(rnd.x),
+                                                        a.beta, renorm) ||
+                                  changed;
                     }
                 }
                 if (changed) {
@@ -866,6 +875,289 @@ __device__ __forceinline__ CS2 cs_pair(const float* p, long long i)
     sincos_angle<FAST>(th.x, &r.s0, &r.c0);
     sincos_angle<FAST>(th.y, &r.s1, &r.c1);
     return r;
+}
+
+// ------------------------------------------------- staged 3D Heisenberg ----
+//
+// 3D Heisenberg, uniform J, Metropolis with the accurate functions, W = L/2 in
+// {32, 64, 128, 256}.  A work item is Y = 512 / W rows times the whole row
+// width of kTileZ consecutive planes; a block of 256 threads gives each
+// thread one column pair of one row and marches through the item's planes.
+// The other colour's planes z-1 .. z+kTileZ (each with its rows y0-1 .. y0+Y,
+// the y halo, wrapped) and the own colour's planes stream into shared memory
+// through one-dimensional bulk copies (the TMA engine, completion counted on
+// an mbarrier per stage) two planes ahead of use, so the threads hold no
+// register window and load latency overlaps the arithmetic.  Persistent
+// blocks take items in order (adjacent stripes of one slab after another).
+// One lane per warp polls each stage's mbarrier while the others wait in the
+// block barrier that follows.  Every wait is bounded: when one runs out the block
+// sets bit 0 of the control block's error word, waits (bounded) for the
+// copies it has in flight and stops; the host reports SL_ETIMEOUT.
+// Decisions, random numbers and arithmetic are those of heis_pair and
+// heis_stream, site for site (the shared heis_field / heis_metropolis).
+constexpr int kTileThreads = 256;
+constexpr int kTileZ = 8;        // planes per work item
+constexpr int kOthStages = 4;    // planes z-1, z, z+1 in use and z+2 in flight
+constexpr int kOwnStages = 2;
+// polls of an mbarrier before a wait gives up: with the 32 ns back-off, at
+// most a few seconds (a completed copy is seen within microseconds)
+constexpr long long kTileWaitLimit = 1LL << 25;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+// global -> shared bulk copy of `bytes` (a multiple of 16, both ends 16-byte
+// aligned) whose completion is counted on the mbarrier `bar`
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes,
+                                          uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+
+// wait for phase `parity` of the mbarrier to complete (non-blocking polls with
+// a short back-off); false after the limit
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+{
+    for (long long it = 0; it < kTileWaitLimit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (it >= 8) __nanosleep(32);
+    }
+    return false;
+}
+
+// Self-test of the bounded wait: an mbarrier armed for 16 bytes that no copy
+// ever delivers; the poll gives up after its limit and the kernel records
+// whether it did (1), or saw the phase complete (0).
+__device__ unsigned int g_wait_selftest;
+
+__global__ void wait_selftest_kernel()
+{
+    __shared__ __align__(8) unsigned long long bar;
+    const uint32_t b = smem_addr(&bar);
+    if (threadIdx.x == 0) {
+        mbar_init(b);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        mbar_expect(b, 16u);
+        g_wait_selftest = mbar_wait(b, 0u) ? 0u : 1u;
+    }
+}
+
+struct TileShape {
+    int W, Y;            // colour columns per row, rows per item
+    int oth_floats;      // one other-colour stage: 3 components x (Y + 2) rows x W
+    int own_floats;      // one own-colour stage: 3 components x Y rows x W
+};
+
+__host__ __device__ inline TileShape tile_shape(int W)
+{
+    TileShape g;
+    g.W = W;
+    g.Y = 512 / W;
+    g.oth_floats = 3 * (g.Y + 2) * W;
+    g.own_floats = 3 * g.Y * W;
+    return g;
+}
+
+template <bool MEAS>
+__global__ void __launch_bounds__(kTileThreads, 3) heis_tile3(const OnArgs a)
+{
+    extern __shared__ __align__(128) float tile_smem[];
+    __shared__ float2 tab[kTurnTab];
+    __shared__ __align__(8) unsigned long long bars[kOthStages + kOwnStages];
+    __shared__ double red[32];
+    fill_turn_table(tab);
+    const unsigned long long t64 = a.ctrl->t;
+    const uint32_t t = (uint32_t)t64;
+    const bool renorm = a.update && a.renorm_every > 0 &&
+                        (t64 + 1) % (unsigned long long)a.renorm_every == 0;
+    const int L = a.L, W = a.W;
+    const TileShape g = tile_shape(W);
+    const int Y = g.Y;
+    const long long H = a.H;
+    const float J = a.J;
+    float* oth_st = tile_smem;                               // kOthStages stages
+    float* own_st = tile_smem + kOthStages * g.oth_floats;  // kOwnStages stages
+    const int yi = threadIdx.x / (W / 2), k0 = 2 * (threadIdx.x % (W / 2));
+    const int nsy = L / Y, items = nsy * (L / kTileZ);
+    const uint32_t bar0 = smem_addr(bars);
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < kOthStages + kOwnStages; ++q) mbar_init(bar0 + 8 * q);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    uint32_t phase = 0;    // bit s: parity of stage s's next completion
+    uint32_t pending = 0;  // bit s: stage s has a fill in flight (every thread tracks it)
+    // other-colour plane pi of the item (plane z0 - 1 + pi, rows y0 - 1 .. y0 + Y)
+    auto issue_oth = [&](int pi, int y0, int z0) {
+        const int s = pi % kOthStages;
+        pending |= 1u << s;
+        if (threadIdx.x != 0) return;
+        // the block's reads of this stage (ordered by the barrier before the
+        // call) come before the bulk copy's writes
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        const uint32_t bar = bar0 + 8 * s;
+        mbar_expect(bar, (uint32_t)g.oth_floats * 4u);
+        int zz = z0 - 1 + pi;
+        zz = zz < 0 ? zz + L : (zz >= L ? zz - L : zz);
+        float* dst = oth_st + s * g.oth_floats;
+        for (int c = 0; c < 3; ++c) {
+            const float* plane = a.oth + c * H + (long long)zz * L * W;
+            float* d = dst + c * (Y + 2) * W;
+            if (y0 == 0) {  // row -1 is row L-1
+                bulk_load(smem_addr(d), plane + (long long)(L - 1) * W, (uint32_t)W * 4u, bar);
+                bulk_load(smem_addr(d + W), plane, (uint32_t)(Y + 1) * W * 4u, bar);
+            } else if (y0 + Y == L) {  // row y0 + Y is row 0
+                bulk_load(smem_addr(d), plane + (long long)(y0 - 1) * W, (uint32_t)(Y + 1) * W * 4u,
+                          bar);
+                bulk_load(smem_addr(d + (Y + 1) * W), plane, (uint32_t)W * 4u, bar);
+            } else {
+                bulk_load(smem_addr(d), plane + (long long)(y0 - 1) * W, (uint32_t)(Y + 2) * W * 4u,
+                          bar);
+            }
+        }
+    };
+    // own-colour plane oi of the item (plane z0 + oi, rows y0 .. y0 + Y - 1)
+    auto issue_own = [&](int oi, int y0, int z0) {
+        const int s = kOthStages + oi % kOwnStages;
+        pending |= 1u << s;
+        if (threadIdx.x != 0) return;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        const uint32_t bar = bar0 + 8 * s;
+        mbar_expect(bar, (uint32_t)g.own_floats * 4u);
+        float* dst = own_st + (oi % kOwnStages) * g.own_floats;
+        for (int c = 0; c < 3; ++c)
+            bulk_load(smem_addr(dst + c * Y * W),
+                      a.own + c * H + ((long long)(z0 + oi) * L + y0) * W, (uint32_t)Y * W * 4u, bar);
+    };
+    // Lane 0 of each warp polls (it observes the copy's completion for its
+    // warp); the block barrier after the waits passes the outcome to every
+    // thread.  A stage whose wait ran out stays marked in flight.
+    auto wait_stage = [&](int s) {
+        const bool ok =
+            (threadIdx.x & 31) != 0 || mbar_wait(bar0 + 8 * s, (phase >> s) & 1u);
+        phase ^= 1u << s;
+        pending &= ~(1u << s);
+        if (!ok) pending |= 1u << s;
+        return ok;
+    };
+    float pe = 0.f, pmx = 0.f, pmy = 0.f, pmz = 0.f;
+    bool failed = false;
+    for (int item = blockIdx.x; item < items && !failed; item += gridDim.x) {
+        const int y0 = (item % nsy) * Y, z0 = (item / nsy) * kTileZ;
+        const int y = y0 + yi;
+        for (int pi = 0; pi < kOthStages; ++pi) issue_oth(pi, y0, z0);
+        for (int oi = 0; oi < kOwnStages; ++oi) issue_own(oi, y0, z0);
+        for (int k = 0; k < kTileZ; ++k) {
+            bool ok = true;
+            if (k == 0) {
+                ok = wait_stage(0) && ok;
+                ok = wait_stage(1) && ok;
+            }
+            ok = wait_stage((k + 2) % kOthStages) && ok;
+            ok = wait_stage(kOthStages + k % kOwnStages) && ok;
+            if (__syncthreads_or(!ok)) {
+                // the phase bits flipped for a completion that did not come
+                phase ^= pending;
+                failed = true;
+                break;
+            }
+            const int z = z0 + k;
+            const int p = (y + z + a.c) & 1;
+            const float* om = oth_st + (k % kOthStages) * g.oth_floats;        // plane z - 1
+            const float* oc = oth_st + ((k + 1) % kOthStages) * g.oth_floats;  // plane z
+            const float* op = oth_st + ((k + 2) % kOthStages) * g.oth_floats;  // plane z + 1
+            const float* ow = own_st + (k % kOwnStages) * g.own_floats;
+            float hA[3], hB[3], sp[3][2], cur2[3][2];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const int row = c * (Y + 2) * W + (yi + 1) * W;
+                const float2 cur = *reinterpret_cast<const float2*>(oc + row + k0);
+                const float edge = oc[row + (p ? ((k0 + 2) & (W - 1)) : ((k0 - 1) & (W - 1)))];
+                const float2 ym = *reinterpret_cast<const float2*>(oc + row - W + k0);
+                const float2 yp = *reinterpret_cast<const float2*>(oc + row + W + k0);
+                const float2 zm = *reinterpret_cast<const float2*>(om + row + k0);
+                const float2 zp = *reinterpret_cast<const float2*>(op + row + k0);
+                const float2 own = *reinterpret_cast<const float2*>(ow + c * Y * W + yi * W + k0);
+                hA[c] = heis_field<3>(p ? cur.y : edge, cur.x, zm.x, zp.x, ym.x, yp.x, J);
+                hB[c] = heis_field<3>(p ? edge : cur.x, cur.y, zm.y, zp.y, ym.y, yp.y, J);
+                sp[c][0] = own.x;
+                sp[c][1] = own.y;
+                cur2[c][0] = cur.x;
+                cur2[c][1] = cur.y;
+            }
+            const int j = (z * L + y) * W + k0;  // global colour index of column k0
+            if (a.update) {
+                bool changed = false;
+#pragma unroll
+                for (int b = 0; b < 2; ++b) {
+                    const uint4 rnd = philox4x32_10(
+                        make_uint4((uint32_t)(j + b), t, a.replica, (kSweep << 1) | (uint32_t)a.c),
+                        a.rk);
+                    const float* h = b ? hB : hA;
+                    const float3 v = sphere_point_tab(tab, rnd.y, rnd.z);
+                    changed = heis_metropolis<false>(sp[0][b], sp[1][b], sp[2][b], v, h[0], h[1],
+                                                     h[2], u24(rnd.x), a.beta, renorm) ||
+                              changed;
+                }
+                if (changed) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c)
+                        *reinterpret_cast<float2*>(a.own + c * H + j) =
+                            make_float2(sp[c][0], sp[c][1]);
+                }
+            }
+            if (MEAS) {
+                pe -= sp[0][0] * hA[0] + sp[1][0] * hA[1] + sp[2][0] * hA[2] + sp[0][1] * hB[0] +
+                      sp[1][1] * hB[1] + sp[2][1] * hB[2];
+                pmx += sp[0][0] + sp[0][1] + cur2[0][0] + cur2[0][1];
+                pmy += sp[1][0] + sp[1][1] + cur2[1][0] + cur2[1][1];
+                pmz += sp[2][0] + sp[2][1] + cur2[2][0] + cur2[2][1];
+            }
+            __syncthreads();  // the stages of plane z - 1 and of own plane z are free
+            if (k + kOthStages < kTileZ + 2) issue_oth(k + kOthStages, y0, z0);
+            if (k + kOwnStages < kTileZ) issue_own(k + kOwnStages, y0, z0);
+        }
+    }
+    if (failed) {
+        // a wait ran out: report it, wait (bounded again) for the copies still
+        // in flight so that none lands after the block has left, then stop
+        if (threadIdx.x == 0) atomicOr(&a.ctrl->error, 1u);
+        for (int s = 0; s < kOthStages + kOwnStages; ++s)
+            if ((pending >> s) & 1u) wait_stage(s);
+        return;
+    }
+    if (!MEAS) return;
+    Partial mine;
+    mine.i0 = mine.i1 = 0;
+    mine.f[0] = block_sum((double)pe, red);
+    mine.f[1] = block_sum((double)pmx, red);
+    mine.f[2] = block_sum((double)pmy, red);
+    mine.f[3] = block_sum((double)pmz, red);
+    store_partial(a.partials, mine);
 }
 
 // XY, 2D: each thread owns the column pair (2q, 2q+1), whose sites share one
@@ -1147,6 +1439,45 @@ OnArgs make_args(const sl_lattice* h, int c)
     return a;
 }
 
+// The staged 3D Heisenberg kernel: uniform J, Metropolis with the accurate
+// functions, W = L/2 in {32, 64, 128, 256}.
+bool tile_ok(const sl_lattice* h)
+{
+    const int W = h->W;
+    return h->n == 3 && h->d == 3 && h->bonds[0][0] == nullptr && !h->slab &&
+           (W == 32 || W == 64 || W == 128 || W == 256) && h->update == SL_UPDATE_METROPOLIS &&
+           !h->fast_math;
+}
+
+cudaError_t launch_tile(const sl_lattice* h, const OnArgs& a, cudaStream_t s)
+{
+    const TileShape g = tile_shape(h->W);
+    const size_t dyn = (size_t)(kOthStages * g.oth_floats + kOwnStages * g.own_floats) * 4;
+    static bool attr_set[2] = {false, false};
+    if (!attr_set[a.measure ? 1 : 0]) {
+        const cudaError_t e =
+            a.measure ? cudaFuncSetAttribute(heis_tile3<true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 65536)
+                      : cudaFuncSetAttribute(heis_tile3<false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 65536);
+        if (e != cudaSuccess) return e;
+        attr_set[a.measure ? 1 : 0] = true;
+    }
+    const long long items = (long long)(h->L / g.Y) * (h->L / kTileZ);
+    // resident blocks per SM (shared memory: the stages plus the 8 KiB table)
+    const int fit = 3;
+    const int per_sm = h->blocks_per_sm > 0 && h->blocks_per_sm < fit ? h->blocks_per_sm : fit;
+    long long grid = (long long)h->sms * per_sm;
+    if (grid > items) grid = items;
+    if (grid > kMaxBlocks) grid = kMaxBlocks;
+    if (a.measure) heis_tile3<true><<<(int)grid, kTileThreads, dyn, s>>>(a);
+    else heis_tile3<false><<<(int)grid, kTileThreads, dyn, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !a.measure) return e;
+    on_finish_kernel<<<1, kFinishThreads, 0, s>>>(a, (unsigned)grid);
+    return cudaGetLastError();
+}
+
 bool on_stream_ok(const sl_lattice* h)
 {
     if (h->bonds[0][0] != nullptr || h->kernel == 1) return false;
@@ -1156,7 +1487,29 @@ bool on_stream_ok(const sl_lattice* h)
 
 }  // namespace
 
-bool on_streams(const sl_lattice* h) { return on_stream_ok(h); }
+bool on_streams(const sl_lattice* h) { return on_stream_ok(h) || (h->kernel == 4 && tile_ok(h)); }
+
+bool on_tile_ok(const sl_lattice* h) { return tile_ok(h); }
+
+}  // namespace spinmc
+
+extern "C" int sl_wait_selftest(void* stream, int* timed_out)
+{
+    using namespace spinmc;
+    if (!timed_out) return fail(SL_EINVAL, "timed_out is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    wait_selftest_kernel<<<1, 32, 0, s>>>();
+    cudaError_t e = cudaGetLastError();
+    unsigned v = 2;
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbolAsync(&v, g_wait_selftest, sizeof v, 0,
+                                                        cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "sl_wait_selftest");
+    *timed_out = (int)v;
+    return SL_OK;
+}
+
+namespace spinmc {
 
 namespace {
 
@@ -1175,6 +1528,7 @@ template <int NC>
 cudaError_t launch_on(const sl_lattice* h, OnArgs a, cudaStream_t s)
 {
     const int var = a.update && h->update == SL_UPDATE_HEATBATH ? 2 : h->fast_math != 0;
+    if (NC == 3 && h->kernel == 4 && tile_ok(h)) return launch_tile(h, a, s);
     if (on_stream_ok(h)) {
         // Heisenberg on column pairs when W % 64 == 0 (unless kernel 3 asks for
         // single columns); XY always takes pairs

@@ -86,6 +86,7 @@ _sig("sl_batch_tuning", _int, _vp, _int, ctypes.POINTER(_int), ctypes.POINTER(_i
      ctypes.POINTER(_dbl))
 _sig("sl_ising_measure_static", _int, _int, _int, _dbl, _vp, _vp, _vp)
 _sig("sl_microbench_threads", _int, ctypes.POINTER(_int))
+_sig("sl_wait_selftest", _int, _vp, ctypes.POINTER(_int))
 _sig("sl_microbench", _int, _int, _int, _vp, _sz, _vp, ctypes.POINTER(_dbl))
 _sig("sl_walkers_required_bytes", _int, _int, _int, _vp, _vp, _int, ctypes.POINTER(_sz))
 _sig("sl_walkers_create", _int, _int, _int, _vp, _vp, _int, _u64, _vp, _sz, _vp,
@@ -347,6 +348,13 @@ def sl_batch_tuning(h):
         if cls >= n:
             break
     return out
+
+
+def sl_wait_selftest(stream):
+    """1 if the bounded wait of the staged kernels gave up as designed."""
+    r = _int()
+    _check(_lib.sl_wait_selftest(stream, ctypes.byref(r)), "sl_wait_selftest")
+    return r.value
 
 
 def sl_microbench_threads():

@@ -188,6 +188,38 @@ def test_streaming_and_generic_kernels(sm, n, d, L, beta, kernel):
     Pair(sm, n, d, L, beta, 6, kernel=kernel, J=-0.8 if n == 3 else 1.0).check()
 
 
+@pytest.mark.parametrize("L,J,renorm", [(64, 1.0, 16), (128, -0.8, 16), (256, 1.0, 16),
+                                        (64, 1.0, 1)])
+def test_staged_tiles_match_oracle_and_column_pairs(sm, L, J, renorm):
+    """The staged 3D Heisenberg kernel (planes streamed into shared memory by
+    bulk asynchronous copies) against the oracle, and spin for spin equal to
+    the column-pair and single-column kernels (every rounding of the field,
+    dE and renormalisation spelled out in one shared helper); renorm = 1
+    renormalises in every sweep."""
+    d, beta = 3, 0.693
+    Pair(sm, 3, d, L, beta, 6, kernel=4, J=J, renorm=renorm).check()
+    spins = []
+    for kern in (2, 3, 4):
+        lat = sm.Lattice(d, L, n=3, J=J, seed=7)
+        lat.set_option(sm.SL_OPT_RENORM_EVERY, renorm)
+        lat.set_option(sm.SL_OPT_KERNEL, kern)
+        E, _ = lat.sweep_series(beta, 5, 3)
+        spins.append((lat.get_spins(), E.cpu().numpy()))
+        lat.close()
+    for other in spins[1:]:
+        np.testing.assert_array_equal(spins[0][0], other[0])
+        np.testing.assert_allclose(spins[0][1], other[1], rtol=1e-6)
+
+
+def test_staged_tiles_refuse_other_lattices(sm):
+    for d, L, n, fast in ((3, 96, 3, 0), (2, 128, 3, 0), (3, 64, 3, 1), (3, 64, 2, 0)):
+        lat = sm.Lattice(d, L, n=n, seed=1)
+        lat.set_option(sm.SL_OPT_FAST_MATH, fast)
+        with pytest.raises(sm.SpinMCError):
+            lat.set_option(sm.SL_OPT_KERNEL, 4)
+        lat.close()
+
+
 @pytest.mark.parametrize("n,d,L,beta", [(3, 3, 64, 0.693), (2, 2, 128, 1.12)])
 def test_streaming_fast_math(sm, n, d, L, beta):
     Pair(sm, n, d, L, beta, 6, fast=1, tie_tol=TIE_TOL_FAST, kernel=2).check()
@@ -317,3 +349,19 @@ def test_precision_report(sm, n, d, L, beta, capsys):
                  p.compared / (p.N * p.nsw)))
     p.check(min_fraction=0.95)
     assert p.max_dE < 1e-4 and p.max_dm < 1e-4
+
+
+def test_bounded_wait_gives_up_and_the_context_stays_usable(sm):
+    """The staged kernels' mbarrier waits are bounded: a wait for bytes that
+    never arrive gives up within seconds, the kernel returns, and the device
+    runs the next sweep normally."""
+    import time
+    import torch
+    t0 = time.perf_counter()
+    assert sm.sl_wait_selftest(torch.cuda.current_stream().cuda_stream) == 1
+    assert time.perf_counter() - t0 < 30
+    lat = sm.Lattice(3, 64, n=3, seed=1)
+    lat.set_option(sm.SL_OPT_KERNEL, 4)
+    E, _ = lat.sweep_series(0.693, 2, 3)
+    assert np.isfinite(E.cpu().numpy()).all()
+    lat.close()
