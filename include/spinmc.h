@@ -207,8 +207,9 @@ int sl_autotune(sl_lattice* lat, double beta, int trial_sweeps, const char* cach
 /*
  * sl_workspace_bytes — device bytes of workspace an update rule needs on this
  * lattice: 0 for SL_UPDATE_METROPOLIS and SL_UPDATE_HEATBATH; for
- * SL_UPDATE_SW, 4 N bytes of cluster labels plus one bit per tile-face bond
- * (Section 3: clusters are labelled in tiles, then the tiles are joined).
+ * SL_UPDATE_SW, 4 N bytes of cluster labels, one bit per tile-face bond and
+ * a list of up to N tile roots (4 N bytes) (Section 3: clusters are labelled
+ * in tiles, then the tiles are joined).
  * SL_EINVAL for a NULL argument or an unknown rule.
  */
 int sl_workspace_bytes(const sl_lattice* lat, int update, size_t* bytes);

@@ -15,19 +15,22 @@
 //               nothing changes, which names every tile cluster by its
 //               smallest site (a y/z bond is skipped when the bond beside it
 //               already joins the same two runs), writes every site's label (the natural index
-//               of its tile root, the smallest site of its tile cluster) and
-//               one bit per active bond that leaves the tile;
+//               of its tile root, the smallest site of its tile cluster),
+//               one bit per active bond that leaves the tile, and appends
+//               its tile roots to a list;
 //   sw_merge    one thread per tile-face bond: unites the two labels of each
 //               active face bond in global memory (same hooking rule);
 //               afterwards the root of every cluster is its smallest site;
-//   sw_resolve  every tile root points straight at its cluster's root; the
-//               cluster roots draw their flip bit;
-//   sw_flip     every site reads its root's bit (at most two lookups: its
-//               tile root, then the cluster root) and flips;
+//   sw_resolve  one thread per listed tile root: follows the parents to the
+//               cluster root g and rewrites the tile root's word as g with
+//               g's flip bit (drawn from g's Philox output);
+//   sw_flip     every site reads its tile root's word (its own word if it is
+//               one) for the flip bit and flips;
 //   sw_measure  E and M of the new configuration, closing the sweep.
 // Label words: bits 0-29 the parent (a site index, N <= 2^30), bit 31 marks
-// a tile root, bit 30 is the flip bit of a cluster root.  Every parent is a
-// smaller or equal index and, beyond a site's first step, a tile root.
+// a tile root; after sw_resolve bit 30 of a tile root's word is its
+// cluster's flip bit.  Every parent is a smaller or equal index and, beyond
+// a site's first step, a tile root.
 // Random numbers: the forward bond (i, i + e_mu) draws output 2 (i & 1) + mu
 // of Philox(i >> 1, t, replica, 5 << 1) in 2D, output mu of
 // Philox(i, t, replica, 5 << 1) in 3D; the cluster rooted at r flips iff the
@@ -70,6 +73,8 @@ struct SwArgs {
     int8_t* s[2];     // colour arrays (0 = up, 1 = down)
     uint32_t* lab;    // N labels, natural order
     uint32_t* face;   // WORDS per tile
+    uint32_t* roots;  // the tile roots of an update (at most N), in no fixed order
+    unsigned* nroots; // their number
     int L;
     int ntx, nty, ntz;
     long long N, ntiles;
@@ -376,6 +381,8 @@ __global__ void __launch_bounds__(kSwThreads, 3) sw_local(const SwArgs a)
     }
 
     // labels: the natural index of each site's tile root; tile roots marked
+    // and counted (bit 2k + e of `mine`)
+    uint32_t mine = 0;
     if (ex) {
 #pragma unroll
         for (int k = 0; k < RPW; ++k) {
@@ -390,13 +397,43 @@ __global__ void __launch_bounds__(kSwThreads, 3) sw_local(const SwArgs a)
                 const uint32_t rx = m % TX, rrow = m / TX;
                 const uint32_t ry = rrow % TY, rz = rrow / TY;
                 w[e] = ((uint32_t)X0 + rx) + L * (((uint32_t)Y0 + ry) + L * ((uint32_t)Z0 + rz));
-                if (m == l0 + e) w[e] |= kTileRoot;
+                if (m == l0 + e) {
+                    w[e] |= kTileRoot;
+                    mine |= 1u << (2 * k + e);
+                }
             }
             const uint32_t i0 = (uint32_t)(X0 + lx0) + L * ((uint32_t)(Y0 + ly) + L * (uint32_t)(Z0 + lz));
             *reinterpret_cast<uint2*>(a.lab + i0) = make_uint2(w[0], w[1]);
         }
     }
     for (int w = threadIdx.x; w < WORDS; w += blockDim.x) a.face[b * WORDS + w] = fm[w];
+    // append the tile roots to the update's list: a warp scan of the counts,
+    // one shared atomic per warp, one global atomic per block
+    __shared__ unsigned blk_count, blk_base;
+    if (threadIdx.x == 0) blk_count = 0;
+    __syncthreads();
+    const unsigned cnt = __popc(mine);
+    unsigned incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    unsigned wbase = 0;
+    if (lane == 31) wbase = atomicAdd(&blk_count, incl);
+    wbase = __shfl_sync(0xFFFFFFFFu, wbase, 31);
+    __syncthreads();
+    if (threadIdx.x == 0) blk_base = atomicAdd(a.nroots, blk_count);
+    __syncthreads();
+    unsigned pos = blk_base + wbase + incl - cnt;
+    for (uint32_t bits = mine; bits; bits &= bits - 1) {
+        const int bit = __ffs(bits) - 1;
+        const int k = bit >> 1, e = bit & 1;
+        const int row = warp + NW * k;
+        const int ly = row % TY, lz = row / TY;
+        a.roots[pos++] = (uint32_t)(X0 + lx0 + e) +
+                         L * ((uint32_t)(Y0 + ly) + L * (uint32_t)(Z0 + lz));
+    }
 }
 
 template <int D>
@@ -444,62 +481,34 @@ __global__ void __launch_bounds__(256) sw_merge(const SwArgs a)
     }
 }
 
-// Every tile root is pointed straight at its cluster's root; cluster roots
-// draw the flip bit.  A thread owns four consecutive labels and is their only
-// writer here (non-tile-root labels are not touched), so it loads and stores
-// them as one vector.
+// One thread per listed tile root: follow the parents to the cluster root g
+// (the smallest site of the cluster) and rewrite the tile root's word as g
+// with g's flip bit, the top bit of output 0 of Philox(g, t, replica, 6 << 1).
+// Tile roots are each other's parents, so a chase may read a word another
+// thread has just rewritten; the new word points at g itself, so the chase
+// still ends at g.
 __global__ void __launch_bounds__(256) sw_resolve(const SwArgs a)
 {
     const uint32_t t = (uint32_t)a.ctrl->t;
-    const long long n4 = a.N >> 2;
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n4;
-         q += (long long)gridDim.x * blockDim.x) {
-        const uint4 v = __ldcg(reinterpret_cast<const uint4*>(a.lab) + q);
-        uint32_t w[4] = {v.x, v.y, v.z, v.w};
-        if (!((w[0] | w[1] | w[2] | w[3]) & kTileRoot)) continue;
-        bool changed = false;
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            if (!(w[e] & kTileRoot)) continue;
-            const uint32_t i = (uint32_t)(4 * q + e);
-            const uint32_t p0 = w[e] & kMask;
-            if (p0 == i) {
-                const uint4 r = philox4x32_10(make_uint4(i, t, a.replica, kSwFlip << 1), a.rk);
-                if (r.x >> 31) {
-                    w[e] |= kFlipBit;
-                    changed = true;
-                }
-                continue;
-            }
-            uint32_t p = p0;
-            while (true) {
-                const uint32_t g = gload(a.lab + p) & kMask;
-                if (g == p) break;
-                p = g;
-            }
-            if (p != p0) {
-                w[e] = p | kTileRoot;
-                changed = true;
-            }
+    const unsigned n = *a.nroots;
+    for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+        const uint32_t r = __ldcg(a.roots + q);
+        uint32_t p = gload(a.lab + r) & kMask;
+        while (true) {
+            const uint32_t g = gload(a.lab + p) & kMask;
+            if (g == p) break;
+            p = g;
         }
-        if (changed)
-            __stcg(reinterpret_cast<uint4*>(a.lab) + q, make_uint4(w[0], w[1], w[2], w[3]));
+        const uint4 rnd = philox4x32_10(make_uint4(p, t, a.replica, kSwFlip << 1), a.rk);
+        gstore(a.lab + r, p | kTileRoot | ((rnd.x >> 31) ? kFlipBit : 0u));
     }
 }
 
-// flip bit of site i's cluster from its label word l: the parent is the site
-// itself (a cluster root), a cluster root, or a tile root whose word names
-// the cluster root
+// flip bit of site i's cluster from its label word l: a tile root carries it,
+// any other site's parent is its tile root
 __device__ __forceinline__ uint32_t root_bit(const SwArgs& a, uint32_t i, uint32_t l)
 {
-    uint32_t r = l & kMask, word = l;
-    while (r != i) {
-        word = __ldg(a.lab + r);
-        const uint32_t g = word & kMask;
-        if (g == r) break;
-        i = r;
-        r = g;
-    }
+    const uint32_t word = (l & kTileRoot) ? l : __ldg(a.lab + (l & kMask));
     return (word & kFlipBit) ? 1u : 0u;
 }
 
@@ -619,9 +628,11 @@ cudaError_t sw_update(const SwArgs& a0, cudaStream_t s)
 {
     SwArgs a = a0;
     const long long mergers = a.ntiles * SwFace<D>::WORDS * 32;
+    cudaError_t e = cudaMemsetAsync(a.nroots, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
     sw_local<D><<<(unsigned)a.ntiles, kSwThreads, 0, s>>>(a);
     sw_merge<D><<<grid_for(mergers, 256), 256, 0, s>>>(a);
-    sw_resolve<<<grid_for(a.N / 4, 256), 256, 0, s>>>(a);
+    sw_resolve<<<grid_for(a.N, 256), 256, 0, s>>>(a);
     sw_flip<<<grid_for((a.N / 2 + 3) / 4, 256), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
@@ -634,7 +645,8 @@ size_t sw_workspace_bytes(int d, int L)
     const size_t N = (size_t)L * L * (d == 3 ? L : 1);
     const long long nt = d == 2 ? tiles_of<2>(L, ntx, nty, ntz) : tiles_of<3>(L, ntx, nty, ntz);
     const size_t words = d == 2 ? SwFace<2>::WORDS : SwFace<3>::WORDS;
-    return align_up(N * 4) + align_up((size_t)nt * words * 4);
+    // labels, tile-face bits, the tile-root list and its count
+    return align_up(N * 4) + align_up((size_t)nt * words * 4) + align_up(N * 4) + align_up(4);
 }
 
 cudaError_t ising_sw_sweeps(const sl_lattice* h, const SweepParams& p, int64_t count,
@@ -645,6 +657,15 @@ cudaError_t ising_sw_sweeps(const sl_lattice* h, const SweepParams& p, int64_t c
     a.s[1] = (int8_t*)h->spins[1];
     a.lab = (uint32_t*)h->ws;
     a.face = (uint32_t*)((char*)h->ws + align_up((size_t)h->N * 4));
+    {
+        int ntx, nty, ntz;
+        const long long nt = h->d == 2 ? tiles_of<2>(h->L, ntx, nty, ntz)
+                                       : tiles_of<3>(h->L, ntx, nty, ntz);
+        const size_t words = h->d == 2 ? SwFace<2>::WORDS : SwFace<3>::WORDS;
+        char* after_face = (char*)a.face + align_up((size_t)nt * words * 4);
+        a.roots = (uint32_t*)after_face;
+        a.nroots = (unsigned*)(after_face + align_up((size_t)h->N * 4));
+    }
     a.L = h->L;
     a.N = h->N;
     a.ntiles = h->d == 2 ? tiles_of<2>(h->L, a.ntx, a.nty, a.ntz)
