@@ -160,6 +160,25 @@ __device__ __forceinline__ void tile_origin(const SwArgs& a, long long b, int& X
     nz = D == 3 ? min(TZ, a.L - Z0) : 1;
 }
 
+// position of the q-th (from 0) set bit of m; q < popc(m)
+__device__ __forceinline__ int nth_set_bit(uint32_t m, int q)
+{
+    int pos = 0;
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1) {
+        const uint32_t low = m & ((1u << w) - 1u);
+        const int c = __popc(low);
+        if (q >= c) {
+            q -= c;
+            m >>= w;
+            pos += w;
+        } else {
+            m = low;
+        }
+    }
+    return pos;
+}
+
 __device__ __forceinline__ bool bond_active(const SwArgs& a, uint8_t s0, uint8_t s1, uint32_t u)
 {
     return (int)(s0 ^ s1) == a.anti && !a.never && u <= a.thr;
@@ -341,6 +360,37 @@ __global__ void __launch_bounds__(kSwThreads, 3) sw_local(const SwArgs a)
             }
         }
     }
+    // Only run heads (the first site of each x-run) take part in the rounds:
+    // every other site keeps pointing at its head, so a label is read through
+    // the head (two steps) and the jumps run over the heads alone, dealt out
+    // to the warp's lanes (lane l takes the l-th and (l + 32)-th head of each
+    // of its rows: one jump per lane where a row has at most 32 heads, against
+    // two sites per lane otherwise).  Heads are decided by the x-bond ballots.
+    uint32_t heads[RPW];  // per row: two 16-bit tile-local sites, 0xFFFF = none
+    {
+        const uint32_t valid = nx >= 64 ? 0xFFFFFFFFu : ((1u << (nx >> 1)) - 1u);
+#pragma unroll
+        for (int k = 0; k < RPW; ++k) {
+            heads[k] = 0xFFFFFFFFu;
+            const int row = warp + NW * k;
+            const int ly = row % TY, lz = row / TY;
+            if (ly >= ny || lz >= nz) continue;
+            const uint32_t h0 = ~(bx[1][row] << 1) & valid;  // even sites starting a run
+            const uint32_t h1 = ~bx[0][row] & valid;         // odd sites starting a run
+            const int n0 = __popc(h0), n = n0 + __popc(h1);
+            uint32_t w = 0;
+#pragma unroll
+            for (int slot = 0; slot < 2; ++slot) {
+                const int q = lane + 32 * slot;
+                uint32_t site = 0xFFFFu;
+                if (q < n)
+                    site = (uint32_t)(TX * row) + (q < n0 ? 2u * (uint32_t)nth_set_bit(h0, q)
+                                                          : 2u * (uint32_t)nth_set_bit(h1, q - n0) + 1u);
+                w |= site << (16 * slot);
+            }
+            heads[k] = w;
+        }
+    }
     volatile uint32_t* vp = par;
     while (true) {
         bool changed = false;
@@ -351,30 +401,26 @@ __global__ void __launch_bounds__(kSwThreads, 3) sw_local(const SwArgs a)
             const int mu = 1 + bit % (D - 1);
             const uint32_t u = (uint32_t)(lx0 + e + TX * (warp + NW * k));
             const uint32_t v = u + (mu == 1 ? (uint32_t)TX : (uint32_t)(TX * TY));
-            const uint32_t pu = vp[u], pv = vp[v];
+            const uint32_t pu = vp[vp[u]], pv = vp[vp[v]];
             if (pu != pv) {
                 atomicMin(par + max(pu, pv), min(pu, pv));
                 changed = true;
             }
         }
         __syncthreads();
-        if (ex) {
 #pragma unroll
-            for (int k = 0; k < RPW; ++k) {
-                const int row = warp + NW * k;
-                const int ly = row % TY, lz = row / TY;
-                if (ly >= ny || lz >= nz) continue;
+        for (int k = 0; k < RPW; ++k) {
 #pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    const uint32_t l = (uint32_t)(lx0 + e + TX * row);
-                    uint32_t p = vp[l];
-                    while (true) {
-                        const uint32_t q = vp[p];
-                        if (q == p) break;
-                        p = q;
-                    }
-                    vp[l] = p;
+            for (int slot = 0; slot < 2; ++slot) {
+                const uint32_t l = (heads[k] >> (16 * slot)) & 0xFFFFu;
+                if (l == 0xFFFFu) continue;
+                uint32_t p = vp[l];
+                while (true) {
+                    const uint32_t q = vp[p];
+                    if (q == p) break;
+                    p = q;
                 }
+                vp[l] = p;
             }
         }
         if (!__syncthreads_or(changed)) break;
@@ -393,7 +439,7 @@ __global__ void __launch_bounds__(kSwThreads, 3) sw_local(const SwArgs a)
             uint32_t w[2];
 #pragma unroll
             for (int e = 0; e < 2; ++e) {
-                const uint32_t m = par[l0 + e];  // smallest site of the tile cluster
+                const uint32_t m = vp[vp[l0 + e]];  // smallest site of the tile cluster
                 const uint32_t rx = m % TX, rrow = m / TX;
                 const uint32_t ry = rrow % TY, rz = rrow / TY;
                 w[e] = ((uint32_t)X0 + rx) + L * (((uint32_t)Y0 + ry) + L * ((uint32_t)Z0 + rz));
