@@ -106,6 +106,26 @@ __device__ __forceinline__ void count_planes(const uint32_t (&u)[6], uint32_t& b
     }
 }
 
+// floor(n / L) for n < 2^26 from M = floor((2^32 - 1) / L) + 1: M L = 2^32 + e
+// with 0 <= e < L, so n M / 2^32 exceeds n / L by n e / (L 2^32) < 1 / L,
+// which never reaches the next integer
+__device__ __forceinline__ int div_small(int n, uint32_t M)
+{
+    return (int)__umulhi((uint32_t)n, M);
+}
+
+// Append the comparison u > th to the low end of a plane word (pl = 2 pl +
+// [u > th]) given nth = ~th: u + ~th = u - th - 1 + 2^32 carries out iff
+// u > th, and the doubling adds that carry in.
+__device__ __forceinline__ uint32_t push_gt(uint32_t pl, uint32_t u, uint32_t nth)
+{
+    uint32_t d, r;
+    asm("add.cc.u32 %0, %2, %3;\n\taddc.u32 %1, %4, %4;"
+        : "=r"(d), "=r"(r)
+        : "r"(u), "r"(nth), "r"(pl));
+    return r;
+}
+
 // A barrier over the nthr threads of one sample's sub-group: the whole CTA
 // (barrier 0) or named barrier `bar` (1..15) of nthr threads.
 __device__ __forceinline__ void group_sync(int bar, int nthr)
@@ -129,6 +149,7 @@ __device__ void run_sample(const BatchArgs& a, int s, int L, unsigned char* base
     uint32_t* S1 = S0 + H;
     uint8_t* B0 = reinterpret_cast<uint8_t*>(S1 + H);
     uint8_t* B1 = B0 + H;
+    // complemented thresholds (~th) of each slot's current temperature
     uint4* thr_slot = reinterpret_cast<uint4*>(B0 + ((2 * H + 15) / 16) * 16);
     long long* E_slot = reinterpret_cast<long long*>(thr_slot + kMaxTemps);
     int* unsat = reinterpret_cast<int*>(E_slot + kMaxTemps);
@@ -136,6 +157,7 @@ __device__ void run_sample(const BatchArgs& a, int s, int L, unsigned char* base
     const int lane = tid & 31, warp = tid >> 5;
     const uint32_t active = nt == 32 ? 0xFFFFFFFFu : ((1u << nt) - 1u);
     const uint32_t gs = a.sample0 + (uint32_t)s;  // the sample's global index
+    const uint32_t Minv = 0xFFFFFFFFu / (uint32_t)L + 1u;  // for div_small by L
 
     // load the sample
     const long long w0 = a.word_off[s];
@@ -150,7 +172,7 @@ __device__ void run_sample(const BatchArgs& a, int s, int L, unsigned char* base
     group_sync(bar, nthr);
     if (tid < nt) {
         const uint4 th = reinterpret_cast<const uint4*>(a.thr_temp)[tid];
-        thr_slot[sot[tid]] = th;
+        thr_slot[sot[tid]] = make_uint4(~th.x, ~th.y, ~th.z, ~th.w);
     }
     group_sync(bar, nthr);
 
@@ -166,21 +188,23 @@ __device__ void run_sample(const BatchArgs& a, int s, int L, unsigned char* base
             for (int g = tid; g < G; g += nthr) {
                 // planes g_k[b]: bit r set iff slot r's u at site 4g+b exceeds
                 // threshold k of its temperature
+                // (slots from the highest down, each comparison pushed in at
+                // bit 0, so slot r ends at bit r)
                 uint32_t pl[4][3];
 #pragma unroll
                 for (int b = 0; b < 4; ++b) pl[b][0] = pl[b][1] = pl[b][2] = 0u;
 #pragma unroll
-                for (int r = 0; r < kMaxTemps; ++r) {
+                for (int r = kMaxTemps - 1; r >= 0; --r) {
                     if (r < nt) {
                         const uint4 rnd = philox4x32_10(
                             make_uint4((uint32_t)g, (uint32_t)t, gs * (uint32_t)nt + (uint32_t)r, ctr_w), a.rk);
-                        const uint4 th = thr_slot[r];
+                        const uint4 nth = thr_slot[r];
                         const uint32_t u[4] = {rnd.x, rnd.y, rnd.z, rnd.w};
 #pragma unroll
                         for (int b = 0; b < 4; ++b) {
-                            if (u[b] > th.x) pl[b][0] |= 1u << r;
-                            if (u[b] > th.y) pl[b][1] |= 1u << r;
-                            if (D == 3 && u[b] > th.z) pl[b][2] |= 1u << r;
+                            pl[b][0] = push_gt(pl[b][0], u[b], nth.x);
+                            pl[b][1] = push_gt(pl[b][1], u[b], nth.y);
+                            if (D == 3) pl[b][2] = push_gt(pl[b][2], u[b], nth.z);
                         }
                     }
                 }
@@ -188,9 +212,10 @@ __device__ void run_sample(const BatchArgs& a, int s, int L, unsigned char* base
                 for (int b = 0; b < 4; ++b) {
                     const int j = 4 * g + b;
                     const int i0 = 2 * j;
-                    int x = i0 % L;
-                    const int rr = i0 / L;
-                    const int y = rr % L, z = rr / L;
+                    const int rr = div_small(i0, Minv);
+                    int x = i0 - rr * L;
+                    const int z = div_small(rr, Minv);
+                    const int y = rr - z * L;
                     x += (c + y + z) & 1;
                     int nm[3], np[3];
                     {
@@ -273,7 +298,10 @@ __device__ void run_sample(const BatchArgs& a, int s, int L, unsigned char* base
                 }
             }
             __syncwarp();
-            if (k < nt) thr_slot[sot[k]] = reinterpret_cast<const uint4*>(a.thr_temp)[k];
+            if (k < nt) {
+                const uint4 th = reinterpret_cast<const uint4*>(a.thr_temp)[k];
+                thr_slot[sot[k]] = make_uint4(~th.x, ~th.y, ~th.z, ~th.w);
+            }
             unsat[lane] = 0;
         }
         group_sync(bar, nthr);
