@@ -419,17 +419,20 @@ def configure(spinmc, lat, wl):
         lat.set_option(spinmc.SL_OPT_MULTIHIT, wl["multihit"])
 
 
-def time_sweeps(spinmc, wl, steps, warmup, replica, want_clocks, local, shape=None):
+def time_sweeps(spinmc, wl, steps, warmup, replica, want_clocks, local, shape=None,
+                tune_cache=None):
     """Device-timed K sweeps of one lattice, after the launch-shape autotuner
-    picked rows per thread and the grid cap (outside the timed region);
-    returns (ms, clocks, E of the last sweep) and fills `shape`."""
+    picked rows per thread and the grid cap (outside the timed region; its
+    choice is read from and written to `tune_cache` when one is given, so a
+    profiled run can repeat the shape a plain run picked); returns (ms,
+    clocks, E of the last sweep) and fills `shape`."""
     import torch
     from paper_1107_5463_gb300 import inputs
     storage = spinmc.SL_STORE_BITS if wl["storage"] == "bits" else None
     lat = spinmc.Lattice(wl["d"], wl["L"], n=wl["n"], seed=inputs.DEFAULT_SEED, replica=replica,
                          storage=storage)
     configure(spinmc, lat, wl)
-    R, cap = lat.autotune(wl["beta"], 3)
+    R, cap = lat.autotune(wl["beta"], 3, cache_path=tune_cache)
     if shape is not None:
         shape.update(rows_per_thread=R, blocks_per_sm=cap, tuned_by="sl_autotune")
     E = torch.empty(max(steps, warmup, 1), dtype=torch.float64, device="cuda")
@@ -775,6 +778,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--e2e-jobs", type=int, default=3)
+    ap.add_argument("--tune-cache", default=None,
+                    help="JSON-lines file the launch-shape autotuner reads and appends "
+                         "(lets a profiled run repeat a plain run's shape)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -853,7 +859,7 @@ def main():
     N = L ** d
     shape = {}
     ms, clocks, e_last = time_sweeps(spinmc, wl, args.steps, args.warmup, rank, rank == 0, local,
-                                     shape)
+                                     shape, args.tune_cache)
     ms = max_over_ranks(ms, world)
     hits = wl.get("multihit") or 1
     value = N * hits * args.steps * world / (ms * 1e6)

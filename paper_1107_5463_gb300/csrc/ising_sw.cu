@@ -10,11 +10,11 @@
 //               faces into shared memory (one warp per row, one lane per site
 //               pair), draws the bond uniforms, joins each row's x-runs of
 //               active bonds through warp ballots, then joins the runs along
-//               y and z by rounds of hooking (atomicMin of the larger label
-//               onto the smaller) and pointer jumping in shared memory until
-//               nothing changes, which names every tile cluster by its
-//               smallest site (a y/z bond is skipped when the bond beside it
-//               already joins the same two runs), writes every site's label (the natural index
+//               y and z by a lock-free union-find in shared memory (the
+//               larger root linked below the smaller by compare-and-swap),
+//               which names every tile cluster by its smallest site (a y/z
+//               bond is skipped when the bond beside it already joins the
+//               same two runs), writes every site's label (the natural index
 //               of its tile root, the smallest site of its tile cluster),
 //               one bit per active bond that leaves the tile, and appends
 //               its tile roots to a list;
@@ -179,6 +179,21 @@ __device__ __forceinline__ int nth_set_bit(uint32_t m, int q)
     return pos;
 }
 
+// root of x in the shared parent array, halving the path on the way (a
+// halving store only ever replaces a non-root's parent by an ancestor)
+__device__ __forceinline__ uint32_t sfind(volatile uint32_t* par, uint32_t x)
+{
+    uint32_t p = par[x];
+    while (p != x) {
+        const uint32_t g = par[p];
+        if (g == p) return p;
+        par[x] = g;
+        x = g;
+        p = par[x];
+    }
+    return x;
+}
+
 __device__ __forceinline__ bool bond_active(const SwArgs& a, uint8_t s0, uint8_t s1, uint32_t u)
 {
     return (int)(s0 ^ s1) == a.anti && !a.never && u <= a.thr;
@@ -324,14 +339,9 @@ __global__ void __launch_bounds__(kSwThreads, 3) sw_local(const SwArgs a)
     }
     __syncthreads();
 
-    // Join the runs along y and z by rounds of hooking and pointer jumping:
-    // every bond (u, v) whose ends carry different labels lowers the larger
-    // label's entry to the smaller (atomicMin), then every site follows its
-    // parents to a root and keeps it, until a round changes nothing.  Labels
-    // only decrease and stay inside the cluster, so the fixed point names
-    // every tile cluster by its smallest site.  A bond is left out when the
-    // bond at x - 1 is active and x - 1, x are joined in both rows (the same
-    // two runs).
+    // The runs are joined along y and z by the active bonds between rows.  A
+    // bond is left out when the bond at x - 1 is active and x - 1, x are
+    // joined in both rows (the same two runs).
     uint32_t pend = 0;  // bit (k, e, mu): y/z bond of row k, site e, direction mu
     if (ex) {
 #pragma unroll
@@ -360,12 +370,12 @@ __global__ void __launch_bounds__(kSwThreads, 3) sw_local(const SwArgs a)
             }
         }
     }
-    // Only run heads (the first site of each x-run) take part in the rounds:
-    // every other site keeps pointing at its head, so a label is read through
-    // the head (two steps) and the jumps run over the heads alone, dealt out
-    // to the warp's lanes (lane l takes the l-th and (l + 32)-th head of each
-    // of its rows: one jump per lane where a row has at most 32 heads, against
-    // two sites per lane otherwise).  Heads are decided by the x-bond ballots.
+    // Every parent is a run head (the first site of an x-run), so after the
+    // heads have jumped to their roots a label is read through the head (two
+    // steps).  The heads are dealt out to the warp's lanes for the jump (lane
+    // l takes the l-th and (l + 32)-th head of each of its rows: one jump per
+    // lane where a row has at most 32 heads, against two sites per lane
+    // otherwise); they are decided by the x-bond ballots.
     uint32_t heads[RPW];  // per row: two 16-bit tile-local sites, 0xFFFF = none
     {
         const uint32_t valid = nx >= 64 ? 0xFFFFFFFFu : ((1u << (nx >> 1)) - 1u);
@@ -391,40 +401,46 @@ __global__ void __launch_bounds__(kSwThreads, 3) sw_local(const SwArgs a)
             heads[k] = w;
         }
     }
+    // One union per remaining y/z bond, lock-free: find both roots (path
+    // halving), link the larger root below the smaller by compare-and-swap,
+    // retry from the new roots if another link got there first.  Parents only
+    // ever point to smaller indices and a root links only below a smaller
+    // root, so the root of every tile cluster ends as its smallest site
+    // whatever order the unions run in.  Then every head jumps to its root.
     volatile uint32_t* vp = par;
-    while (true) {
-        bool changed = false;
-        for (uint32_t bits = pend; bits; bits &= bits - 1) {
-            const int bit = __ffs(bits) - 1;
-            const int k = bit / (2 * (D - 1));
-            const int e = (bit / (D - 1)) & 1;
-            const int mu = 1 + bit % (D - 1);
-            const uint32_t u = (uint32_t)(lx0 + e + TX * (warp + NW * k));
-            const uint32_t v = u + (mu == 1 ? (uint32_t)TX : (uint32_t)(TX * TY));
-            const uint32_t pu = vp[vp[u]], pv = vp[vp[v]];
-            if (pu != pv) {
-                atomicMin(par + max(pu, pv), min(pu, pv));
-                changed = true;
-            }
+    for (uint32_t bits = pend; bits; bits &= bits - 1) {
+        const int bit = __ffs(bits) - 1;
+        const int k = bit / (2 * (D - 1));
+        const int e = (bit / (D - 1)) & 1;
+        const int mu = 1 + bit % (D - 1);
+        const uint32_t u = (uint32_t)(lx0 + e + TX * (warp + NW * k));
+        const uint32_t v = u + (mu == 1 ? (uint32_t)TX : (uint32_t)(TX * TY));
+        uint32_t ra = sfind(vp, u), rb = sfind(vp, v);
+        while (ra != rb) {
+            const uint32_t hi = max(ra, rb), lo = min(ra, rb);
+            const uint32_t old = atomicCAS(par + hi, hi, lo);
+            if (old == hi) break;
+            ra = sfind(vp, old);
+            rb = sfind(vp, lo);
         }
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < RPW; ++k) {
-#pragma unroll
-            for (int slot = 0; slot < 2; ++slot) {
-                const uint32_t l = (heads[k] >> (16 * slot)) & 0xFFFFu;
-                if (l == 0xFFFFu) continue;
-                uint32_t p = vp[l];
-                while (true) {
-                    const uint32_t q = vp[p];
-                    if (q == p) break;
-                    p = q;
-                }
-                vp[l] = p;
-            }
-        }
-        if (!__syncthreads_or(changed)) break;
     }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < RPW; ++k) {
+#pragma unroll
+        for (int slot = 0; slot < 2; ++slot) {
+            const uint32_t l = (heads[k] >> (16 * slot)) & 0xFFFFu;
+            if (l == 0xFFFFu) continue;
+            uint32_t p = vp[l];
+            while (true) {
+                const uint32_t q = vp[p];
+                if (q == p) break;
+                p = q;
+            }
+            vp[l] = p;
+        }
+    }
+    __syncthreads();
 
     // labels: the natural index of each site's tile root; tile roots marked
     // and counted (bit 2k + e of `mine`)
