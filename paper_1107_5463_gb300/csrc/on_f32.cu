@@ -202,7 +202,10 @@ __device__ __forceinline__ bool heis_metropolis(float& sx, float& sy, float& sz,
     const float dE = -__fmaf_rn(__fsub_rn(v.z, sz), hz,
                                 __fmaf_rn(__fsub_rn(v.y, sy), hy,
                                           __fmul_rn(__fsub_rn(v.x, sx), hx)));
-    if (dE <= 0.f || u < boltzmann<FAST>(__fmul_rn(-beta, dE))) {
+    // the Boltzmann factor is evaluated whatever the sign of dE, so the step
+    // is straight-line code the scheduler can interleave with other sites
+    const float w = boltzmann<FAST>(__fmul_rn(-beta, dE));
+    if ((dE <= 0.f) | (u < w)) {
         sx = v.x;
         sy = v.y;
         sz = v.z;
@@ -807,11 +810,16 @@ __global__ void __launch_bounds__(256, D == 2 ? 3 : 2) heis_pair(const OnArgs a)
             hB.z = heis_field<D>(p ? ez : cur.z.x, cur.z.y, prev.z.y, nxt.z.y, vm.z.y, vp.z.y, J);
             if (a.update) {
                 bool changed = false;
+                // both sites' random numbers first: two independent chains
+                uint4 rnd2[2];
 #pragma unroll
-                for (int b = 0; b < 2; ++b) {
-                    const uint4 rnd = philox4x32_10(
+                for (int b = 0; b < 2; ++b)
+                    rnd2[b] = philox4x32_10(
                         make_uint4((uint32_t)(j + b), t, a.replica, (kSweep << 1) | (uint32_t)a.c),
                         a.rk);
+#pragma unroll
+                for (int b = 0; b < 2; ++b) {
+                    const uint4 rnd = rnd2[b];
                     float& sx = b ? s.x.y : s.x.x;
                     float& sy = b ? s.y.y : s.y.x;
                     float& sz = b ? s.z.y : s.z.x;
@@ -1292,13 +1300,15 @@ __global__ void __launch_bounds__(256) xy_stream(const OnArgs a)
                 const float dE0 = -((nx0 - sx0) * hx0 + (ny0 - sy0) * hy0);
                 const float dE1 = -((nx1 - sx1) * hx1 + (ny1 - sy1) * hy1);
                 bool ch = false;
-                if (dE0 <= 0.f || u24(rnd.x) < boltzmann<FAST>(-a.beta * dE0)) {
+                const float w0 = boltzmann<FAST>(-a.beta * dE0);
+                const float w1 = boltzmann<FAST>(-a.beta * dE1);
+                if ((dE0 <= 0.f) | (u24(rnd.x) < w0)) {
                     th.x = n0;
                     sx0 = nx0;
                     sy0 = ny0;
                     ch = true;
                 }
-                if (dE1 <= 0.f || u24(rnd.z) < boltzmann<FAST>(-a.beta * dE1)) {
+                if ((dE1 <= 0.f) | (u24(rnd.z) < w1)) {
                     th.y = n1;
                     sx1 = nx1;
                     sy1 = ny1;
