@@ -193,20 +193,27 @@ __device__ void run_sample(const BatchArgs& a, int s, int L, unsigned char* base
                 uint32_t pl[4][3];
 #pragma unroll
                 for (int b = 0; b < 4; ++b) pl[b][0] = pl[b][1] = pl[b][2] = 0u;
+                auto draw = [&](int r) {
+                    const uint4 rnd = philox4x32_10(
+                        make_uint4((uint32_t)g, (uint32_t)t, gs * (uint32_t)nt + (uint32_t)r, ctr_w), a.rk);
+                    const uint4 nth = thr_slot[r];
+                    const uint32_t u[4] = {rnd.x, rnd.y, rnd.z, rnd.w};
 #pragma unroll
-                for (int r = kMaxTemps - 1; r >= 0; --r) {
-                    if (r < nt) {
-                        const uint4 rnd = philox4x32_10(
-                            make_uint4((uint32_t)g, (uint32_t)t, gs * (uint32_t)nt + (uint32_t)r, ctr_w), a.rk);
-                        const uint4 nth = thr_slot[r];
-                        const uint32_t u[4] = {rnd.x, rnd.y, rnd.z, rnd.w};
-#pragma unroll
-                        for (int b = 0; b < 4; ++b) {
-                            pl[b][0] = push_gt(pl[b][0], u[b], nth.x);
-                            pl[b][1] = push_gt(pl[b][1], u[b], nth.y);
-                            if (D == 3) pl[b][2] = push_gt(pl[b][2], u[b], nth.z);
-                        }
+                    for (int b = 0; b < 4; ++b) {
+                        pl[b][0] = push_gt(pl[b][0], u[b], nth.x);
+                        pl[b][1] = push_gt(pl[b][1], u[b], nth.y);
+                        if (D == 3) pl[b][2] = push_gt(pl[b][2], u[b], nth.z);
                     }
+                };
+                if (nt == kMaxTemps) {
+                    // no branch between the draws, so the scheduler can
+                    // interleave several Philox blocks
+#pragma unroll
+                    for (int r = kMaxTemps - 1; r >= 0; --r) draw(r);
+                } else {
+#pragma unroll
+                    for (int r = kMaxTemps - 1; r >= 0; --r)
+                        if (r < nt) draw(r);
                 }
 #pragma unroll
                 for (int b = 0; b < 4; ++b) {

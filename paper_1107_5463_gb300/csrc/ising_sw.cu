@@ -249,6 +249,18 @@ __global__ void __launch_bounds__(kSwThreads, 3) sw_local(const SwArgs a)
             dst[nx] = (uint8_t)a.s[(x + y + z) & 1u][(rowbase + x) >> 1];
         }
     }
+    // 2D: the bond uniforms of both of the warp's rows are drawn here, with
+    // no branch between them, while the spin loads are in flight (rows
+    // outside a ragged tile draw values nobody reads)
+    uint4 pre[D == 2 ? RPW : 1];
+    if (D == 2) {
+#pragma unroll
+        for (int k = 0; k < RPW; ++k) {
+            const int ly = (warp + NW * k) % TY;
+            const uint32_t i0 = (uint32_t)(X0 + lx0) + L * (uint32_t)(Y0 + ly);
+            pre[k] = philox4x32_10(make_uint4(i0 >> 1, t, a.replica, kSwBond << 1), a.rk);
+        }
+    }
     __syncthreads();
 
     // Bond activation, one warp per row.  A row splits into x-runs of sites
@@ -267,7 +279,7 @@ __global__ void __launch_bounds__(kSwThreads, 3) sw_local(const SwArgs a)
             // uniforms of the x / y / z bonds of the even (e = 0) and odd site
             uint4 r0, r1;
             if (D == 2) {
-                r0 = philox4x32_10(make_uint4(i0 >> 1, t, a.replica, kSwBond << 1), a.rk);
+                r0 = pre[D == 2 ? k : 0];
                 r1 = make_uint4(r0.z, r0.w, 0u, 0u);
             } else {
                 r0 = philox4x32_10(make_uint4(i0, t, a.replica, kSwBond << 1), a.rk);

@@ -205,12 +205,14 @@ __global__ void __launch_bounds__(32) walk_kernel(const WalkArgs a)
         uint32_t oa, ob;
         sweep_order(a, t, oa, ob);
         const int64_t inc = WL && active ? ((int64_t)1 << (32 - stage)) : 0;
-        uint4 rnd = make_uint4(0, 0, 0, 0);
         const uint32_t nmask = (uint32_t)(N - 1);
-        for (uint32_t q = 0; q < (uint32_t)N; ++q) {
-            if ((q & 3) == 0)
-                rnd = philox4x32_10(make_uint4(q >> 2, t, walker, (WL ? kWL : kMUCA) << 1), a.rk);
-            const uint32_t u = (q & 3) == 0 ? rnd.x : ((q & 3) == 1 ? rnd.y : ((q & 3) == 2 ? rnd.z : rnd.w));
+        const uint32_t purpose = (WL ? kWL : kMUCA) << 1;
+        // the block of the next four attempts is drawn while the current four
+        // run (the attempts depend on each other, the draws do not; N is a
+        // multiple of 4, and the draw after the last block goes unused)
+        uint4 rnd_nx = philox4x32_10(make_uint4(0u, t, walker, purpose), a.rk);
+        // one attempt at position q of the sweep with uniform u
+        auto attempt = [&](uint32_t q, uint32_t u) {
             const uint32_t i = (oa * q + ob) & nmask;  // N divides 2^32
             uint32_t own;
             const int nu = unlike([&](uint32_t w) { return col[w]; }, i, L, a.log2L, lane, own);
@@ -236,6 +238,14 @@ __global__ void __launch_bounds__(32) walk_kernel(const WalkArgs a)
                 H[kr * 32 + lane] += 1u;
             }
             __syncwarp();
+        };
+        for (uint32_t q = 0; q < (uint32_t)N; q += 4) {
+            const uint4 rnd = rnd_nx;
+            rnd_nx = philox4x32_10(make_uint4((q >> 2) + 1u, t, walker, purpose), a.rk);
+            attempt(q, rnd.x);
+            attempt(q + 1, rnd.y);
+            attempt(q + 2, rnd.z);
+            attempt(q + 3, rnd.w);
         }
         if (WL && active) {
             int nv = 0;
