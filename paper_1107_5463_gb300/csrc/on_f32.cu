@@ -1216,6 +1216,9 @@ __global__ void __launch_bounds__(256) xy_stream(const OnArgs a)
             if (p0 ? lane == 31 : lane == 0)
                 edge_pf = __ldg(a.oth + (long long)m0 * W + (p0 ? kr : kl));
         }
+        // two rows at a time for Metropolis (their draws and sin/cos interleave);
+        // the heat-bath's attempt loops do better one row at a time
+#pragma unroll (HB ? 1 : 2)
         for (int r = 0; r < R; ++r) {
             const int m = m0 + r;
             const int p = (m + a.c) & 1;
