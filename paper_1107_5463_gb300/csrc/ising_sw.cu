@@ -589,44 +589,65 @@ __device__ __forceinline__ uint32_t root_bit(const SwArgs& a, uint32_t i, uint32
 // Every site flips iff its cluster's root drew the flip bit.  A thread takes
 // four site pairs (x even, x + 1): eight labels and one 32-bit word of each
 // colour array.
+// Threads of a block share rows: tq threads per row (the whole block on a
+// long row), so the row's coordinates and colour come from one division per
+// row rather than per word.
+struct RowSplit {
+    int tq, rpb, rsub, q0;
+    __device__ RowSplit(int Q)
+    {
+        tq = Q >= (int)blockDim.x ? (int)blockDim.x : Q;
+        rpb = (int)blockDim.x / tq;
+        rsub = (int)threadIdx.x / tq;
+        q0 = (int)threadIdx.x - rsub * tq;
+    }
+};
+
 __global__ void __launch_bounds__(256) sw_flip(const SwArgs a)
 {
     const long long H = a.N >> 1;
-    const long long nq = (H + 3) >> 2;
-    const int L = a.L;
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nq;
-         q += (long long)gridDim.x * blockDim.x) {
-        const long long j0 = 4 * q;
-        if (j0 + 4 <= H) {
-            const uint4 la = __ldg(reinterpret_cast<const uint4*>(a.lab) + 2 * q);
-            const uint4 lb = __ldg(reinterpret_cast<const uint4*>(a.lab) + 2 * q + 1);
-            const uint32_t lw[8] = {la.x, la.y, la.z, la.w, lb.x, lb.y, lb.z, lb.w};
-            uint32_t fl0 = 0u, fl1 = 0u;  // flips of colour 0 / colour 1 bytes
+    const int L = a.L, W = L >> 1;
+    if ((W & 3) == 0) {
+        // rows of W colour entries, 4 per word of each colour array; the
+        // labels of the 8 sites of word q are the uint4 pair 2q, 2q + 1
+        const int Q = W >> 2;
+        const long long rows = H / W;
+        const RowSplit rs(Q);
+        if (rs.rsub >= rs.rpb) return;
+        for (long long row = (long long)blockIdx.x * rs.rpb + rs.rsub; row < rows;
+             row += (long long)gridDim.x * rs.rpb) {
+            const bool c0 = ((row % L + row / L) & 1) != 0;  // colour of the even sites
+            for (int qi = rs.q0; qi < Q; qi += rs.tq) {
+                const long long q = row * Q + qi;
+                const uint4 la = __ldg(reinterpret_cast<const uint4*>(a.lab) + 2 * q);
+                const uint4 lb = __ldg(reinterpret_cast<const uint4*>(a.lab) + 2 * q + 1);
+                const uint32_t lw[8] = {la.x, la.y, la.z, la.w, lb.x, lb.y, lb.z, lb.w};
+                const uint32_t i0 = (uint32_t)(8 * q);
+                uint32_t fl0 = 0u, fl1 = 0u;  // flips of colour 0 / colour 1 bytes
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const long long i0 = 2 * (j0 + e);
-                const long long row = i0 / L;
-                const bool c0 = ((row % L + row / L) & 1) != 0;  // colour of the even site
-                const uint32_t fe = root_bit(a, (uint32_t)i0, lw[2 * e]) << (8 * e);
-                const uint32_t fo = root_bit(a, (uint32_t)i0 + 1, lw[2 * e + 1]) << (8 * e);
-                fl0 |= c0 ? fo : fe;
-                fl1 |= c0 ? fe : fo;
-            }
-            if (fl0) reinterpret_cast<uint32_t*>(a.s[0])[q] ^= fl0;
-            if (fl1) reinterpret_cast<uint32_t*>(a.s[1])[q] ^= fl1;
-        } else {
-            for (long long j = j0; j < H; ++j) {
-                const long long i0 = 2 * j;
-                const long long row = i0 / L;
-                const int c0 = (int)((row % L + row / L) & 1);
-#pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    const uint32_t i = (uint32_t)(i0 + e);
-                    const int8_t f = (int8_t)root_bit(a, i, __ldg(a.lab + i));
-                    int8_t* sp = a.s[c0 ^ e] + j;
-                    *sp = (int8_t)(*sp ^ f);
+                for (int e = 0; e < 4; ++e) {
+                    const uint32_t fe = root_bit(a, i0 + 2 * e, lw[2 * e]) << (8 * e);
+                    const uint32_t fo = root_bit(a, i0 + 2 * e + 1, lw[2 * e + 1]) << (8 * e);
+                    fl0 |= c0 ? fo : fe;
+                    fl1 |= c0 ? fe : fo;
                 }
+                if (fl0) reinterpret_cast<uint32_t*>(a.s[0])[q] ^= fl0;
+                if (fl1) reinterpret_cast<uint32_t*>(a.s[1])[q] ^= fl1;
             }
+        }
+        return;
+    }
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < H;
+         j += (long long)gridDim.x * blockDim.x) {
+        const long long i0 = 2 * j;
+        const long long row = i0 / L;
+        const int c0 = (int)((row % L + row / L) & 1);
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const uint32_t i = (uint32_t)(i0 + e);
+            const int8_t f = (int8_t)root_bit(a, i, __ldg(a.lab + i));
+            int8_t* sp = a.s[c0 ^ e] + j;
+            *sp = (int8_t)(*sp ^ f);
         }
     }
 }
@@ -642,32 +663,33 @@ __global__ void __launch_bounds__(256) sw_measure(const SwArgs a, Partial* parti
     __shared__ long long red[32];
     const int L = a.L, W = L / 2, Q = W / 4;
     const long long rows = (long long)L * (D == 3 ? L : 1);
-    const long long items = rows * Q;
     const uint32_t* own = reinterpret_cast<const uint32_t*>(a.s[1]);
     const uint32_t* oth = reinterpret_cast<const uint32_t*>(a.s[0]);
     const uint32_t ones = 0x01010101u;
     long long bond = 0, down = 0;
-    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < items;
-         it += (long long)gridDim.x * blockDim.x) {
-        const int q = (int)(it % Q);
-        const long long row = it / Q;
+    const RowSplit rs(Q);
+    for (long long row = (long long)blockIdx.x * rs.rpb + rs.rsub; rs.rsub < rs.rpb && row < rows;
+         row += (long long)gridDim.x * rs.rpb) {
         const int y = (int)(row % L), z = D == 3 ? (int)(row / L) : 0;
         const int p = (y + z + 1) & 1;
         const long long base = row * Q;
-        const uint32_t A = __ldcs(own + base + q);
-        const uint32_t cur = __ldg(oth + base + q);
-        const uint32_t S = p ? __funnelshift_r(cur, __ldg(oth + base + (q + 1 == Q ? 0 : q + 1)), 8)
-                             : __funnelshift_l(__ldg(oth + base + (q == 0 ? Q - 1 : q - 1)), cur, 8);
-        const long long ym = row - y + (y == 0 ? L - 1 : y - 1);
-        const long long yp = row - y + (y == L - 1 ? 0 : y + 1);
-        uint32_t nd = cur + S + __ldg(oth + ym * Q + q) + __ldg(oth + yp * Q + q);
-        if (D == 3) {
-            const long long zm = (z == 0 ? L - 1 : z - 1), zp = (z == L - 1 ? 0 : z + 1);
-            nd += __ldg(oth + (zm * L + y) * Q + q) + __ldg(oth + (zp * L + y) * Q + q);
+        for (int q = rs.q0; q < Q; q += rs.tq) {
+            const uint32_t A = __ldcs(own + base + q);
+            const uint32_t cur = __ldg(oth + base + q);
+            const uint32_t S =
+                p ? __funnelshift_r(cur, __ldg(oth + base + (q + 1 == Q ? 0 : q + 1)), 8)
+                  : __funnelshift_l(__ldg(oth + base + (q == 0 ? Q - 1 : q - 1)), cur, 8);
+            const long long ym = row - y + (y == 0 ? L - 1 : y - 1);
+            const long long yp = row - y + (y == L - 1 ? 0 : y + 1);
+            uint32_t nd = cur + S + __ldg(oth + ym * Q + q) + __ldg(oth + yp * Q + q);
+            if (D == 3) {
+                const long long zm = (z == 0 ? L - 1 : z - 1), zp = (z == L - 1 ? 0 : z + 1);
+                nd += __ldg(oth + (zm * L + y) * Q + q) + __ldg(oth + (zp * L + y) * Q + q);
+            }
+            const uint32_t na = (nd ^ (A * 7u)) - A * (uint32_t)(7 - 2 * D);
+            bond += 8 * D - 2 * (long long)__dp4a(na, ones, 0u);
+            down += (long long)__dp4a(A, ones, __dp4a(cur, ones, 0u));
         }
-        const uint32_t na = (nd ^ (A * 7u)) - A * (uint32_t)(7 - 2 * D);
-        bond += 8 * D - 2 * (long long)__dp4a(na, ones, 0u);
-        down += (long long)__dp4a(A, ones, __dp4a(cur, ones, 0u));
     }
     Partial mine;
     mine.i0 = block_sum(bond, red);
@@ -707,7 +729,7 @@ cudaError_t sw_update(const SwArgs& a0, cudaStream_t s)
     sw_local<D><<<(unsigned)a.ntiles, kSwThreads, 0, s>>>(a);
     sw_merge<D><<<grid_for(mergers, 256), 256, 0, s>>>(a);
     sw_resolve<<<grid_for(a.N, 256), 256, 0, s>>>(a);
-    sw_flip<<<grid_for((a.N / 2 + 3) / 4, 256), 256, 0, s>>>(a);
+    sw_flip<<<grid_for((a.N / 2 + 3) / 4, 256), 256, 0, s>>>(a);  // at most one block per row used
     return cudaGetLastError();
 }
 
