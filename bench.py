@@ -420,21 +420,32 @@ def configure(spinmc, lat, wl):
 
 
 def time_sweeps(spinmc, wl, steps, warmup, replica, want_clocks, local, shape=None,
-                tune_cache=None):
+                tune_cache=None, fixed_shape=None):
     """Device-timed K sweeps of one lattice, after the launch-shape autotuner
     picked rows per thread and the grid cap (outside the timed region; its
     choice is read from and written to `tune_cache` when one is given, so a
     profiled run can repeat the shape a plain run picked); returns (ms,
-    clocks, E of the last sweep) and fills `shape`."""
+    clocks, E of the last sweep) and fills `shape`.  `fixed_shape` = (rows per
+    thread, blocks per SM, kernel variant) sets the launch shape instead of
+    tuning it (0 keeps the library's default for that option)."""
     import torch
     from paper_1107_5463_gb300 import inputs
     storage = spinmc.SL_STORE_BITS if wl["storage"] == "bits" else None
     lat = spinmc.Lattice(wl["d"], wl["L"], n=wl["n"], seed=inputs.DEFAULT_SEED, replica=replica,
                          storage=storage)
     configure(spinmc, lat, wl)
-    R, cap = lat.autotune(wl["beta"], 3, cache_path=tune_cache)
-    if shape is not None:
-        shape.update(rows_per_thread=R, blocks_per_sm=cap, tuned_by="sl_autotune")
+    if fixed_shape is not None:
+        R, cap, kern = fixed_shape
+        lat.set_option(spinmc.SL_OPT_ROWS, R)
+        lat.set_option(spinmc.SL_OPT_BLOCKS_PER_SM, cap)
+        if kern:
+            lat.set_option(spinmc.SL_OPT_KERNEL, kern)
+        if shape is not None:
+            shape.update(rows_per_thread=R, blocks_per_sm=cap, kernel=kern, tuned_by="--shape")
+    else:
+        R, cap = lat.autotune(wl["beta"], 3, cache_path=tune_cache)
+        if shape is not None:
+            shape.update(rows_per_thread=R, blocks_per_sm=cap, tuned_by="sl_autotune")
     E = torch.empty(max(steps, warmup, 1), dtype=torch.float64, device="cuda")
     m = torch.empty_like(E)
     spinmc.sl_sweep_series(lat.h, wl["beta"], warmup, inputs.DEFAULT_SEED, E, m)
@@ -778,6 +789,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--e2e-jobs", type=int, default=3)
+    ap.add_argument("--shape", default=None,
+                    help="ROWS,BLOCKS_PER_SM,KERNEL: fix the launch shape (and for 3D "
+                         "Heisenberg the kernel: 2 column pairs, 3 single columns, 4 "
+                         "staged tiles) instead of tuning it; 0 keeps a default")
     ap.add_argument("--tune-cache", default=None,
                     help="JSON-lines file the launch-shape autotuner reads and appends "
                          "(lets a profiled run repeat a plain run's shape)")
@@ -858,8 +873,11 @@ def main():
         return
     N = L ** d
     shape = {}
+    fixed = tuple(int(v) for v in args.shape.split(",")) if args.shape else None
+    if fixed is not None and len(fixed) != 3:
+        ap.error("--shape takes ROWS,BLOCKS_PER_SM,KERNEL")
     ms, clocks, e_last = time_sweeps(spinmc, wl, args.steps, args.warmup, rank, rank == 0, local,
-                                     shape, args.tune_cache)
+                                     shape, args.tune_cache, fixed)
     ms = max_over_ranks(ms, world)
     hits = wl.get("multihit") or 1
     value = N * hits * args.steps * world / (ms * 1e6)
