@@ -205,9 +205,10 @@ __device__ void run_sample(const BatchArgs& a, int s, int L, unsigned char* base
                         if (D == 3) pl[b][2] = push_gt(pl[b][2], u[b], nth.z);
                     }
                 };
-                if (nt == kMaxTemps) {
+                if (D == 3 && nt == kMaxTemps) {
                     // no branch between the draws, so the scheduler can
-                    // interleave several Philox blocks
+                    // interleave several Philox blocks (3D; in 2D the
+                    // interleaved draws spill registers and run slower)
 #pragma unroll
                     for (int r = kMaxTemps - 1; r >= 0; --r) draw(r);
                 } else {

@@ -420,13 +420,7 @@ __global__ void __launch_bounds__(kSwThreads, 3) sw_local(const SwArgs a)
     // root, so the root of every tile cluster ends as its smallest site
     // whatever order the unions run in.  Then every head jumps to its root.
     volatile uint32_t* vp = par;
-    for (uint32_t bits = pend; bits; bits &= bits - 1) {
-        const int bit = __ffs(bits) - 1;
-        const int k = bit / (2 * (D - 1));
-        const int e = (bit / (D - 1)) & 1;
-        const int mu = 1 + bit % (D - 1);
-        const uint32_t u = (uint32_t)(lx0 + e + TX * (warp + NW * k));
-        const uint32_t v = u + (mu == 1 ? (uint32_t)TX : (uint32_t)(TX * TY));
+    auto unite = [&](uint32_t u, uint32_t v) {
         uint32_t ra = sfind(vp, u), rb = sfind(vp, v);
         while (ra != rb) {
             const uint32_t hi = max(ra, rb), lo = min(ra, rb);
@@ -434,6 +428,39 @@ __global__ void __launch_bounds__(kSwThreads, 3) sw_local(const SwArgs a)
             if (old == hi) break;
             ra = sfind(vp, old);
             rb = sfind(vp, lo);
+        }
+    };
+    if (D == 2) {
+        // the warp's bonds are packed into a shared list (a scan of the lanes'
+        // counts places them) and dealt out evenly, so the warp runs as many
+        // union rounds as its mean load needs rather than its busiest lane's
+        __shared__ uint16_t plist[NW][D == 2 ? 2 * RPW * 32 : 1];
+        const unsigned cnt = __popc(pend);
+        unsigned incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned x = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= o) incl += x;
+        }
+        const unsigned total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        unsigned pos = incl - cnt;
+        for (uint32_t bits = pend; bits; bits &= bits - 1) {
+            const int bit = __ffs(bits) - 1;  // bit 2k + e: row k, site e
+            plist[warp][pos++] = (uint16_t)(lx0 + (bit & 1) + TX * (warp + NW * (bit >> 1)));
+        }
+        __syncwarp();
+        for (unsigned q = lane; q < total; q += 32) {
+            const uint32_t u = plist[warp][q];
+            unite(u, u + (uint32_t)TX);
+        }
+    } else {
+        for (uint32_t bits = pend; bits; bits &= bits - 1) {
+            const int bit = __ffs(bits) - 1;
+            const int k = bit / (2 * (D - 1));
+            const int e = (bit / (D - 1)) & 1;
+            const int mu = 1 + bit % (D - 1);
+            const uint32_t u = (uint32_t)(lx0 + e + TX * (warp + NW * k));
+            unite(u, u + (mu == 1 ? (uint32_t)TX : (uint32_t)(TX * TY)));
         }
     }
     __syncthreads();
