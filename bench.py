@@ -120,6 +120,8 @@ WORKLOADS = {
                                     "[0.5, 3], replica exchange every sweep, one persistent graph-captured "
                                     "launch, samples per CTA chosen by the autotuner"),
 }
+for _name, _wl in WORKLOADS.items():
+    _wl["name"] = _name
 HEADLINE = "ising2d_L16384_i8"
 
 
@@ -155,9 +157,9 @@ def kernel_source_hash(files):
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload):
-    """DRAM bytes per launch of the dominant kernel from a committed ncu
-    summary, only if the kernel sources are unchanged since it was taken."""
+def recorded_profile(workload):
+    """The committed ncu record of a workload's dominant kernel, only if the
+    kernel sources are unchanged since it was taken."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -166,7 +168,31 @@ def recorded_traffic(workload):
     e = j.get(workload)
     if not e or e.get("source_hash") != kernel_source_hash(e.get("source_files", [])):
         return None
-    return e.get("dram_bytes_per_launch")
+    return e
+
+
+def recorded_traffic(workload):
+    """DRAM bytes per launch of the dominant kernel from a committed ncu
+    summary, only if the kernel sources are unchanged since it was taken."""
+    e = recorded_profile(workload)
+    return e.get("dram_bytes_per_launch") if e else None
+
+
+def issue_fraction(workload, flips_per_ns):
+    """The kernel's issue use on the instructions it actually executes: the
+    thread instructions per site update that ncu counted (committed record,
+    same sources), at one warp instruction per cycle per scheduler (128
+    lanes per SM per clock at the maximum SM clock), against the measured
+    rate; None without a current record."""
+    e = recorded_profile(workload)
+    ipc = e.get("thread_instructions_per_site") if e else None
+    peak = alu_peak_tops() if (ipc and torch_cuda()) else None
+    if not peak:
+        return None
+    bound = peak * 1e3 / ipc
+    return {"instructions_per_site": ipc, "peak": peak, "unit": "T thread instructions/s",
+            "bound_flips_per_ns": bound, "frac": flips_per_ns / bound,
+            "source": e.get("summary")}
 
 
 class Clocks:
@@ -336,6 +362,10 @@ def roofline_for(wl, flips_per_ns, launch_ms=None, hbm=None, peak_kind="measured
         out["hbm"] = hbm_obj
     out["bound_flips_per_ns"] = min(hbm_bound, alu_bound)
     out["traffic"] = traffic
+    if wl.get("name"):
+        iss = issue_fraction(wl["name"], flips_per_ns)
+        if iss:
+            out["issue"] = iss
     if kernel_name:
         out["kernel"] = kernel_name
     if launch_ms is not None and N is not None:
@@ -958,7 +988,8 @@ def main():
             v2 = batch_run(spinmc, plain_lattices=0, d=2, sizes=[32] * 1024)
             v2["paper_gtx480_flips_per_ns"] = 1 / 0.0023
             v2["over_paper_gtx480"] = v2["value"] / v2["paper_gtx480_flips_per_ns"]
-            v2["roofline"] = roofline_for(dict(WORKLOADS["ea3d_batch_1024x32"], d=2, ops=26),
+            v2["roofline"] = roofline_for(dict(WORKLOADS["ea3d_batch_1024x32"], d=2, ops=26,
+                                               name="ea2d_batch_L32_1024x32"),
                                           v2["value"], kernel_name="ea_pt_persistent<2>")
             var["ea2d_batch_L32_1024x32"] = v2
             line["variants"] = var

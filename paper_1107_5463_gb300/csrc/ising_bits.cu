@@ -113,6 +113,8 @@ __global__ void __launch_bounds__(128) bits_stream(const BitArgs a)
             ym_nx = __ldg(a.oth + row(y_m, m0) * WW + w);
             yp_nx = __ldg(a.oth + row(y_p, m0) * WW + w);
         }
+        // two rows per loop pass, so their Philox blocks interleave
+#pragma unroll 2
         for (int r = 0; r < R; ++r) {
             const int m = m0 + r;
             const int yy = D == 3 ? y3 : m;
