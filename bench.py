@@ -166,9 +166,13 @@ def recorded_profile(workload):
     with open(p) as f:
         j = json.load(f)
     e = j.get(workload)
-    if not e or e.get("source_hash") != kernel_source_hash(e.get("source_files", [])):
+    if not e:
         return None
-    return e
+    try:
+        current = kernel_source_hash(e.get("source_files", []))
+    except OSError:  # a source file is gone: the record cannot be current
+        return None
+    return e if e.get("source_hash") == current else None
 
 
 def recorded_traffic(workload):
