@@ -592,16 +592,26 @@ __global__ void __launch_bounds__(256) sw_resolve(const SwArgs a)
 {
     const uint32_t t = (uint32_t)a.ctrl->t;
     const unsigned n = *a.nroots;
-    for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
-        const uint32_t r = __ldcg(a.roots + q);
-        uint32_t p = gload(a.lab + r) & kMask;
+    const unsigned stride = gridDim.x * blockDim.x;
+    // two roots per pass with their chases interleaved, so each thread keeps
+    // two dependent load chains in flight (a missing second root repeats the
+    // first and stores nothing)
+    for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += 2 * stride) {
+        const bool two = q + stride < n;
+        const uint32_t r0 = __ldcg(a.roots + q);
+        const uint32_t r1 = two ? __ldcg(a.roots + q + stride) : r0;
+        uint32_t p0 = gload(a.lab + r0) & kMask, p1 = gload(a.lab + r1) & kMask;
         while (true) {
-            const uint32_t g = gload(a.lab + p) & kMask;
-            if (g == p) break;
-            p = g;
+            const uint32_t g0 = gload(a.lab + p0) & kMask;
+            const uint32_t g1 = gload(a.lab + p1) & kMask;
+            if (g0 == p0 && g1 == p1) break;
+            p0 = g0;
+            p1 = g1;
         }
-        const uint4 rnd = philox4x32_10(make_uint4(p, t, a.replica, kSwFlip << 1), a.rk);
-        gstore(a.lab + r, p | kTileRoot | ((rnd.x >> 31) ? kFlipBit : 0u));
+        const uint4 rnd0 = philox4x32_10(make_uint4(p0, t, a.replica, kSwFlip << 1), a.rk);
+        const uint4 rnd1 = philox4x32_10(make_uint4(p1, t, a.replica, kSwFlip << 1), a.rk);
+        gstore(a.lab + r0, p0 | kTileRoot | ((rnd0.x >> 31) ? kFlipBit : 0u));
+        if (two) gstore(a.lab + r1, p1 | kTileRoot | ((rnd1.x >> 31) ? kFlipBit : 0u));
     }
 }
 
