@@ -384,34 +384,51 @@ __global__ void __launch_bounds__(kSwThreads, 3) sw_local(const SwArgs a)
     }
     // Every parent is a run head (the first site of an x-run), so after the
     // heads have jumped to their roots a label is read through the head (two
-    // steps).  The heads are dealt out to the warp's lanes for the jump (lane
-    // l takes the l-th and (l + 32)-th head of each of its rows: one jump per
-    // lane where a row has at most 32 heads, against two sites per lane
-    // otherwise); they are decided by the x-bond ballots.
-    uint32_t heads[RPW];  // per row: two 16-bit tile-local sites, 0xFFFF = none
+    // steps).  The warp lists the heads of its rows in shared memory (each
+    // lane places its own by a population count of the ballot below it) and
+    // deals the list out over its lanes for the jump; the heads are decided
+    // by the x-bond ballots.
+    // (3D, whose tile already fills most of the shared memory, keeps the
+    // heads in registers instead: lane l takes the l-th and (l + 32)-th
+    // head of each of its rows)
+    __shared__ uint16_t hlist[NW][D == 2 ? RPW * TX : 1];
+    unsigned nh = 0;                   // 2D: heads listed by the warp (warp-uniform)
+    uint32_t heads[D == 2 ? 1 : RPW];  // 3D: per row two 16-bit sites, 0xFFFF = none
     {
         const uint32_t valid = nx >= 64 ? 0xFFFFFFFFu : ((1u << (nx >> 1)) - 1u);
+        const uint32_t below = (1u << lane) - 1u;
 #pragma unroll
         for (int k = 0; k < RPW; ++k) {
-            heads[k] = 0xFFFFFFFFu;
+            if (D == 3) heads[D == 2 ? 0 : k] = 0xFFFFFFFFu;
             const int row = warp + NW * k;
             const int ly = row % TY, lz = row / TY;
             if (ly >= ny || lz >= nz) continue;
             const uint32_t h0 = ~(bx[1][row] << 1) & valid;  // even sites starting a run
             const uint32_t h1 = ~bx[0][row] & valid;         // odd sites starting a run
-            const int n0 = __popc(h0), n = n0 + __popc(h1);
-            uint32_t w = 0;
+            const unsigned n0 = __popc(h0);
+            if (D == 2) {
+                if ((h0 >> lane) & 1u)
+                    hlist[warp][nh + __popc(h0 & below)] = (uint16_t)(TX * row + lx0);
+                if ((h1 >> lane) & 1u)
+                    hlist[warp][nh + n0 + __popc(h1 & below)] = (uint16_t)(TX * row + lx0 + 1);
+                nh += n0 + __popc(h1);
+            } else {
+                const int n = (int)n0 + __popc(h1);
+                uint32_t w = 0;
 #pragma unroll
-            for (int slot = 0; slot < 2; ++slot) {
-                const int q = lane + 32 * slot;
-                uint32_t site = 0xFFFFu;
-                if (q < n)
-                    site = (uint32_t)(TX * row) + (q < n0 ? 2u * (uint32_t)nth_set_bit(h0, q)
-                                                          : 2u * (uint32_t)nth_set_bit(h1, q - n0) + 1u);
-                w |= site << (16 * slot);
+                for (int slot = 0; slot < 2; ++slot) {
+                    const int q = lane + 32 * slot;
+                    uint32_t site = 0xFFFFu;
+                    if (q < n)
+                        site = (uint32_t)(TX * row) +
+                               (q < (int)n0 ? 2u * (uint32_t)nth_set_bit(h0, q)
+                                            : 2u * (uint32_t)nth_set_bit(h1, q - (int)n0) + 1u);
+                    w |= site << (16 * slot);
+                }
+                heads[D == 2 ? 0 : k] = w;
             }
-            heads[k] = w;
         }
+        __syncwarp();
     }
     // One union per remaining y/z bond, lock-free: find both roots (path
     // halving), link the larger root below the smaller by compare-and-swap,
@@ -464,20 +481,25 @@ __global__ void __launch_bounds__(kSwThreads, 3) sw_local(const SwArgs a)
         }
     }
     __syncthreads();
-#pragma unroll
-    for (int k = 0; k < RPW; ++k) {
-#pragma unroll
-        for (int slot = 0; slot < 2; ++slot) {
-            const uint32_t l = (heads[k] >> (16 * slot)) & 0xFFFFu;
-            if (l == 0xFFFFu) continue;
-            uint32_t p = vp[l];
-            while (true) {
-                const uint32_t q = vp[p];
-                if (q == p) break;
-                p = q;
-            }
-            vp[l] = p;
+    auto jump = [&](uint32_t l) {
+        uint32_t p = vp[l];
+        while (true) {
+            const uint32_t g = vp[p];
+            if (g == p) break;
+            p = g;
         }
+        vp[l] = p;
+    };
+    if (D == 2) {
+        for (unsigned q = lane; q < nh; q += 32) jump(hlist[warp][q]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < RPW; ++k)
+#pragma unroll
+            for (int slot = 0; slot < 2; ++slot) {
+                const uint32_t l = (heads[D == 2 ? 0 : k] >> (16 * slot)) & 0xFFFFu;
+                if (l != 0xFFFFu) jump(l);
+            }
     }
     __syncthreads();
 
@@ -704,9 +726,65 @@ __global__ void __launch_bounds__(256) sw_measure(const SwArgs a, Partial* parti
     const uint32_t* oth = reinterpret_cast<const uint32_t*>(a.s[0]);
     const uint32_t ones = 0x01010101u;
     long long bond = 0, down = 0;
+    // one site word: A own, cur the other colour's word at the same place,
+    // S its x-shifted neighbour word, nv the y (and z) neighbour words
+    auto word = [&](uint32_t A, uint32_t cur, uint32_t S, uint32_t nv) {
+        const uint32_t nd = cur + S + nv;
+        const uint32_t na = (nd ^ (A * 7u)) - A * (uint32_t)(7 - 2 * D);
+        bond += 8 * D - 2 * (long long)__dp4a(na, ones, 0u);
+        down += (long long)__dp4a(A, ones, __dp4a(cur, ones, 0u));
+    };
+    if ((Q & 3) == 0) {
+        // 16-byte chunks of four words: 128-bit loads, the x shift inside the
+        // chunk, one edge word from the chunk beside it
+        const int Q4 = Q >> 2;
+        const uint4* own4 = reinterpret_cast<const uint4*>(own);
+        const uint4* oth4 = reinterpret_cast<const uint4*>(oth);
+        const RowSplit rs(Q4);
+        for (long long row = (long long)blockIdx.x * rs.rpb + rs.rsub;
+             rs.rsub < rs.rpb && row < rows; row += (long long)gridDim.x * rs.rpb) {
+            const int y = (int)(row % L), z = D == 3 ? (int)(row / L) : 0;
+            const int p = (y + z + 1) & 1;
+            const long long ym = row - y + (y == 0 ? L - 1 : y - 1);
+            const long long yp = row - y + (y == L - 1 ? 0 : y + 1);
+            const long long zm = D == 3 ? ((z == 0 ? L - 1 : z - 1) * (long long)L + y) : 0;
+            const long long zp = D == 3 ? ((z == L - 1 ? 0 : z + 1) * (long long)L + y) : 0;
+            for (int c = rs.q0; c < Q4; c += rs.tq) {
+                const uint4 A = __ldcs(own4 + row * Q4 + c);
+                const uint4 cur = __ldg(oth4 + row * Q4 + c);
+                const uint32_t edge =
+                    __ldg(oth + row * Q + (p ? (c + 1 == Q4 ? 0 : 4 * c + 4) : (c == 0 ? Q - 1 : 4 * c - 1)));
+                uint4 nv = __ldg(oth4 + ym * Q4 + c);
+                const uint4 v2 = __ldg(oth4 + yp * Q4 + c);
+                nv.x += v2.x;
+                nv.y += v2.y;
+                nv.z += v2.z;
+                nv.w += v2.w;
+                if (D == 3) {
+                    const uint4 v3 = __ldg(oth4 + zm * Q4 + c);
+                    const uint4 v4 = __ldg(oth4 + zp * Q4 + c);
+                    nv.x += v3.x + v4.x;
+                    nv.y += v3.y + v4.y;
+                    nv.z += v3.z + v4.z;
+                    nv.w += v3.w + v4.w;
+                }
+                if (p) {
+                    word(A.x, cur.x, __funnelshift_r(cur.x, cur.y, 8), nv.x);
+                    word(A.y, cur.y, __funnelshift_r(cur.y, cur.z, 8), nv.y);
+                    word(A.z, cur.z, __funnelshift_r(cur.z, cur.w, 8), nv.z);
+                    word(A.w, cur.w, __funnelshift_r(cur.w, edge, 8), nv.w);
+                } else {
+                    word(A.x, cur.x, __funnelshift_l(edge, cur.x, 8), nv.x);
+                    word(A.y, cur.y, __funnelshift_l(cur.x, cur.y, 8), nv.y);
+                    word(A.z, cur.z, __funnelshift_l(cur.y, cur.z, 8), nv.z);
+                    word(A.w, cur.w, __funnelshift_l(cur.z, cur.w, 8), nv.w);
+                }
+            }
+        }
+    }
     const RowSplit rs(Q);
-    for (long long row = (long long)blockIdx.x * rs.rpb + rs.rsub; rs.rsub < rs.rpb && row < rows;
-         row += (long long)gridDim.x * rs.rpb) {
+    for (long long row = (long long)blockIdx.x * rs.rpb + rs.rsub;
+         (Q & 3) != 0 && rs.rsub < rs.rpb && row < rows; row += (long long)gridDim.x * rs.rpb) {
         const int y = (int)(row % L), z = D == 3 ? (int)(row / L) : 0;
         const int p = (y + z + 1) & 1;
         const long long base = row * Q;
@@ -718,14 +796,12 @@ __global__ void __launch_bounds__(256) sw_measure(const SwArgs a, Partial* parti
                   : __funnelshift_l(__ldg(oth + base + (q == 0 ? Q - 1 : q - 1)), cur, 8);
             const long long ym = row - y + (y == 0 ? L - 1 : y - 1);
             const long long yp = row - y + (y == L - 1 ? 0 : y + 1);
-            uint32_t nd = cur + S + __ldg(oth + ym * Q + q) + __ldg(oth + yp * Q + q);
+            uint32_t nv = __ldg(oth + ym * Q + q) + __ldg(oth + yp * Q + q);
             if (D == 3) {
                 const long long zm = (z == 0 ? L - 1 : z - 1), zp = (z == L - 1 ? 0 : z + 1);
-                nd += __ldg(oth + (zm * L + y) * Q + q) + __ldg(oth + (zp * L + y) * Q + q);
+                nv += __ldg(oth + (zm * L + y) * Q + q) + __ldg(oth + (zp * L + y) * Q + q);
             }
-            const uint32_t na = (nd ^ (A * 7u)) - A * (uint32_t)(7 - 2 * D);
-            bond += 8 * D - 2 * (long long)__dp4a(na, ones, 0u);
-            down += (long long)__dp4a(A, ones, __dp4a(cur, ones, 0u));
+            word(A, cur, S, nv);
         }
     }
     Partial mine;

@@ -48,7 +48,7 @@ def test_sw_2d_parity(sm, L):
     run_both(sm, 2, L, BETA_C, 12)
 
 
-@pytest.mark.parametrize("L", [2, 4, 6, 16, 34])
+@pytest.mark.parametrize("L", [2, 4, 6, 16, 32, 34])
 def test_sw_3d_parity(sm, L):
     run_both(sm, 3, L, BETA_3D, 8)
 
