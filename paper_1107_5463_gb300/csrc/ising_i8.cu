@@ -291,9 +291,10 @@ __global__ void __launch_bounds__(128) i8_stream(const I8Args a)
             ym_nx = ld_rows(a.oth + off(y_m, zz0) + k0);
             yp_nx = ld_rows(a.oth + off(y_p, zz0) + k0);
         }
-        // 2D: two rows per loop pass, so their Philox blocks interleave (in 3D
-        // the extra registers cost more than the overlap gains)
-#pragma unroll (D == 2 ? 2 : 1)
+        // two rows per loop pass, so their Philox blocks interleave (not for
+        // the 3D measuring pass, whose extra registers cost more than the
+        // overlap gains)
+#pragma unroll ((D == 2 || !MEAS) ? 2 : 1)
         for (int r = 0; r < R; ++r) {
             const int m = m0 + r;
             int yy, zz;
