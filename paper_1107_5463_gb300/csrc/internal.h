@@ -66,7 +66,8 @@ struct sl_lattice {
     void* staging;           // natural-order staging area
     size_t staging_bytes;
     spinmc::Ctrl* ctrl;
-    spinmc::Partial* partials;
+    spinmc::Partial* partials;  // kMaxBlocks block partials, then the integer
+                                // totals a deferred byte pass accumulates
     bool bonds_have_zero;
     // options
     int renorm_every, fast_math, kernel, rows, use_graph;

@@ -65,8 +65,9 @@ __device__ __forceinline__ void fadd(uint32_t a, uint32_t b, uint32_t c, uint32_
     k = (a & b) | (c & (a ^ b));
 }
 
-// MEAS: the measuring (colour-1) pass, which stores its block partials for
-// bits_finish_kernel; the other pass is compiled without the counters.
+// MEAS: the measuring (colour-1) pass, whose blocks add their integer totals
+// into the accumulator after the block partials for bits_finish_kernel; the
+// other pass is compiled without the counters.
 // SLAB: a slab of a split lattice (halo planes, global offsets).
 template <int D, int JNEG, bool MEAS, bool SLAB = false>
 __global__ void __launch_bounds__(128) bits_stream(const BitArgs a)
@@ -198,17 +199,24 @@ __global__ void __launch_bounds__(128) bits_stream(const BitArgs a)
     Partial mine;
     mine.i0 = block_sum(bond, red);
     mine.i1 = block_sum((long long)down, red);
-    mine.f[0] = mine.f[1] = mine.f[2] = mine.f[3] = 0.0;
-    store_partial(a.partials, mine);
+    // integer totals: the order of the additions does not matter
+    if (threadIdx.x == 0) {
+        Partial* acc = a.partials + kMaxBlocks;
+        atomicAdd(reinterpret_cast<unsigned long long*>(&acc->i0), (unsigned long long)mine.i0);
+        atomicAdd(reinterpret_cast<unsigned long long*>(&acc->i1), (unsigned long long)mine.i1);
+    }
 }
 
-// Adds the partials a measuring pass of nblocks blocks stored and closes the
-// pass (one block of kFinishThreads).
-__global__ void __launch_bounds__(kFinishThreads) bits_finish_kernel(const BitArgs a,
-                                                                     unsigned nblocks)
+// Closes a measuring pass from the totals its blocks added into the
+// accumulator, and clears the accumulator for the next pass (one thread; the
+// kernel boundary orders it after the pass).
+__global__ void bits_finish_kernel(const BitArgs a)
 {
-    const Partial tot = sum_partials<false>(a.partials, nblocks);
-    if (threadIdx.x == 0) bits_finish(a, tot);
+    Partial* acc = a.partials + kMaxBlocks;
+    Partial tot = *acc;
+    acc->i0 = 0;
+    acc->i1 = 0;
+    bits_finish(a, tot);
 }
 
 // wofs: global index of local word 0 (the global colour index of entry 0 / 32)
@@ -343,7 +351,7 @@ cudaError_t launch(const sl_lattice* h, const BitArgs& a, cudaStream_t s)
     if (a.measure) {
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        bits_finish_kernel<<<1, kFinishThreads, 0, s>>>(a, (unsigned)grid);
+        bits_finish_kernel<<<1, 1, 0, s>>>(a);
     }
     return cudaGetLastError();
 }

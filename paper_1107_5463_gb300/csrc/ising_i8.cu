@@ -51,7 +51,7 @@ struct I8Args {
     int measure;  // accumulate E and M and finish the pass
     int update;   // 0: standalone measurement (no moves, no sweep advance)
     int advance;  // a measurement that closes a sweep: write the series, t + 1
-    int defer;    // i8_stream: store block partials for i8_finish_kernel
+    int defer;    // i8_stream: add the block totals into the accumulator for i8_finish_kernel
     int Lz;       // planes along the slowest axis (L, or the slab's planes)
     int wrap;     // 1: periodic along the slowest axis; 0: halo planes at -1 and Lz
     int par;      // parity of the first plane's global index
@@ -456,19 +456,28 @@ __global__ void __launch_bounds__(128) i8_stream(const I8Args a)
     mine.i1 = block_sum((long long)down, red);
     mine.f[0] = mine.f[1] = mine.f[2] = mine.f[3] = 0.0;
     if (a.defer) {
-        store_partial(a.partials, mine);
+        // integer totals: the order of the additions does not matter, so
+        // every block adds its own into the pass's accumulator
+        if (threadIdx.x == 0) {
+            Partial* acc = a.partials + kMaxBlocks;
+            atomicAdd(reinterpret_cast<unsigned long long*>(&acc->i0), (unsigned long long)mine.i0);
+            atomicAdd(reinterpret_cast<unsigned long long*>(&acc->i1), (unsigned long long)mine.i1);
+        }
         return;
     }
     finish_pass(a.ctrl, a.partials, mine, [&](const Partial& tot) { i8_finish(a, tot); });
 }
 
-// Adds the partials an i8_stream measuring pass of nblocks blocks stored and
-// closes the pass (one block of kFinishThreads).
-__global__ void __launch_bounds__(kFinishThreads) i8_finish_kernel(const I8Args a,
-                                                                   unsigned nblocks)
+// Closes an i8_stream measuring pass from the totals its blocks added into
+// the accumulator after the block partials, and clears the accumulator for
+// the next pass (one thread; the kernel boundary orders it after the pass).
+__global__ void i8_finish_kernel(const I8Args a)
 {
-    const Partial tot = sum_partials<false>(a.partials, nblocks);
-    if (threadIdx.x == 0) i8_finish(a, tot);
+    Partial* acc = a.partials + kMaxBlocks;
+    Partial tot = *acc;
+    acc->i0 = 0;
+    acc->i1 = 0;
+    i8_finish(a, tot);
 }
 
 // ------------------------------------------------------ init / layout ----
@@ -636,7 +645,7 @@ cudaError_t launch_pass(const sl_lattice* h, I8Args a, cudaStream_t s, bool stre
         if (a.defer) {
             const cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) return e;
-            i8_finish_kernel<<<1, kFinishThreads, 0, s>>>(a, (unsigned)grid);
+            i8_finish_kernel<<<1, 1, 0, s>>>(a);
         }
     } else {
         const int grid = grid_for((h->H + 3) >> 2, 256);

@@ -106,7 +106,7 @@ Layout make_layout(int d, int L, int n, int j_layout, int storage, int Lz = 0, b
     y.off_ctrl = off;
     off += align_up(sizeof(Ctrl));
     y.off_partials = off;
-    off += align_up(sizeof(Partial) * kMaxBlocks);
+    off += align_up(sizeof(Partial) * (kMaxBlocks + 1));
     y.total = off;
     return y;
 }
@@ -397,6 +397,8 @@ int create_lattice(int d, int L, int n, int j_layout, int storage, double J, con
         return st;
     }
     e = cudaMemsetAsync(h->ctrl, 0, sizeof(Ctrl), h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(h->partials + kMaxBlocks, 0, sizeof(Partial), h->stream);
     if (e == cudaSuccess && storage == SL_STORE_I8) e = ising_i8_init(h, h->stream);
     if (e == cudaSuccess && storage == SL_STORE_BITS) e = ising_bits_init(h, h->stream);
     if (e == cudaSuccess && n > 1) e = on_init(h, h->stream);
