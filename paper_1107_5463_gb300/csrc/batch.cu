@@ -267,16 +267,32 @@ __device__ void run_sample(const BatchArgs& a, int s, int L, unsigned char* base
             }
             group_sync(bar, nthr);
         }
-        // per-slot unsatisfied bonds: column sums of the counters
+        // per-slot unsatisfied bonds: the warp's counters are summed slot by
+        // slot in bitsliced form, by a butterfly of bitsliced adds over the
+        // lanes (five rounds; a sum of 32 counters below 256 needs 13
+        // planes), after which lane r reads slot r's total from bit r
         {
+            uint32_t w[13];
+#pragma unroll
+            for (int b = 0; b < 13; ++b) w[b] = b < 8 ? cnt[b] : 0u;
+#pragma unroll
+            for (int lvl = 0; lvl < 5; ++lvl) {
+                const int nb = 9 + lvl;  // planes that can be set after this round
+                uint32_t c = 0u;
+#pragma unroll
+                for (int b = 0; b < 13; ++b) {
+                    if (b < nb) {
+                        const uint32_t x =
+                            b < nb - 1 ? __shfl_xor_sync(0xFFFFFFFFu, w[b], 16 >> lvl) : 0u;
+                        const uint32_t sum = w[b] ^ x ^ c;
+                        c = (w[b] & x) | (c & (w[b] ^ x));
+                        w[b] = sum;
+                    }
+                }
+            }
             int mine = 0;
 #pragma unroll
-            for (int b = 0; b < 8; ++b)
-#pragma unroll
-                for (int r = 0; r < 32; ++r) {
-                    const unsigned v = __ballot_sync(0xFFFFFFFFu, (cnt[b] >> r) & 1u);
-                    if (lane == r) mine += __popc(v) << b;
-                }
+            for (int b = 0; b < 13; ++b) mine |= (int)((w[b] >> lane) & 1u) << b;
             atomicAdd(&unsat[lane], mine);
         }
         group_sync(bar, nthr);
