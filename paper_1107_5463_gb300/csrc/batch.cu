@@ -207,9 +207,12 @@ __device__ void run_sample(const BatchArgs& a, int s, int L, unsigned char* base
                 };
                 if (D == 3 && nt == kMaxTemps) {
                     // no branch between the draws, so the scheduler can
-                    // interleave several Philox blocks (3D; in 2D the
-                    // interleaved draws spill registers and run slower)
+                    // interleave several Philox blocks
 #pragma unroll
+                    for (int r = kMaxTemps - 1; r >= 0; --r) draw(r);
+                } else if (nt == kMaxTemps) {
+                    // (2D: eight at a time, which keeps the registers in bounds)
+#pragma unroll 8
                     for (int r = kMaxTemps - 1; r >= 0; --r) draw(r);
                 } else {
 #pragma unroll

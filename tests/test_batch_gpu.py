@@ -77,7 +77,8 @@ def test_start_state_and_couplings(sm):
 
 
 @pytest.mark.parametrize("d,Ls,nt", [(3, [4, 8, 12], 8), (3, [8, 12, 16, 24, 32], 32),
-                                     (2, [8, 16, 32], 16), (3, [8], 2), (2, [4, 12], 5)])
+                                     (2, [8, 16, 32], 16), (2, [8, 16, 32, 32], 32),
+                                     (3, [8], 2), (2, [4, 12], 5)])
 def test_parity_ten_sweeps(sm, d, Ls, nt):
     check_batch(sm, d, Ls, nt, inputs.geometric_betas(nt), 10)
 
